@@ -1,0 +1,138 @@
+/*
+ * dgmx — nodal discontinuous Galerkin solver for the 3D Maxwell equations on
+ * straight-sided tetrahedra, for one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: Kloeckner, Warburton & Hesthaven, "High-Order Discontinuous Galerkin
+ * Methods by GPU Metaprogramming" (arXiv 1211.0582).
+ *   - Section 2, eq. (semidiscrete-dg): du/dt = -sum_nu D^nu F(u) + L [n.F - (n.F)*],
+ *     evaluated element by element (local differentiation + flux gather + flux lifting).
+ *   - Section 2, eq. (dg-reference-matrices): affine elements, per-element J_k, dr/dx.
+ *   - Section 2, Fig. (lifting-matrix): lifting matrix L = M^-1 [M^A1 ... M^A4].
+ *   - Section 5, Fig. (flux-code) a: Maxwell flux n.(F - F*)_E = 1/2 n x ([H] - alpha n x [E]).
+ *   - Section 5: RK4 time stepping (here the five-stage low-storage scheme of
+ *     Carpenter & Kennedy, 2N storage).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Fields: six FP32 fields ordered Ex, Ey, Ez, Hx, Hy, Hz. A field vector is a
+ * DEVICE buffer laid out [6][K][Np_pad] (element-major structure of arrays):
+ * value of field c at node i of element k is at c*K*Np_pad + k*Np_pad + i.
+ * Np = (N+1)(N+2)(N+3)/6 nodes per element, Np_pad = Np rounded up to a
+ * multiple of 4 (16-byte rows). Padding entries are ignored on input and
+ * written as zero on output. Field buffers must be 16-byte aligned.
+ * Node order within an element is the warp & blend lattice order
+ * (t outer, s middle, r inner) on the reference tetrahedron
+ * (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1); dg_node_coords() returns it.
+ *
+ * Ownership: the caller owns every field, residual and gradient buffer; the
+ * library owns operators, mesh/geometry data and internal scratch, allocated by
+ * dg_mesh_upload() and freed by dg_destroy(). All device work is ordered on the
+ * CUDA stream given to dg_create() (borrowed, not owned; NULL = legacy default
+ * stream). Calls return after enqueueing, except where a host output is written.
+ *
+ * Errors: every function returns a dg_status; no exception crosses the ABI and
+ * nothing aborts the process. dg_last_error() describes the last failure on a
+ * context. A context is not thread-safe: use one per host thread.
+ */
+#ifndef DGMX_H
+#define DGMX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,         /* invalid argument (null pointer, size, alignment) */
+  DG_ERR_MESH = -2,        /* invalid mesh (bad index, inverted element, non-conforming face) */
+  DG_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  DG_ERR_NONFINITE = -4,   /* a NaN or Inf was detected in a result */
+  DG_ERR_TIMEOUT = -5,     /* a device-side wait exceeded its iteration limit */
+  DG_ERR_UNSUPPORTED = -6, /* valid request that this build does not implement */
+  DG_ERR_OOM = -7          /* device allocation failed */
+} dg_status;
+
+typedef enum {
+  DG_FP32 = 0,   /* FP32 arithmetic on the CUDA cores */
+  DG_BF16X3 = 1, /* D and LIFT contractions on tensor cores, BF16 hi+lo split, FP32 accumulate */
+  DG_FP16X3 = 2  /* same with FP16 hi+lo split (row-scaled), FP32 accumulate */
+} dg_precision;
+
+/* Create a context for polynomial order N (1..7) and the given arithmetic.
+ * cuda_stream is a cudaStream_t (may be NULL). *out receives the context.
+ * Builds the reference operators on the host and makes no CUDA call; the
+ * tensor-core precisions are checked against the device at dg_mesh_upload.
+ * Errors: DG_ERR_ARG (N out of range, bad precision), DG_ERR_CUDA. */
+int dg_create(dg_ctx **out, int N, int precision, void *cuda_stream);
+
+/* Release the context and everything it owns. NULL is accepted. */
+int dg_destroy(dg_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none); valid until the next call.
+ * ctx may be NULL (then the last failure of dg_create is reported). */
+const char *dg_last_error(const dg_ctx *ctx);
+
+/* Set up operators (Section 2: warp & blend nodes, orthonormal-basis
+ * Vandermonde, Dr/Ds/Dt, LIFT, face-node maps) and upload the mesh.
+ * All inputs are HOST arrays: VX/VY/VZ (Nv vertex coordinates, FP64), EToV
+ * (K x 4 vertex indices, 0-based, int32), eps/mu (K relative permittivity and
+ * permeability per element, > 0; NULL means 1), bc (K x 4 face tags or NULL:
+ * every boundary face is a perfect electric conductor, the only supported
+ * boundary, tag 1; tags of interior faces are ignored). Geometric factors and
+ * Jacobian inverses are computed on the device in FP64 and stored in FP32.
+ * Replaces any previous mesh. Synchronises the stream before returning.
+ * Errors: DG_ERR_ARG, DG_ERR_MESH (index out of range, J_k <= 0, a face shared
+ * by more than two elements, neighbouring face nodes that do not coincide),
+ * DG_ERR_UNSUPPORTED (a boundary tag other than 1), DG_ERR_OOM, DG_ERR_CUDA. */
+int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, const double *VZ,
+                   int64_t K, const int32_t *EToV, const float *eps, const float *mu,
+                   const int32_t *bc);
+
+/* Sizes of the uploaded layout: Np, Np_pad and K (any pointer may be NULL). */
+int dg_layout(const dg_ctx *ctx, int *Np, int *Np_pad, int64_t *K);
+
+/* Reference operators built by dg_create (HOST FP64 copies, row-major; any
+ * pointer may be NULL): nodes r, s, t (Np), Dr/Ds/Dt and the mass matrix M
+ * (Np x Np), LIFT (Np x 4Nfp, face blocks in the order t=-1, s=-1,
+ * r+s+t=-1, r=-1) and Fmask (4 x Nfp volume node of each face node). Needs no
+ * GPU and no mesh. */
+int dg_operators(const dg_ctx *ctx, double *r, double *s, double *t, double *Dr, double *Ds, double *Dt,
+                 double *M, double *LIFT, int32_t *Fmask);
+
+/* Physical node coordinates, HOST output xyz[3][K][Np] (FP64, unpadded). */
+int dg_node_coords(dg_ctx *ctx, double *xyz);
+
+/* Replace the per-element permittivity (DEVICE pointer to K FP32 values > 0)
+ * without re-uploading the mesh; impedances are recomputed on the device. */
+int dg_set_eps(dg_ctx *ctx, const float *eps_dev);
+
+/* Semi-discrete right-hand side rhs = A(eps) u (eq. semidiscrete-dg with the
+ * Maxwell flux; alpha = 1 upwind, 0 central): the volume term (local
+ * differentiation with the chain rule, giving curl H and -curl E), the flux
+ * gather (upwind flux with impedance-weighted material jumps, PEC mirror on
+ * boundary faces) and the flux lifting, scaled by 1/eps and 1/mu.
+ * u and rhs are DEVICE field vectors ([6][K][Np_pad] FP32) and must not alias.
+ * Errors: DG_ERR_ARG (null/misaligned/aliasing), DG_ERR_CUDA. */
+int dg_rhs(dg_ctx *ctx, const float *u, float *rhs, float alpha);
+
+/* Advance nsteps LSERK4 steps of size dt: for each of the five stages s,
+ * res <- a_s res + dt A u, u <- u + b_s res (one fused kernel per stage).
+ * u and res are DEVICE field vectors, updated in place; res should be zero
+ * before the first step of a run (a_1 = 0 makes its old value irrelevant).
+ * Uses a library-owned scratch field vector for the stage ping-pong.
+ * Errors: DG_ERR_ARG, DG_ERR_CUDA. */
+int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);
+
+/* Discrete energy 1/2 sum_k J_k (eps_k E^T M E + mu_k H^T M H), reduced in
+ * FP64 on the device; *E_out is a HOST double. Synchronises the stream.
+ * Returns DG_ERR_NONFINITE if the energy is NaN or Inf. */
+int dg_energy(dg_ctx *ctx, const float *u, double *E_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGMX_H */

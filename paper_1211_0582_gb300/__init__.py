@@ -1,0 +1,161 @@
+"""Python binding of libdgmx (nodal DG for 3D Maxwell on GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library behind the C ABI declared in include/dgmx.h. PyTorch supplies device
+memory and streams. There is no CPU fallback: if the library cannot be built
+or loaded, the import of `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libdgmx.so")
+_lock = threading.Lock()
+_lib = None
+
+DG_OK = 0
+STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_CUDA", -4: "DG_ERR_NONFINITE",
+          -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_UNSUPPORTED", -7: "DG_ERR_OOM"}
+PRECISION = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
+
+
+class DGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libdgmx.so (building it with nvcc if it is not there yet)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                from . import build as _build
+                _build.build()
+            L = C.CDLL(_LIB_PATH)
+            vp, i64, i32, dbl, flt = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_float
+            L.dg_create.argtypes = [C.POINTER(vp), i32, i32, vp]
+            L.dg_destroy.argtypes = [vp]
+            L.dg_last_error.argtypes = [vp]
+            L.dg_last_error.restype = C.c_char_p
+            L.dg_mesh_upload.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp]
+            L.dg_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
+            L.dg_operators.argtypes = [vp] + [vp] * 9
+            L.dg_node_coords.argtypes = [vp, vp]
+            L.dg_set_eps.argtypes = [vp, vp]
+            L.dg_rhs.argtypes = [vp, vp, vp, flt]
+            L.dg_step.argtypes = [vp, vp, vp, dbl, i32, flt]
+            L.dg_energy.argtypes = [vp, vp, C.POINTER(dbl)]
+            _lib = L
+    return _lib
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _t_ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One mesh, one polynomial order, one arithmetic, one CUDA stream."""
+
+    def __init__(self, N: int, precision: str = "fp32", stream=None):
+        import torch
+        self.N = N
+        self.precision = precision
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        handle = C.c_void_p()
+        sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+        rc = lib().dg_create(C.byref(handle), N, PRECISION[precision], sp)
+        if rc != DG_OK:
+            raise DGError(rc, lib().dg_last_error(None).decode())
+        self._h = handle
+        self.K = 0
+        Np, Npad, K = C.c_int(), C.c_int(), C.c_int64()
+        lib().dg_layout(self._h, C.byref(Np), C.byref(Npad), C.byref(K))
+        self.Np, self.Npad = Np.value, Npad.value
+        self.Nfp = (N + 1) * (N + 2) // 2
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().dg_destroy(h)
+            self._h = None
+
+    def _check(self, rc: int):
+        if rc != DG_OK:
+            raise DGError(rc, lib().dg_last_error(self._h).decode())
+
+    # ---------------------------------------------------------------- setup
+    def upload(self, VX, VY, VZ, EToV, eps=None, mu=None, bc=None):
+        VX, VY, VZ = (np.ascontiguousarray(v, dtype=np.float64) for v in (VX, VY, VZ))
+        EToV = np.ascontiguousarray(EToV, dtype=np.int32)
+        eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float32)
+        mu = None if mu is None else np.ascontiguousarray(mu, dtype=np.float32)
+        bc = None if bc is None else np.ascontiguousarray(bc, dtype=np.int32)
+        K = EToV.shape[0]
+        self._check(lib().dg_mesh_upload(self._h, VX.size, _np_ptr(VX), _np_ptr(VY), _np_ptr(VZ), K,
+                                         _np_ptr(EToV), _np_ptr(eps), _np_ptr(mu), _np_ptr(bc)))
+        self.K = K
+        return self
+
+    def operators(self) -> dict:
+        Np, Nfp = self.Np, self.Nfp
+        out = dict(r=np.zeros(Np), s=np.zeros(Np), t=np.zeros(Np), Dr=np.zeros((Np, Np)),
+                   Ds=np.zeros((Np, Np)), Dt=np.zeros((Np, Np)), M=np.zeros((Np, Np)),
+                   LIFT=np.zeros((Np, 4 * Nfp)), Fmask=np.zeros((4, Nfp), dtype=np.int32))
+        self._check(lib().dg_operators(self._h, *[_np_ptr(out[k]) for k in
+                                                  ("r", "s", "t", "Dr", "Ds", "Dt", "M", "LIFT", "Fmask")]))
+        return out
+
+    def node_coords(self):
+        xyz = np.zeros((3, self.K, self.Np))
+        self._check(lib().dg_node_coords(self._h, _np_ptr(xyz)))
+        return xyz[0], xyz[1], xyz[2]
+
+    def set_eps(self, eps_dev):
+        self._check(lib().dg_set_eps(self._h, _t_ptr(eps_dev)))
+
+    # ---------------------------------------------------------------- fields
+    def zeros(self, device="cuda"):
+        import torch
+        return torch.zeros((6, self.K, self.Npad), dtype=torch.float32, device=device)
+
+    def to_device(self, u, device="cuda"):
+        """[6][K][Np] array -> padded FP32 device tensor [6][K][Npad]."""
+        import torch
+        out = torch.zeros((6, self.K, self.Npad), dtype=torch.float32)
+        out[:, :, :self.Np] = torch.as_tensor(np.asarray(u), dtype=torch.float32)
+        return out.to(device)
+
+    def from_device(self, t) -> np.ndarray:
+        return t[:, :, :self.Np].double().cpu().numpy()
+
+    # ---------------------------------------------------------------- operators
+    def rhs(self, u, out=None, alpha: float = 1.0):
+        out = self.zeros(u.device) if out is None else out
+        self._check(lib().dg_rhs(self._h, _t_ptr(u), _t_ptr(out), float(alpha)))
+        return out
+
+    def step(self, u, res, dt: float, nsteps: int = 1, alpha: float = 1.0):
+        self._check(lib().dg_step(self._h, _t_ptr(u), _t_ptr(res), float(dt), int(nsteps), float(alpha)))
+        return u, res
+
+    def energy(self, u) -> float:
+        E = C.c_double()
+        self._check(lib().dg_energy(self._h, _t_ptr(u), C.byref(E)))
+        return E.value

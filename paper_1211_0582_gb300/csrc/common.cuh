@@ -1,0 +1,90 @@
+// Internal definitions shared by the CUDA translation units of libdgmx.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "refops.h"
+
+namespace dgmx {
+
+// Per-element FP32 record (64 bytes): metric terms, material factors, Jacobian.
+enum GeoSlot {
+  G_RX = 0, G_RY, G_RZ, G_SX, G_SY, G_SZ, G_TX, G_TY, G_TZ,
+  G_IEPS = 9, G_IMU = 10, G_Z = 11, G_Y = 12, G_J = 13,
+  G_STRIDE = 16
+};
+
+// Stage kinds of the fused kernels.
+enum StageMode { MODE_RHS = 0, MODE_LSERK = 1 };
+
+// Arguments of one fused right-hand-side / LSERK-stage launch.
+struct StageArgs {
+  const float *u;      // [6][K][Npad] state the right-hand side is evaluated at
+  float *rhs;          // MODE_RHS: output [6][K][Npad]
+  float *res;          // MODE_LSERK: residual, updated in place
+  float *u_out;        // MODE_LSERK: u + b * res (must not alias u)
+  const float *geo;    // [K][16]
+  const float4 *fgeo;  // [K][4] {nx, ny, nz, Fscale}
+  const int2 *fconn;   // [K][4] {neighbour element, connection kind}
+  const float *DT;     // [3][Np][Npad]  transposed Dr, Ds, Dt
+  const float *LT;     // [4Nfp][Npad]   transposed LIFT
+  const uint8_t *fmask;  // [4Nfp]  volume node of each face node
+  const uint8_t *nbrtab; // [96][Nfp] neighbour volume node per connection kind
+  int64_t K;
+  float alpha;         // 1 upwind, 0 central
+  float rk_a, rk_b, dt;
+};
+
+// Launchers, one per kernel family (defined in the .cu files).
+cudaError_t launch_stage_simt(int N, int mode, const StageArgs &a, cudaStream_t s);
+template <int N>
+cudaError_t launch_simt_order(int mode, const StageArgs &a, cudaStream_t s);
+
+struct GeometryArgs {
+  int64_t K;
+  const double *VX, *VY, *VZ;
+  const int32_t *EToV;
+  const float *eps, *mu;
+  float *geo;
+  float4 *fgeo;
+  int *bad;  // first element index with J <= 0 (atomicMin), K if none
+};
+cudaError_t launch_geometry(const GeometryArgs &a, cudaStream_t s);
+cudaError_t launch_set_eps(int64_t K, const float *eps, float *geo, int *bad, cudaStream_t s);
+cudaError_t launch_energy(int N, int64_t K, int Npad, const float *u, const float *geo, const double *M,
+                          double *out, cudaStream_t s);
+
+// Five-stage fourth-order low-storage Runge-Kutta coefficients (Carpenter &
+// Kennedy 1994, 2N storage).
+extern const double kLserkA[5];
+extern const double kLserkB[5];
+extern const double kLserkC[5];
+
+} // namespace dgmx
+
+// Library context (opaque to callers).
+struct dg_ctx {
+  int N = 0;
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  dgmx::RefOps ops;
+  std::string err;
+  int64_t K = 0;
+  int64_t Nv = 0;
+  // device data owned by the context
+  float *d_geo = nullptr;
+  float4 *d_fgeo = nullptr;
+  int2 *d_fconn = nullptr;
+  float *d_DT = nullptr;
+  float *d_LT = nullptr;
+  uint8_t *d_tab = nullptr;  // fmask (4Nfp) followed by the neighbour-node table (96 Nfp)
+  double *d_M = nullptr;
+  float *d_scratch = nullptr;  // field vector for the LSERK stage ping-pong
+  double *d_red = nullptr;     // reduction outputs
+  int *d_flag = nullptr;
+  void *tc = nullptr;          // tensor-core operator buffers (precision != DG_FP32)
+  std::vector<double> host_vert;   // VX, VY, VZ (kept for node coordinates)
+  std::vector<int32_t> host_EToV;
+};

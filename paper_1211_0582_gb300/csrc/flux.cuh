@@ -1,0 +1,48 @@
+// Device-side pieces shared by the fused right-hand-side kernels: sizes per
+// polynomial order and the Maxwell numerical flux at one face node.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace dgmx {
+
+template <int N>
+struct Dims {
+  static constexpr int NP = (N + 1) * (N + 2) * (N + 3) / 6; // nodes per element
+  static constexpr int NFP = (N + 1) * (N + 2) / 2;          // nodes per face
+  static constexpr int NPP = (NP + 3) / 4 * 4;               // padded row length
+  static constexpr int NQ = NPP / 4;                         // float4 per row
+  static constexpr int NFF = 4 * NFP;                        // face nodes per element
+};
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+// Flux difference n.(F - F*) at one face node, times Fscale (Section 5,
+// Fig. flux-code a, with jumps dq = q+ - q- and impedance weights for
+// material jumps):
+//   flux_E = n x (Z+ dH - alpha n x dE) / (Z- + Z+)
+//   flux_H = -n x (Y+ dE + alpha n x dH) / (Y- + Y+)
+// qm/qp: Ex Ey Ez Hx Hy Hz on the interior/exterior side; out: 6 values.
+__device__ __forceinline__ void maxwell_flux(float4 nf, const float *qm, const float *qp, float Zm, float Zp,
+                                             float Ym, float Yp, float alpha, float *out) {
+  const float nx = nf.x, ny = nf.y, nz = nf.z, fs = nf.w;
+  float dEx = qp[0] - qm[0], dEy = qp[1] - qm[1], dEz = qp[2] - qm[2];
+  float dHx = qp[3] - qm[3], dHy = qp[4] - qm[4], dHz = qp[5] - qm[5];
+  // n x dE, n x dH
+  float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
+  float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
+  float wE = fs / (Zm + Zp), wH = -fs / (Ym + Yp);
+  float vx = Zp * dHx - alpha * cEx, vy = Zp * dHy - alpha * cEy, vz = Zp * dHz - alpha * cEz;
+  out[0] = wE * (ny * vz - nz * vy);
+  out[1] = wE * (nz * vx - nx * vz);
+  out[2] = wE * (nx * vy - ny * vx);
+  vx = Yp * dEx + alpha * cHx;
+  vy = Yp * dEy + alpha * cHy;
+  vz = Yp * dEz + alpha * cHz;
+  out[3] = wH * (ny * vz - nz * vy);
+  out[4] = wH * (nz * vx - nx * vz);
+  out[5] = wH * (nx * vy - ny * vx);
+}
+
+} // namespace dgmx

@@ -1,0 +1,215 @@
+// FP32 CUDA-core form of the fused right-hand side / LSERK stage.
+//
+// One block owns EB consecutive elements and runs the paper's four subtasks
+// (Section 2, Fig. dg-subtasks) on them without leaving the SM:
+//   1. stage the block's fields u[6][EB][Npad] in shared memory (float4 loads,
+//      coalesced because each field's element rows are contiguous);
+//   2. local differentiation: thread (element e, node quad q) forms
+//      u_r, u_s, u_t = D_{r,s,t} u for its four nodes and six fields, then the
+//      chain rule (eq. dg-reference-matrices) and the curls;
+//   3. flux gather (eq. num-flux): interior trace from shared memory,
+//      exterior trace from the neighbour's row (L2), PEC mirror on walls,
+//      upwind flux with impedance weights, times Fscale, into shared memory;
+//   4. flux lifting: LIFT (Np x 4Nfp) times the face fluxes, added to the
+//      curls and scaled by 1/eps, 1/mu;
+// then either stores the right-hand side or applies the low-storage RK
+// update res = a res + dt rhs, u_out = u + b res (operator assembly).
+// The transposed operators D^T[j][i], LIFT^T[m][i] are read as float4 along i
+// through the read-only cache; they are small and stay cache resident.
+#pragma once
+#include "common.cuh"
+#include "flux.cuh"
+
+namespace dgmx {
+
+template <int N>
+struct SimtCfg {
+  using D = Dims<N>;
+  static constexpr int EB = 240 / D::NQ;                 // elements per block
+  static constexpr int NT = (EB * D::NQ + 31) / 32 * 32; // threads per block
+  static constexpr size_t SMEM =
+      (size_t(6) * EB * D::NPP + size_t(6) * EB * D::NFF) * 4 + ((100 * D::NFP + 15) / 16) * 16;
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
+  using D = Dims<N>;
+  using Cfg = SimtCfg<N>;
+  constexpr int NP = D::NP, NFP = D::NFP, NPP = D::NPP, NQ = D::NQ, NFF = D::NFF;
+  constexpr int EB = Cfg::EB, NT = Cfg::NT;
+  extern __shared__ float4 smem4[];
+  float *s_u = reinterpret_cast<float *>(smem4);             // [6][EB][NPP]
+  float *s_fl = s_u + 6 * EB * NPP;                          // [6][EB][NFF]
+  uint8_t *s_fm = reinterpret_cast<uint8_t *>(s_fl + 6 * EB * NFF); // [NFF]
+  uint8_t *s_nb = s_fm + NFF;                                // [96][NFP]
+
+  const int tid = threadIdx.x;
+  const int64_t k0 = int64_t(blockIdx.x) * EB;
+  const int64_t KN = a.K * NPP;
+
+  for (int idx = tid; idx < 6 * EB * NQ; idx += NT) {
+    int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
+    int e = rem / NQ, q = rem - e * NQ;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k0 + e < a.K) v = ldg4(a.u + c * KN + (k0 + e) * NPP + 4 * q);
+    reinterpret_cast<float4 *>(s_u)[(c * EB + e) * NQ + q] = v;
+  }
+  for (int idx = tid; idx < NFF + kConnKinds * NFP; idx += NT)
+    s_fm[idx] = idx < NFF ? a.fmask[idx] : a.nbrtab[idx - NFF];
+  __syncthreads();
+
+  const int e = tid / NQ, q = tid - (tid / NQ) * NQ;
+  const bool owner = tid < EB * NQ;
+  const int64_t k = k0 + (owner ? e : 0);
+  const bool live = owner && k < a.K;
+  float vol[6][4];
+
+  // ---- local differentiation + chain rule + curl
+  if (owner) {
+    float acc[3][6][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) acc[d][c][n] = 0.f;
+    const float *su = s_u + e * NPP;
+#pragma unroll 2
+    for (int j = 0; j < NP; ++j) {
+      float4 dr = ldg4(a.DT + (0 * NP + j) * NPP + 4 * q);
+      float4 ds = ldg4(a.DT + (1 * NP + j) * NPP + 4 * q);
+      float4 dt = ldg4(a.DT + (2 * NP + j) * NPP + 4 * q);
+      const float dv[3][4] = {{dr.x, dr.y, dr.z, dr.w}, {ds.x, ds.y, ds.z, ds.w}, {dt.x, dt.y, dt.z, dt.w}};
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        float uj = su[c * EB * NPP + j];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int n = 0; n < 4; ++n) acc[d][c][n] = fmaf(dv[d][n], uj, acc[d][c][n]);
+      }
+    }
+    const float *g = a.geo + (live ? k : 0) * G_STRIDE;
+    float m[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m[i] = __ldg(g + i);
+    // m = {rx ry rz sx sy sz tx ty tz}: d/dx_l = m[l] d/dr + m[3+l] d/ds + m[6+l] d/dt
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      float dd[6][3];
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) dd[c][l] = m[l] * acc[0][c][n] + m[3 + l] * acc[1][c][n] + m[6 + l] * acc[2][c][n];
+      vol[0][n] = dd[5][1] - dd[4][2];    // (curl H)_x
+      vol[1][n] = dd[3][2] - dd[5][0];    // (curl H)_y
+      vol[2][n] = dd[4][0] - dd[3][1];    // (curl H)_z
+      vol[3][n] = -(dd[2][1] - dd[1][2]); // -(curl E)_x
+      vol[4][n] = -(dd[0][2] - dd[2][0]); // -(curl E)_y
+      vol[5][n] = -(dd[1][0] - dd[0][1]); // -(curl E)_z
+    }
+  }
+
+  // ---- flux gather
+  for (int it = tid; it < EB * NFF; it += NT) {
+    int ee = it / NFF, fm = it - ee * NFF;
+    int f = fm / NFP, mm = fm - f * NFP;
+    int64_t kk = k0 + ee;
+    float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (kk < a.K) {
+      int vm = s_fm[fm];
+      float qm[6], qp[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) qm[c] = s_u[(c * EB + ee) * NPP + vm];
+      int2 cn = __ldg(a.fconn + kk * 4 + f);
+      float4 nf = __ldg(a.fgeo + kk * 4 + f);
+      float Zm = __ldg(a.geo + kk * G_STRIDE + G_Z), Ym = __ldg(a.geo + kk * G_STRIDE + G_Y);
+      float Zp = Zm, Yp = Ym;
+      if (cn.y == kBoundaryConn) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          qp[c] = -qm[c];
+          qp[c + 3] = qm[c + 3];
+        }
+      } else {
+        int vn = s_nb[cn.y * NFP + mm];
+        const float *up = a.u + int64_t(cn.x) * NPP + vn;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) qp[c] = __ldg(up + c * KN);
+        Zp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Z);
+        Yp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Y);
+      }
+      maxwell_flux(nf, qm, qp, Zm, Zp, Ym, Yp, a.alpha, fl);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s_fl[(c * EB + ee) * NFF + fm] = fl[c];
+  }
+  __syncthreads();
+
+  if (!owner) return;
+  // ---- flux lifting
+  {
+    const float *sf = s_fl + e * NFF;
+#pragma unroll 4
+    for (int fm = 0; fm < NFF; ++fm) {
+      float4 L = ldg4(a.LT + fm * NPP + 4 * q);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        float gv = sf[c * EB * NFF + fm];
+        vol[c][0] = fmaf(L.x, gv, vol[c][0]);
+        vol[c][1] = fmaf(L.y, gv, vol[c][1]);
+        vol[c][2] = fmaf(L.z, gv, vol[c][2]);
+        vol[c][3] = fmaf(L.w, gv, vol[c][3]);
+      }
+    }
+  }
+  if (!live) return;
+  // ---- material scaling and output / operator assembly
+  const float ie = __ldg(a.geo + k * G_STRIDE + G_IEPS), im = __ldg(a.geo + k * G_STRIDE + G_IMU);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const float w = c < 3 ? ie : im;
+    float r4[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) r4[n] = (4 * q + n < NP) ? vol[c][n] * w : 0.f;
+    const int64_t off = c * KN + k * NPP + 4 * q;
+    if (MODE == MODE_RHS) {
+      *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+    } else {
+      float4 rs = *reinterpret_cast<const float4 *>(a.res + off);
+      float4 uo = reinterpret_cast<const float4 *>(s_u)[(c * EB + e) * NQ + q];
+      float rv[4] = {rs.x, rs.y, rs.z, rs.w}, uv[4] = {uo.x, uo.y, uo.z, uo.w};
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        bool pad = 4 * q + n >= NP;
+        rv[n] = pad ? 0.f : fmaf(a.rk_a, rv[n], a.dt * r4[n]);
+        uv[n] = pad ? 0.f : fmaf(a.rk_b, rv[n], uv[n]);
+      }
+      *reinterpret_cast<float4 *>(a.res + off) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+      *reinterpret_cast<float4 *>(a.u_out + off) = make_float4(uv[0], uv[1], uv[2], uv[3]);
+    }
+  }
+}
+
+template <int N>
+cudaError_t launch_simt_order(int mode, const StageArgs &a, cudaStream_t s) {
+  using Cfg = SimtCfg<N>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e1 = cudaFuncSetAttribute(k_stage_simt<N, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(Cfg::SMEM));
+    cudaError_t e2 = cudaFuncSetAttribute(k_stage_simt<N, MODE_LSERK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(Cfg::SMEM));
+    if (e1 != cudaSuccess) return e1;
+    if (e2 != cudaSuccess) return e2;
+    configured = true;
+  }
+  unsigned blocks = unsigned((a.K + Cfg::EB - 1) / Cfg::EB);
+  if (mode == MODE_RHS)
+    k_stage_simt<N, MODE_RHS><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
+  else
+    k_stage_simt<N, MODE_LSERK><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+} // namespace dgmx
