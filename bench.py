@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: nodal DG Maxwell right-hand-side throughput on GB300.
+
+Workload (default): the unit cube cut into 24^3 hexahedra x 6 = 82,944
+tetrahedra, interior vertices jittered by +-10% of h (seed 1), polynomial
+order N=5 (Np=56), eps = mu = 1, PEC walls, upwind flux, initial data the
+closed-form (1,1,1) cavity eigenmode, FP32 fields [6][K][Np_pad], LSERK4 with
+dt = 0.5 h / N^2. One benchmark step is one LSERK4 time step = five fused
+right-hand-side stages. The metric is GDOF/s per right-hand-side evaluation:
+5 * DOF * steps / time, DOF = 6 Np K.
+
+Arms:
+  default           the CUDA library through the C ABI (device-resident inputs,
+                    CUDA-event timing), plus an end-to-end number with the
+                    host<->device copies of every step inside the timed region.
+  --impl reference  the FP64 CPU oracle, timed on the host cores on a bounded
+                    sample of the same workload (5 right-hand-side evaluations
+                    on a fixed sample of elements per step).
+Multi-GPU (torchrun): independent replicas, one per GPU; value = all ranks'
+units / max-over-ranks time (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Maxwell DG RHS GDOF/s at N=5/7, TC split vs FP32 at equal error; adjoint cost"
+UNIT = "GDOF/s"
+STAGES = 5
+NUM_SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def flops_per_element(N: int) -> float:
+    """Algorithmic flops of one fused stage per element (see the design notes)."""
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    Nfp = (N + 1) * (N + 2) // 2
+    volume = 2 * 3 * 6 * Np * Np          # Dr, Ds, Dt on six fields
+    chain = Np * (6 * 2 * 3 * 2 + 6)      # two physical derivatives per field (3 FMA each) + curls
+    flux = 4 * Nfp * 60                   # jumps, cross products, weights per face node
+    lift = 2 * 6 * Np * 4 * Nfp           # LIFT on six fields
+    update = 6 * Np * (1 + 4)             # material scale + LSERK update
+    return float(volume + chain + flux + lift + update)
+
+
+def bytes_per_element(N: int, Npad: int) -> float:
+    """Algorithmic DRAM bytes of one fused LSERK stage per element: read u and
+    res, write res and u_out (FP32), plus the per-element geometry (64 B),
+    face geometry (64 B) and face connectivity (32 B)."""
+    return 4 * 6 * Npad * 4 + 64 + 64 + 32
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(device_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], None, set()
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for name, flag in zip(self.NAMES, p[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_workload(N: int, n: int):
+    import workloads as W
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    return VX, VY, VZ, EToV
+
+
+def cpu_oracle_rate(N: int, n: int, sample_elems: int, reps: int = 1):
+    """Oracle (FP64, single thread) right-hand side on a fixed element sample of
+    the same mesh: returns (GDOF/s per RHS, seconds, elements)."""
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    VX, VY, VZ, EToV = make_workload(N, n)
+    m = O.Mesh(N, VX, VY, VZ, EToV)
+    x, y, z = m.coords()
+    u = W.cavity_mode(x, y, z, 0.0)
+    elems = np.sort(np.unique((W.uniform(31, sample_elems) * m.K).astype(np.int64)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        m.rhs_subset(u, elems)
+    dt = time.perf_counter() - t0
+    dof = 6 * m.Np * elems.size * reps
+    return dof / dt / 1e9, dt, int(elems.size), m, u, elems
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    N, n = args.order, args.n
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    # size the per-step sample so that one step (5 RHS evaluations) takes about a second
+    _, t1, e1, m, u, _ = cpu_oracle_rate(N, n, 256)
+    per_elem = t1 / e1
+    sample = int(max(64, min(m.K, 1.0 / (STAGES * per_elem))))
+    import numpy as np
+    import workloads as W
+    elems = np.sort(np.unique((W.uniform(31, sample) * m.K).astype(np.int64)))
+    for _ in range(args.warmup):
+        for _ in range(STAGES):
+            m.rhs_subset(u, elems)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(STAGES):
+            m.rhs_subset(u, elems)
+    dt = time.perf_counter() - t0
+    dof = 6 * Np * elems.size
+    value = STAGES * dof * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, m.K, Np),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{STAGES} oracle RHS evaluations per step on {elems.size} of {m.K} elements"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, K, Np):
+    return {"workload": f"PEC cube cavity, {args.n}^3x6 jittered tets, N={args.order}, upwind, LSERK4",
+            "K": int(K), "N": args.order, "Np": Np, "dof": 6 * Np * int(K), "rhs_per_step": STAGES,
+            "precision": args.precision, "l2": "inputs larger than L2 (u, res, u_out: 3 x 6 K Np_pad x 4 B per stage)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1211_0582_gb300 as dg
+    import workloads as W
+
+    world, rank, local = dist_setup()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    N, n = args.order, args.n
+    VX, VY, VZ, EToV = make_workload(N, n)
+    K = EToV.shape[0]
+    s = dg.Solver(N, precision=args.precision, stream=stream).upload(VX, VY, VZ, EToV)
+    x, y, z = s.node_coords()
+    u0_host = W.cavity_mode(x, y, z, 0.0)
+    h = 1.0 / n
+    dt = 0.5 * h / N ** 2
+    Np, Npad = s.Np, s.Npad
+    dof = 6 * Np * K
+    u = s.to_device(u0_host, device)
+    res = s.zeros(device)
+
+    # ---- warm-up
+    s.step(u, res, dt, args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0.record(stream)
+    s.step(u, res, dt, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * STAGES * dof * args.steps / (ms * 1e-3) / 1e9
+    launches = STAGES * args.steps
+    launch_ms = ms / launches
+
+    # sanity: the run must stay finite and bounded (upwind: energy does not grow)
+    energy = s.energy(u)
+
+    # ---- end to end: host inputs -> device -> one step -> host result, every step
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    u_h = torch.empty((6, K, Npad), dtype=torch.float32).pin_memory()
+    r_h = torch.zeros((6, K, Npad), dtype=torch.float32).pin_memory()
+    u_h.copy_(u.cpu())
+    out_h = torch.empty_like(u_h).pin_memory()
+    ud, rd = torch.empty_like(u), torch.empty_like(res)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        ud.copy_(u_h, non_blocking=True)
+        rd.copy_(r_h, non_blocking=True)
+        s.step(ud, rd, dt, 1)
+        out_h.copy_(ud, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    field_bytes = 6 * K * Npad * 4
+    e2e_value = world * STAGES * dof * e2e_steps / (e2e_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the fused stage kernel)
+    peaks, peak_kind = measured_peaks()
+    if args.precision == "fp32":
+        peak_tf = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = flops_per_element(N) * K / (launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf, "traffic": args.traffic,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
+    else:
+        peak = peaks["hbm_gbs"]
+        achieved = bytes_per_element(N, Npad) * K / (launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": args.traffic, "peak_source": f"hbm_gbs ({peak_kind})"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "data": "synthetic", "config": config_dict(args, K, Np),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes,
+                "d2h_bytes_per_step": field_bytes, "steps": e2e_steps},
+        "gpu_launches": launches, "roofline": roof, "clocks": clk,
+        "kernel_ms_per_launch": launch_ms, "energy_after": energy,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, ne, *_ = cpu_oracle_rate(N, n, args.cpu_sample)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"1 oracle RHS on {ne} of {K} elements ({secs:.1f} s, FP64, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3", "fp16x3"], default="fp32")
+    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--n", type=int, default=24, help="hexahedra per cube edge")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-sample", type=int, default=50000, help="elements in the oracle CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the stage kernel (from a capture), if known")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -127,6 +127,12 @@ int dg_rhs(dg_ctx *ctx, const float *u, float *rhs, float alpha);
  * Errors: DG_ERR_ARG, DG_ERR_CUDA. */
 int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);
 
+/* Wait for all work enqueued on the context's stream and report device-side
+ * failures: returns DG_ERR_TIMEOUT (and clears the flag) if a tensor-core
+ * kernel gave up waiting for its matrix units after its iteration limit
+ * (about one second), DG_ERR_CUDA if the stream reports an error. */
+int dg_sync(dg_ctx *ctx);
+
 /* Discrete energy 1/2 sum_k J_k (eps_k E^T M E + mu_k H^T M H), reduced in
  * FP64 on the device; *E_out is a HOST double. Synchronises the stream.
  * Returns DG_ERR_NONFINITE if the energy is NaN or Inf. */

@@ -56,6 +56,7 @@ def lib():
             L.dg_rhs.argtypes = [vp, vp, vp, flt]
             L.dg_step.argtypes = [vp, vp, vp, dbl, i32, flt]
             L.dg_energy.argtypes = [vp, vp, C.POINTER(dbl)]
+            L.dg_sync.argtypes = [vp]
             _lib = L
     return _lib
 
@@ -154,6 +155,9 @@ class Solver:
     def step(self, u, res, dt: float, nsteps: int = 1, alpha: float = 1.0):
         self._check(lib().dg_step(self._h, _t_ptr(u), _t_ptr(res), float(dt), int(nsteps), float(alpha)))
         return u, res
+
+    def sync(self):
+        self._check(lib().dg_sync(self._h))
 
     def energy(self, u) -> float:
         E = C.c_double()

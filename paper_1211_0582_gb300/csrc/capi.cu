@@ -246,6 +246,7 @@ int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, 
     e = launch_geometry(g, s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_scratch, 0, field_bytes(ctx), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag + 1, 0, 15 * sizeof(int), s);
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -353,6 +354,19 @@ int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alph
     cudaError_t e = cudaMemcpyAsync(u, cur, field_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "dg_step");
   }
+  return DG_OK;
+}
+
+int dg_sync(dg_ctx *ctx) {
+  if (!ctx) return DG_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "dg_sync");
+  if (ctx->K <= 0) return DG_OK;
+  int flag = 0, zero = 0;
+  e = cudaMemcpy(&flag, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flag) e = cudaMemcpy(ctx->d_flag + 1, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "dg_sync");
+  if (flag) return set_err(ctx, DG_ERR_TIMEOUT, "a tensor-core kernel timed out waiting for its MMA completion barrier");
   return DG_OK;
 }
 

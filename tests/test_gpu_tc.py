@@ -1,0 +1,97 @@
+"""GPU parity of the tensor-core split-precision path against the FP64 oracle.
+
+Tolerances (relative discrete l2 against FP64), derived from the split
+arithmetic: a BF16 pair carries 16 significant bits (dropped terms ~3 * 2^-17
+per product), an FP16 pair 22 bits (~3 * 2^-23), both amplified by the
+cancellation in D u of smooth or random fields and then accumulated in FP32.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1211_0582_gb300 as dg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": 2e-4, "fp16x3": 1e-5}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def pair(N, n, precision, eps=True):
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    e = W.element_eps(K, seed=2) if eps else None
+    s = dg.Solver(N, precision=precision).upload(VX, VY, VZ, EToV, eps=e)
+    m = O.Mesh(N, VX, VY, VZ, EToV, eps=None if e is None else e.astype(np.float64))
+    return s, m
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("N,n", [(1, 3), (2, 3), (3, 3), (4, 3), (5, 4)])
+def test_tc_rhs_parity(precision, N, n):
+    s, m = pair(N, n, precision)
+    u = np.random.default_rng(11).standard_normal(m.shape)
+    for alpha in (1.0, 0.0):
+        ref = m.rhs(u, alpha)
+        got = s.from_device(s.rhs(s.to_device(u), alpha=alpha))
+        err = rel_l2(got, ref)
+        print(f"{precision} N={N} alpha={alpha}: rel l2 {err:.3e}")
+        assert err < TOL[precision]
+    s.sync()
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+def test_tc_smooth_field_and_scaling(precision):
+    # a smooth field (strong cancellation in D u) at tiny and large magnitudes:
+    # the FP16 row scaling must keep the relative error independent of scale.
+    s, m = pair(5, 3, precision)
+    x, y, z = m.coords()
+    u = W.cavity_mode(x, y, z, 0.0) + W.gaussian_pulse(x, y, z) * 0.01
+    ref = m.rhs(u)
+    for scale in (1.0, 1e-6, 1e5):
+        got = s.from_device(s.rhs(s.to_device(u * scale))) / scale
+        err = rel_l2(got, ref)
+        print(f"{precision} scale={scale:g}: rel l2 {err:.3e}")
+        assert err < 2 * TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+def test_tc_lserk_steps(precision):
+    N = 4
+    s, m = pair(N, 3, precision)
+    x, y, z = m.coords()
+    u0 = W.cavity_mode(x, y, z, 0.0)
+    dt = 0.5 / 3 / N ** 2
+    ref, _ = m.lserk(u0, dt, 3)
+    ud, rd = s.to_device(u0), s.zeros()
+    s.step(ud, rd, dt, 3)
+    s.sync()
+    assert rel_l2(s.from_device(ud), ref) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+def test_tc_full_size_sampled(precision):
+    # the 24^3 x 6 jittered mesh at N=5, the benchmark workload
+    N, n = 5, 24
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    s = dg.Solver(N, precision=precision).upload(VX, VY, VZ, EToV)
+    m = O.Mesh(N, VX, VY, VZ, EToV)
+    x, y, z = m.coords()
+    u = W.cavity_mode(x, y, z, 0.0) + 0.05 * np.random.default_rng(17).standard_normal(m.shape)
+    got = s.from_device(s.rhs(s.to_device(u)))
+    elems = np.unique((W.uniform(21, 300) * m.K).astype(np.int64))
+    err = rel_l2(got[:, elems], m.rhs_subset(u, elems))
+    print(f"{precision} full size sampled: rel l2 {err:.3e}")
+    assert err < TOL[precision]
+
+
+def test_tc_unsupported_order_reports_cleanly():
+    VX, VY, VZ, EToV = W.kuhn_cube(1)
+    s = dg.Solver(7, precision="fp16x3")
+    with pytest.raises(dg.DGError) as e:
+        s.upload(VX, VY, VZ, EToV)
+    assert e.value.code == -6
