@@ -322,7 +322,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16x3", "fp16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3", "fp16x3"], default="fp16x3")
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--n", type=int, default=24, help="hexahedra per cube edge")
     ap.add_argument("--e2e-steps", type=int, default=50)

@@ -37,7 +37,7 @@ namespace dgmx {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kTileElems = 20; // 4 TMEM lane quarters x 5 elements
 constexpr int kRows = 120;     // (element, field) rows actually used per tile
 constexpr int kMaxTcOrder = 5;
@@ -76,9 +76,6 @@ struct TcState {
   int sms = 0;
 };
 
-// Compact row (6 e + f) -> TMEM lane / operand row (32 * quarter + lane).
-__device__ __forceinline__ int op_row(int ridx) { return 32 * (ridx / 30) + ridx % 30; }
-
 template <bool BF16>
 __device__ __forceinline__ void split4(float4 v, uint2 &hi, uint2 &lo) {
   if constexpr (BF16) {
@@ -96,18 +93,72 @@ __device__ __forceinline__ void split4(float4 v, uint2 &hi, uint2 &lo) {
   }
 }
 
-// Power-of-two scale bringing the row maximum into [0.5, 1) (FP16 range guard).
+// Warm L2 with [p, p + bytes) (bytes a multiple of 16, p 16-byte aligned).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  if (bytes == 0) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Operand row (32 * quarter + lane) -> compact row (6 e + f), or -1 for the
+// two unused lanes of each quarter.
+__device__ __forceinline__ int compact_row(int r) {
+  const int l = r & 31;
+  return l < 30 ? (r >> 5) * 30 + l : -1;
+}
+
+// Split the FP32 staging rows [120][ld] (first `cols` columns) into the hi/lo
+// K-major operands, scaled per row. Work items are ordered so that each
+// half-warp writes one 128-byte core matrix (8 rows x 16 bytes): conflict-free
+// shared stores. Padding positions are never written (they stay zero).
+template <bool BF16>
+__device__ __forceinline__ void convert_rows(const float *src, int ld, int cols, int Kp, const float *scale,
+                                             uint8_t *dst_hi, uint8_t *dst_lo, int tid) {
+  const int kgroups = Kp / 8;
+  const int units = 128 * kgroups * 2;
+  for (int u = tid; u < units; u += kThreads) {
+    const int rr = u & 7, qh = (u >> 3) & 1;
+    const int rest = u >> 4;
+    const int kg = rest % kgroups, g = rest / kgroups;
+    const int r = 8 * g + rr, k = 8 * kg + 4 * qh;
+    const int cr = compact_row(r);
+    if (cr < 0 || k >= cols) continue;
+    float4 v = *reinterpret_cast<const float4 *>(src + cr * ld + k);
+    if constexpr (!BF16) {
+      const float sc = scale[cr];
+      v.x *= sc, v.y *= sc, v.z *= sc, v.w *= sc;
+    }
+    uint2 hi, lo;
+    split4<BF16>(v, hi, lo);
+    const uint32_t off = umma::kmajor_offset(uint32_t(r), uint32_t(k), uint32_t(Kp));
+    *reinterpret_cast<uint2 *>(dst_hi + off) = hi;
+    *reinterpret_cast<uint2 *>(dst_lo + off) = lo;
+  }
+}
+
+// Power-of-two scale bringing a row maximum mx (>= 0) into [0.5, 1) and its
+// inverse, from the exponent field of mx (FP16 range guard). Zero, subnormal
+// or non-finite maxima give scale 1.
 __device__ __forceinline__ void row_scale(float mx, float &scale, float &inv) {
-  if (!(mx > 0.f) || !isfinite(mx)) {
+  const uint32_t ex = (__float_as_uint(mx) >> 23) & 0xFFu;
+  if (ex == 0u || ex >= 253u) {
     scale = 1.f;
     inv = 1.f;
     return;
   }
-  int e;
-  frexpf(mx, &e);
-  e = max(-120, min(120, e));
-  scale = ldexpf(1.f, -e);
-  inv = ldexpf(1.f, e);
+  scale = __uint_as_float((253u - ex) << 23);
+  inv = __uint_as_float((ex + 1u) << 23);
+}
+
+// Maximum of |row| over `len` FP32 values, 4 threads per row (row = tid / 4
+// for tid < 4 * kRows), combined with shuffles inside the 4-lane group.
+__device__ __forceinline__ float row_absmax4(const float *rows, int ld, int len, int tid) {
+  const int r = tid >> 2, part = tid & 3;
+  float mx = 0.f;
+  if (r < kRows)
+    for (int j = part; j < len; j += 4) mx = fmaxf(mx, fabsf(rows[r * ld + j]));
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  return mx;
 }
 
 // Three split products per K step: hi*hi, hi*lo, lo*hi, FP32 accumulation.
@@ -140,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *s_fl = reinterpret_cast<float *>(smem + T::OFF_FL);
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
-  float *s_sc1 = reinterpret_cast<float *>(smem + T::OFF_SC); // [128] scale, then inverse at +128
+  float *s_sc1 = reinterpret_cast<float *>(smem + T::OFF_SC); // [128] scale, inverse at +128
   float *s_sc2 = s_sc1 + 256;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 8);
@@ -148,6 +199,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t KN = a.K * NPP;
   const uint32_t sbase = umma::smem_u32(smem);
+
+  // warm L2 with everything a tile streams from HBM (fields, residual, geometry)
+  auto prefetch_tile = [&](int t) {
+    if (t >= ntiles) return;
+    const int64_t kb = int64_t(t) * kTileElems;
+    const int64_t ne = a.K - kb < kTileElems ? a.K - kb : kTileElems;
+    const uint32_t rowbytes = uint32_t(ne * NPP * 4);
+    for (int f = 0; f < 6; ++f) {
+      prefetch_l2(a.u + f * KN + kb * NPP, rowbytes);
+      if (MODE == MODE_LSERK) prefetch_l2(a.res + f * KN + kb * NPP, rowbytes);
+    }
+    prefetch_l2(a.fconn + kb * 4, uint32_t(ne * 4 * sizeof(int2)));
+    prefetch_l2(a.fgeo + kb * 4, uint32_t(ne * 4 * sizeof(float4)));
+    prefetch_l2(a.geo + kb * G_STRIDE, uint32_t(ne * G_STRIDE * 4));
+  };
 
   // ---- one-time setup: zero the A operands (padding rows/columns stay zero),
   // load the resident operators and the face tables, allocate TMEM.
@@ -161,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     umma::mbar_init(bar, 1);
     umma::fence_mbar_init();
+    prefetch_tile(blockIdx.x);
   }
   if (warp == 0) umma::tmem_alloc(tslot, T::TCOLS);
   umma::fence_proxy_async();
@@ -169,8 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
 
-  // epilogue constants of this thread: TMEM quarter, node half, element/field
-  const int quarter = warp & 3, half = warp >> 2;
+  // epilogue roles: TMEM lane quarter (warp % 4) and node-chunk part (warp / 4)
+  const int quarter = warp & 3, part = warp >> 2;
   const bool lane_used = lane < 30;
   const int ep = lane_used ? lane / 6 : 4;
   const int fld = lane_used ? lane % 6 : 5;
@@ -182,51 +249,58 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int e_loc = quarter * 5 + ep;
   const int ridx = e_loc * 6 + fld;
   const uint32_t lane_taddr = tmem + (uint32_t(quarter * 32) << 16);
+  constexpr int NCH = (NP + 7) / 8; // 8-node chunks per row
+  constexpr int CPP = (NCH + 3) / 4; // chunks per part
+  const int ch0 = part * CPP;
+  const int ch1 = (part + 1) * CPP < NCH ? (part + 1) * CPP : NCH;
 
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t k0 = int64_t(tile) * kTileElems;
+    if (tid == 0) prefetch_tile(tile + gridDim.x);
 
-    // ---- 1. stage the tile's fields in shared memory (FP32, pads zeroed)
-    for (int idx = tid; idx < 6 * kTileElems * NQ; idx += kThreads) {
-      int f = idx / (kTileElems * NQ), rem = idx - f * (kTileElems * NQ);
-      int e = rem / NQ, q = rem - e * NQ;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k0 + e < a.K) {
-        v = ldg4(a.u + f * KN + (k0 + e) * NPP + 4 * q);
-        if (4 * q + 3 >= NP) {
-          if (4 * q + 0 >= NP) v.x = 0.f;
-          if (4 * q + 1 >= NP) v.y = 0.f;
-          if (4 * q + 2 >= NP) v.z = 0.f;
-          if (4 * q + 3 >= NP) v.w = 0.f;
+    // ---- 1. stage the tile's fields in shared memory (FP32, pads zeroed);
+    // all loads of a thread are issued before any store
+    {
+      constexpr int TOT = 6 * kTileElems * NQ;
+      constexpr int IT = (TOT + kThreads - 1) / kThreads;
+      float4 v[IT];
+#pragma unroll
+      for (int s = 0; s < IT; ++s) {
+        const int idx = tid + s * kThreads;
+        v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < TOT) {
+          const int f = idx / (kTileElems * NQ), rem = idx - f * (kTileElems * NQ);
+          const int e = rem / NQ, q = rem - e * NQ;
+          if (k0 + e < a.K) v[s] = ldg4(a.u + f * KN + (k0 + e) * NPP + 4 * q);
         }
       }
-      reinterpret_cast<float4 *>(s_u)[(e * 6 + f) * NQ + q] = v;
+#pragma unroll
+      for (int s = 0; s < IT; ++s) {
+        const int idx = tid + s * kThreads;
+        if (idx < TOT) {
+          const int f = idx / (kTileElems * NQ), rem = idx - f * (kTileElems * NQ);
+          const int e = rem / NQ, q = rem - e * NQ;
+          float4 w = v[s];
+          if (4 * q + 3 >= NP) {
+            if (4 * q + 0 >= NP) w.x = 0.f;
+            if (4 * q + 1 >= NP) w.y = 0.f;
+            if (4 * q + 2 >= NP) w.z = 0.f;
+            if (4 * q + 3 >= NP) w.w = 0.f;
+          }
+          reinterpret_cast<float4 *>(s_u)[(e * 6 + f) * NQ + q] = w;
+        }
+      }
     }
     __syncthreads();
 
     // ---- 2. split into the A1 operand (hi/lo), row-scaled for FP16
     if constexpr (!BF16) {
-      if (tid < kRows) {
-        float mx = 0.f;
-        for (int j = 0; j < NP; ++j) mx = fmaxf(mx, fabsf(s_u[tid * NPP + j]));
-        row_scale(mx, s_sc1[tid], s_sc1[128 + tid]);
-      }
+      const float mx = row_absmax4(s_u, NPP, NP, tid);
+      if ((tid & 3) == 0 && (tid >> 2) < kRows) row_scale(mx, s_sc1[tid >> 2], s_sc1[128 + (tid >> 2)]);
       __syncthreads();
     }
-    for (int idx = tid; idx < kRows * NQ; idx += kThreads) {
-      int r = idx / NQ, q = idx - r * NQ;
-      float4 v = reinterpret_cast<const float4 *>(s_u)[r * NQ + q];
-      if constexpr (!BF16) {
-        float sc = s_sc1[r];
-        v.x *= sc, v.y *= sc, v.z *= sc, v.w *= sc;
-      }
-      uint2 hi, lo;
-      split4<BF16>(v, hi, lo);
-      uint32_t off = umma::kmajor_offset(uint32_t(op_row(r)), uint32_t(4 * q), T::K1);
-      *reinterpret_cast<uint2 *>(smem + T::OFF_A1H + off) = hi;
-      *reinterpret_cast<uint2 *>(smem + T::OFF_A1L + off) = lo;
-    }
+    convert_rows<BF16>(s_u, NPP, NPP, T::K1, s_sc1, smem + T::OFF_A1H, smem + T::OFF_A1L, tid);
     umma::fence_proxy_async();
     __syncthreads();
 
@@ -238,64 +312,80 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     // ---- 4. flux gather (overlaps GEMM1): interior trace from shared memory,
-    // exterior trace from the neighbour's row, PEC mirror on walls
-    for (int it = tid; it < kTileElems * NFF; it += kThreads) {
-      int e = it / NFF, fm = it - e * NFF;
-      int f = fm / NFP, mm = fm - f * NFP;
-      int64_t k = k0 + e;
-      float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (k < a.K) {
-        int vm = s_fm[fm];
-        float qm[6], qp[6];
+    // exterior trace from the neighbour's row, PEC mirror on walls. Loads of
+    // all items of a thread are issued before the arithmetic.
+    {
+      constexpr int TOT = kTileElems * NFF;
+      constexpr int IT = (TOT + kThreads - 1) / kThreads;
+      int2 cn[IT];
+      float4 nf[IT];
+      float zm[IT], ym[IT];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) qm[c] = s_u[(e * 6 + c) * NPP + vm];
-        int2 cn = __ldg(a.fconn + k * 4 + f);
-        float4 nf = __ldg(a.fgeo + k * 4 + f);
-        float Zm = __ldg(a.geo + k * G_STRIDE + G_Z), Ym = __ldg(a.geo + k * G_STRIDE + G_Y);
-        float Zp = Zm, Yp = Ym;
-        if (cn.y == kBoundaryConn) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            qp[c] = -qm[c];
-            qp[c + 3] = qm[c + 3];
-          }
-        } else {
-          int vn = s_nb[cn.y * NFP + mm];
-          const float *up = a.u + int64_t(cn.x) * NPP + vn;
-#pragma unroll
-          for (int c = 0; c < 6; ++c) qp[c] = __ldg(up + c * KN);
-          Zp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Z);
-          Yp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Y);
+      for (int s = 0; s < IT; ++s) {
+        const int it = tid + s * kThreads;
+        const int e = it / NFF, fm = it - e * NFF, f = fm / NFP;
+        const int64_t k = k0 + e;
+        cn[s] = make_int2(0, kBoundaryConn);
+        nf[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        zm[s] = 1.f, ym[s] = 1.f;
+        if (it < TOT && k < a.K) {
+          cn[s] = __ldg(a.fconn + k * 4 + f);
+          nf[s] = __ldg(a.fgeo + k * 4 + f);
+          zm[s] = __ldg(a.geo + k * G_STRIDE + G_Z);
+          ym[s] = __ldg(a.geo + k * G_STRIDE + G_Y);
         }
-        maxwell_flux(nf, qm, qp, Zm, Zp, Ym, Yp, a.alpha, fl);
+      }
+      float qp[IT][6], zp[IT], yp[IT];
+#pragma unroll
+      for (int s = 0; s < IT; ++s) {
+        const int it = tid + s * kThreads;
+        const int e = it / NFF, fm = it - e * NFF, f = fm / NFP, mm = fm - f * NFP;
+        zp[s] = zm[s], yp[s] = ym[s];
+        if (it < TOT && k0 + e < a.K && cn[s].y != kBoundaryConn) {
+          const int vn = s_nb[cn[s].y * NFP + mm];
+          const float *up = a.u + int64_t(cn[s].x) * NPP + vn;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qp[s][c] = __ldg(up + c * KN);
+          zp[s] = __ldg(a.geo + int64_t(cn[s].x) * G_STRIDE + G_Z);
+          yp[s] = __ldg(a.geo + int64_t(cn[s].x) * G_STRIDE + G_Y);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qp[s][c] = 0.f;
+        }
       }
 #pragma unroll
-      for (int c = 0; c < 6; ++c) s_fl[(e * 6 + c) * NFF + fm] = fl[c];
+      for (int s = 0; s < IT; ++s) {
+        const int it = tid + s * kThreads;
+        if (it >= TOT) continue;
+        const int e = it / NFF, fm = it - e * NFF;
+        float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (k0 + e < a.K) {
+          const int vm = s_fm[fm];
+          float qm[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qm[c] = s_u[(e * 6 + c) * NPP + vm];
+          if (cn[s].y == kBoundaryConn) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              qp[s][c] = -qm[c];
+              qp[s][c + 3] = qm[c + 3];
+            }
+          }
+          maxwell_flux(nf[s], qm, qp[s], zm[s], zp[s], ym[s], yp[s], a.alpha, fl);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s_fl[(e * 6 + c) * NFF + fm] = fl[c];
+      }
     }
     __syncthreads();
 
     // ---- 5. split the face fluxes into the A2 operand
     if constexpr (!BF16) {
-      if (tid < kRows) {
-        float mx = 0.f;
-        for (int m = 0; m < NFF; ++m) mx = fmaxf(mx, fabsf(s_fl[tid * NFF + m]));
-        row_scale(mx, s_sc2[tid], s_sc2[128 + tid]);
-      }
+      const float mx = row_absmax4(s_fl, NFF, NFF, tid);
+      if ((tid & 3) == 0 && (tid >> 2) < kRows) row_scale(mx, s_sc2[tid >> 2], s_sc2[128 + (tid >> 2)]);
       __syncthreads();
     }
-    for (int idx = tid; idx < kRows * (NFF / 4); idx += kThreads) {
-      int r = idx / (NFF / 4), q = idx - r * (NFF / 4);
-      float4 v = reinterpret_cast<const float4 *>(s_fl)[r * (NFF / 4) + q];
-      if constexpr (!BF16) {
-        float sc = s_sc2[r];
-        v.x *= sc, v.y *= sc, v.z *= sc, v.w *= sc;
-      }
-      uint2 hi, lo;
-      split4<BF16>(v, hi, lo);
-      uint32_t off = umma::kmajor_offset(uint32_t(op_row(r)), uint32_t(4 * q), T::K2);
-      *reinterpret_cast<uint2 *>(smem + T::OFF_A2H + off) = hi;
-      *reinterpret_cast<uint2 *>(smem + T::OFF_A2L + off) = lo;
-    }
+    convert_rows<BF16>(s_fl, NFF, NFF, T::K2, s_sc2, smem + T::OFF_A2H, smem + T::OFF_A2L, tid);
     umma::fence_proxy_async();
     __syncthreads();
 
@@ -306,6 +396,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                              sbase + T::OFF_B2L, T::K2, T::N2);
       umma::commit(bar);
     }
+    // residual of this thread's chunks, loaded while the products run
+    const int64_t k = k0 + e_loc;
+    const bool live = lane_used && k < a.K;
+    float4 rres[2 * CPP];
+#pragma unroll
+    for (int c = 0; c < CPP; ++c)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        rres[2 * c + h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int i = (ch0 + c) * 8 + 4 * h;
+        if (MODE == MODE_LSERK && live && ch0 + c < ch1 && i < NPP)
+          rres[2 * c + h] = *reinterpret_cast<const float4 *>(a.res + fld * KN + k * NPP + i);
+      }
+    float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f;
+    if (live) {
+      const float *g = a.geo + k * G_STRIDE;
+      // d/dx_l = (dr/dx_l) d/dr + (ds/dx_l) d/ds + (dt/dx_l) d/dt
+      g1r = __ldg(g + G_RX + dl1), g1s = __ldg(g + G_SX + dl1), g1t = __ldg(g + G_TX + dl1);
+      g2r = __ldg(g + G_RX + dl2), g2s = __ldg(g + G_SX + dl2), g2t = __ldg(g + G_TX + dl2);
+      w = __ldg(g + (isE ? G_IEPS : G_IMU));
+    }
+    const float inv1 = BF16 ? 1.f : s_sc1[128 + (lane_used ? ridx : 0)];
+    const float inv2 = BF16 ? 1.f : s_sc2[128 + (lane_used ? ridx : 0)];
     const bool ok = umma::mbar_wait_bounded(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -315,66 +428,52 @@ __global__ void __launch_bounds__(kThreads, 1)
     umma::fence_after_sync();
 
     // ---- 7. epilogue: chain rule, curls, lifting, material scale, update
-    {
-      const int64_t k = k0 + e_loc;
-      const bool live = lane_used && k < a.K;
-      float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f;
-      if (live) {
-        const float *g = a.geo + k * G_STRIDE;
-        // d/dx_l = (dr/dx_l) d/dr + (ds/dx_l) d/ds + (dt/dx_l) d/dt
-        g1r = __ldg(g + G_RX + dl1), g1s = __ldg(g + G_SX + dl1), g1t = __ldg(g + G_TX + dl1);
-        g2r = __ldg(g + G_RX + dl2), g2s = __ldg(g + G_SX + dl2), g2t = __ldg(g + G_TX + dl2);
-        w = __ldg(g + (isE ? G_IEPS : G_IMU));
+#pragma unroll
+    for (int c = 0; c < CPP; ++c) {
+      const int ch = ch0 + c;
+      if (ch >= ch1) break;
+      const int i0 = ch * 8;
+      float ur[8], us[8], ut[8], lf[8];
+      umma::tmem_ld8(lane_taddr + uint32_t(i0), ur);
+      umma::tmem_ld8(lane_taddr + uint32_t(T::NB + i0), us);
+      umma::tmem_ld8(lane_taddr + uint32_t(2 * T::NB + i0), ut);
+      umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
+      umma::tmem_wait_ld();
+      float rv[8];
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const float dr = ur[n] * inv1, ds = us[n] * inv1, dt = ut[n] * inv1;
+        const float p1 = g1r * dr + g1s * ds + g1t * dt;
+        const float p2 = g2r * dr + g2s * ds + g2t * dt;
+        const float v1 = __shfl_sync(0xffffffffu, p1, src1);
+        const float v2 = __shfl_sync(0xffffffffu, p2, src2);
+        const float vol = isE ? (v1 - v2) : (v2 - v1);
+        rv[n] = (vol + lf[n] * inv2) * w;
       }
-      const float inv1 = BF16 ? 1.f : s_sc1[128 + (lane_used ? ridx : 0)];
-      const float inv2 = BF16 ? 1.f : s_sc2[128 + (lane_used ? ridx : 0)];
-      constexpr int NCH = (NP + 7) / 8;
-      constexpr int CPH = (NCH + 1) / 2;
-      const int ch_end = (half + 1) * CPH < NCH ? (half + 1) * CPH : NCH;
-      for (int ch = half * CPH; ch < ch_end; ++ch) {
-        const int i0 = ch * 8;
-        float ur[8], us[8], ut[8], lf[8];
-        umma::tmem_ld8(lane_taddr + uint32_t(i0), ur);
-        umma::tmem_ld8(lane_taddr + uint32_t(T::NB + i0), us);
-        umma::tmem_ld8(lane_taddr + uint32_t(2 * T::NB + i0), ut);
-        umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
-        umma::tmem_wait_ld();
-        float rv[8];
+      if (live) {
 #pragma unroll
-        for (int n = 0; n < 8; ++n) {
-          const float dr = ur[n] * inv1, ds = us[n] * inv1, dt = ut[n] * inv1;
-          const float p1 = g1r * dr + g1s * ds + g1t * dt;
-          const float p2 = g2r * dr + g2s * ds + g2t * dt;
-          const float v1 = __shfl_sync(0xffffffffu, p1, src1);
-          const float v2 = __shfl_sync(0xffffffffu, p2, src2);
-          const float vol = isE ? (v1 - v2) : (v2 - v1);
-          rv[n] = (vol + lf[n] * inv2) * w;
-        }
-        if (live) {
+        for (int h = 0; h < 2; ++h) {
+          const int i = i0 + 4 * h;
+          if (i < NPP) {
+            float r4[4];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int i = i0 + 4 * h;
-            if (i < NPP) {
-              float r4[4];
+            for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? rv[4 * h + q] : 0.f;
+            const int64_t off = fld * KN + k * NPP + i;
+            if (MODE == MODE_RHS) {
+              *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+            } else {
+              const float4 rs = rres[2 * c + h];
+              const float4 uo = *reinterpret_cast<const float4 *>(s_u + ridx * NPP + i);
+              const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
+              float nr[4], nu[4];
 #pragma unroll
-              for (int c = 0; c < 4; ++c) r4[c] = (i + c < NP) ? rv[4 * h + c] : 0.f;
-              const int64_t off = fld * KN + k * NPP + i;
-              if (MODE == MODE_RHS) {
-                *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
-              } else {
-                const float4 rs = *reinterpret_cast<const float4 *>(a.res + off);
-                const float4 uo = *reinterpret_cast<const float4 *>(s_u + ridx * NPP + i);
-                const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
-                float nr[4], nu[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                  const bool pad = i + c >= NP;
-                  nr[c] = pad ? 0.f : fmaf(a.rk_a, rsv[c], a.dt * r4[c]);
-                  nu[c] = pad ? 0.f : fmaf(a.rk_b, nr[c], uov[c]);
-                }
-                *reinterpret_cast<float4 *>(a.res + off) = make_float4(nr[0], nr[1], nr[2], nr[3]);
-                *reinterpret_cast<float4 *>(a.u_out + off) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+              for (int q = 0; q < 4; ++q) {
+                const bool pad = i + q >= NP;
+                nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[q], a.dt * r4[q]);
+                nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
               }
+              *reinterpret_cast<float4 *>(a.res + off) = make_float4(nr[0], nr[1], nr[2], nr[3]);
+              *reinterpret_cast<float4 *>(a.u_out + off) = make_float4(nu[0], nu[1], nu[2], nu[3]);
             }
           }
         }
