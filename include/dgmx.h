@@ -127,6 +127,23 @@ int dg_rhs(dg_ctx *ctx, const float *u, float *rhs, float alpha);
  * Errors: DG_ERR_ARG, DG_ERR_CUDA. */
 int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);
 
+/* Same as dg_step, but allocates no device memory in any form: the stage
+ * ping-pong buffer is a fixed array inside the library's device image instead
+ * of the scratch that dg_mesh_upload allocates. For callers that cannot let
+ * the library allocate: applications whose device memory is owned up front by
+ * their own allocator or arena, and time loops that must not risk a cudaMalloc
+ * stall or failure. (The paper has no counterpart; this is a deployment
+ * variant of the LSERK4 driver.)
+ * Limit: 6 * K * Np_pad <= 4,194,304 floats (16 MiB, e.g. N=5 with K <= 12,483);
+ * larger meshes get DG_ERR_ARG. Every GPU that loads the library holds the
+ * 16 MiB array until the process exits. The first call on a device looks up
+ * the array's device address (with that device current); make that first call
+ * before any stream capture. All calls share the array and it keeps the last
+ * call's contents (nothing in it needs to start at zero); calls whose work
+ * overlaps on the GPU race on it. u, res, dt, nsteps, alpha and the errors are
+ * those of dg_step. */
+int dg_step_noalloc(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);
+
 /* Wait for all work enqueued on the context's stream and report device-side
  * failures: returns DG_ERR_TIMEOUT (and clears the flag) if a tensor-core
  * kernel gave up waiting for its matrix units after its iteration limit

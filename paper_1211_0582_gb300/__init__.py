@@ -57,6 +57,7 @@ def lib():
             L.dg_step.argtypes = [vp, vp, vp, dbl, i32, flt]
             L.dg_energy.argtypes = [vp, vp, C.POINTER(dbl)]
             L.dg_sync.argtypes = [vp]
+            L.dg_step_noalloc.argtypes = [vp, vp, vp, dbl, i32, flt]
             _lib = L
     return _lib
 
