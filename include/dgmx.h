@@ -150,6 +150,38 @@ int dg_step_noalloc(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, fl
  * (about one second), DG_ERR_CUDA if the stream reports an error. */
 int dg_sync(dg_ctx *ctx);
 
+/* Transpose of the right-hand-side operator in the Euclidean inner product,
+ * w = A(eps)^T v (DEVICE field vectors, no aliasing), in FP32 on the CUDA
+ * cores: face data Fscale * LIFT^T (W v) per element, then the transposed
+ * curl with D^T and the transposed flux Jacobians gathered from the element's
+ * own and its neighbours' face data. Synchronises the stream. */
+int dg_rhs_transpose(dg_ctx *ctx, const float *v, float *w, float alpha);
+
+/* Forward LSERK4 run from u0 (DEVICE, not modified) for nsteps steps with
+ * permittivity eps (DEVICE, K values; NULL keeps the current one, otherwise it
+ * replaces it as dg_set_eps does), recording E at R receiver nodes after every
+ * step: out (DEVICE FP32) is [nsteps][3][R]; recv (DEVICE int64, R entries) holds
+ * node indices k*Np + i in [0, K*Np). FP32 CUDA-core kernels. Synchronises. */
+int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, float alpha,
+                       const int64_t *recv, int64_t R, float *out);
+
+/* Receiver misfit J = sum_{n=1..nsteps} sum_r |E(recv_r, t_n) - Eref[n-1][.][r]|^2
+ * of the run of dg_receiver_traces, and its exact discrete gradient by the
+ * hand-written adjoint: the transposed LSERK4 recursion swept backwards stage
+ * by stage (lambda_r += b_s lambda_u; lambda_u += dt A^T lambda_r;
+ * dJ/deps += dt <lambda_r, dA/deps u_s>; lambda_r *= a_s), with the forward
+ * state restored from checkpoints saved every ckpt_every steps (one segment of
+ * stage states and stage right-hand sides is recomputed and held at a time).
+ * Inputs (DEVICE): u0 [6][K][Np_pad], eps (K, or NULL = current), recv (R),
+ * Eref [nsteps][3][R] FP32. Outputs: *J (HOST double), dJ_deps (DEVICE, K
+ * doubles, reduced in FP64; may be NULL), dJ_du0 (DEVICE field vector; may be
+ * NULL). FP32 CUDA-core kernels regardless of the context's precision.
+ * Device memory: about (nsteps/ckpt_every + 10 ckpt_every + 8) field vectors.
+ * Synchronises. Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE. */
+int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, int ckpt_every,
+                    float alpha, const int64_t *recv, int64_t R, const float *Eref, double *J, double *dJ_deps,
+                    float *dJ_du0);
+
 /* Discrete energy 1/2 sum_k J_k (eps_k E^T M E + mu_k H^T M H), reduced in
  * FP64 on the device; *E_out is a HOST double. Synchronises the stream.
  * Returns DG_ERR_NONFINITE if the energy is NaN or Inf. */

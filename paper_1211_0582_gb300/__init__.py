@@ -58,6 +58,9 @@ def lib():
             L.dg_energy.argtypes = [vp, vp, C.POINTER(dbl)]
             L.dg_sync.argtypes = [vp]
             L.dg_step_noalloc.argtypes = [vp, vp, vp, dbl, i32, flt]
+            L.dg_rhs_transpose.argtypes = [vp, vp, vp, flt]
+            L.dg_receiver_traces.argtypes = [vp, vp, vp, dbl, i32, flt, vp, i64, vp]
+            L.dg_adjoint_step.argtypes = [vp, vp, vp, dbl, i32, i32, flt, vp, i64, vp, C.POINTER(dbl), vp, vp]
             _lib = L
     return _lib
 
@@ -157,6 +160,30 @@ class Solver:
         self._check(lib().dg_step(self._h, _t_ptr(u), _t_ptr(res), float(dt), int(nsteps), float(alpha)))
         return u, res
 
+    def rhs_transpose(self, v, out=None, alpha: float = 1.0):
+        out = self.zeros(v.device) if out is None else out
+        self._check(lib().dg_rhs_transpose(self._h, _t_ptr(v), _t_ptr(out), float(alpha)))
+        return out
+
+    def receiver_traces(self, u0, recv, dt: float, nsteps: int, eps=None, alpha: float = 1.0):
+        import torch
+        out = torch.empty((nsteps, 3, recv.numel()), dtype=torch.float32, device=u0.device)
+        self._check(lib().dg_receiver_traces(self._h, _t_ptr(u0), None if eps is None else _t_ptr(eps),
+                                             float(dt), int(nsteps), float(alpha), _t_ptr(recv), recv.numel(),
+                                             _t_ptr(out)))
+        return out
+
+    def adjoint(self, u0, recv, Eref, dt: float, nsteps: int, ckpt_every: int = 20, eps=None, alpha: float = 1.0):
+        """Misfit J (float) and its gradients (dJ/deps FP64 [K], dJ/du0 [6][K][Np_pad])."""
+        import torch
+        J = C.c_double()
+        g_eps = torch.empty(self.K, dtype=torch.float64, device=u0.device)
+        g_u0 = torch.empty_like(u0)
+        self._check(lib().dg_adjoint_step(self._h, _t_ptr(u0), None if eps is None else _t_ptr(eps), float(dt),
+                                          int(nsteps), int(ckpt_every), float(alpha), _t_ptr(recv), recv.numel(),
+                                          _t_ptr(Eref), C.byref(J), _t_ptr(g_eps), _t_ptr(g_u0)))
+        return J.value, g_eps, g_u0
+
     def sync(self):
         self._check(lib().dg_sync(self._h))
 
@@ -164,3 +191,35 @@ class Solver:
         E = C.c_double()
         self._check(lib().dg_energy(self._h, _t_ptr(u), C.byref(E)))
         return E.value
+
+
+class ReceiverMisfit:
+    """torch.autograd.Function: J(u0, eps) = sum over steps and receivers of
+    |E - E_ref|^2 for an LSERK4 run. The forward pass calls dg_adjoint_step,
+    which returns the misfit together with its exact discrete gradients (the
+    library's hand-written adjoint); backward scales the saved gradients by the
+    incoming gradient of J."""
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _Misfit(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, u0, eps, solver, recv, Eref, dt, nsteps, ckpt_every, alpha):
+                J, g_eps, g_u0 = solver.adjoint(u0.contiguous(), recv, Eref, dt, nsteps, ckpt_every,
+                                                eps=eps.contiguous(), alpha=alpha)
+                ctx.save_for_backward(g_u0, g_eps)
+                return torch.tensor(J, dtype=torch.float64, device=u0.device)
+
+            @staticmethod
+            def backward(ctx, gJ):
+                g_u0, g_eps = ctx.saved_tensors
+                return (gJ.to(g_u0.dtype) * g_u0, (gJ * g_eps).to(torch.float32),
+                        None, None, None, None, None, None, None)
+
+        return _Misfit
+
+    @classmethod
+    def apply(cls, u0, eps, solver, recv, Eref, dt, nsteps, ckpt_every=20, alpha=1.0):
+        return cls._fn().apply(u0, eps, solver, recv, Eref, dt, nsteps, ckpt_every, alpha)

@@ -1,0 +1,710 @@
+// Hand-written discrete adjoint of the LSERK4-stepped DG operator (FP32 CUDA
+// cores, FP64 gradient reductions).
+//
+// The forward map is u_{n+1} = Step(u_n), each step five stages
+// r_s = a_s r_{s-1} + dt A u_{s-1}, u_s = u_{s-1} + b_s r_s, with A = A(eps) the
+// semi-discrete operator of eq. (semidiscrete-dg). Its exact transpose is
+// swept backwards, stage by stage:
+//     lr <- lr + b_s lu;   lu <- lu + dt A^T lr;   g_eps += dt <lr, dA/deps u_s>;   lr <- a_s lr
+// and the receiver misfit J = sum_n |P u_n - E_ref,n|^2 adds 2 P^T (P u_n - E_ref,n)
+// to lu at the end of each step n.
+//
+// A^T in gather form (no atomics on global memory): with W = diag(1/eps, 1/mu),
+//   1. face data g = Fscale * LIFT^T (W lr), element-local (k_adj_lift);
+//   2. per element: the transposed curl with D^T and the chain rule, plus the
+//      transposed flux Jacobians applied to the element's own g (interior
+//      side) and to the neighbour's g at the matching face node (exterior
+//      side), with the PEC mirror folded in on walls (k_adj_vol).
+// eps enters A through 1/eps on the E rows and through the impedance weights
+// Z = sqrt(mu/eps), Y = 1/Z of every face flux in which the element takes
+// part (as interior or exterior side); k_adj_vol gathers all of these for its
+// own element, so each element's gradient is written by one block only.
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/dgmx.h"
+#include "common.cuh"
+#include "flux.cuh"
+
+namespace dgmx {
+
+struct AdjArgs {
+  const float *lr_in;  // lambda_r (read)
+  float *lr_out;       // k_adj_lift: lr + b lu (may alias lr_in, may be null); k_adj_vol: a * lr
+  const float *lu_in;  // lambda_u (read; null = 0)
+  float *lu_out;       // k_adj_vol: lu + dt A^T lr
+  float *g;            // face data [6][K][NFF]
+  const float *u_s;    // stage state (eps gradient; null = no gradient)
+  const float *rhs_s;  // A u_s at that stage
+  double *grad;        // K, FP64 accumulation of dt <lr, dA/deps u_s>
+  const float *geo;
+  const float4 *fgeo;
+  const int2 *fconn;
+  const float *Dn;     // [3][Np][Npad] D_d[i][j]
+  const float *LF;     // [Np][NFF] LIFT
+  const uint8_t *fmask, *nbrtab, *nbrface;
+  int64_t K;
+  float alpha, a, b, dt;
+};
+
+namespace {
+
+template <int N>
+struct AdjCfg {
+  using D = Dims<N>;
+  static constexpr int MQ = D::NFF / 4;                       // face-node quads
+  static constexpr int EB1 = 240 / MQ > 0 ? 240 / MQ : 1;     // elements per lift block
+  static constexpr int NT1 = (EB1 * MQ + 31) / 32 * 32;
+  static constexpr int EB2 = 240 / D::NQ;                     // elements per volume block
+  static constexpr int NT2 = (EB2 * D::NQ + 31) / 32 * 32;
+  static constexpr size_t SMEM1 = size_t(6) * EB1 * D::NPP * 4;
+  static constexpr size_t SMEM2 =
+      (size_t(6) * EB2 * D::NPP * 2 + size_t(18) * EB2 * D::NPP + EB2) * 4 + ((200 * D::NFP + 15) / 16) * 16;
+};
+
+__device__ __forceinline__ void cross3(const float *a, const float *b, float *c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Transposed flux Jacobians of one face node for the face owner with normal n
+// and weights (Zm, Zp, Ym, Yp), applied to its face data g = (gE, gH):
+// contributions to the owner's interior trace (em, hm) and to the exterior
+// trace (ep, hp). With flux_E = (Zp/Zs) n x dH - (alpha/Zs) n x n x dE and
+// flux_H = -(Yp/Ys) n x dE - (alpha/Ys) n x n x dH, dq = q+ - q-, and
+// (n x .)^T = -(n x .), (n x n x .)^T = n x n x .
+__device__ __forceinline__ void flux_transpose(const float *n, const float *g, float Zm, float Zp, float Ym, float Yp,
+                                               float alpha, float *ep, float *hp) {
+  float nE[3], nH[3], nnE[3], nnH[3];
+  cross3(n, g, nE);
+  cross3(n, g + 3, nH);
+  cross3(n, nE, nnE);
+  cross3(n, nH, nnH);
+  const float zs = 1.f / (Zm + Zp), ys = 1.f / (Ym + Yp);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    hp[c] = -(Zp * zs) * nE[c] - (alpha * ys) * nnH[c];
+    ep[c] = -(alpha * zs) * nnE[c] + (Yp * ys) * nH[c];
+  }
+}
+
+// <g, d flux / d(weights)>: returns the contractions with the partial
+// derivatives in Zm, Zp, Ym, Yp of the (unscaled) flux at one face node.
+__device__ __forceinline__ void flux_weight_partials(const float *n, const float *qm, const float *qp, float Zm,
+                                                     float Zp, float Ym, float Yp, float alpha, const float *g,
+                                                     float &sZm, float &sZp, float &sYm, float &sYp) {
+  float f[6];
+  maxwell_flux(make_float4(n[0], n[1], n[2], 1.f), qm, qp, Zm, Zp, Ym, Yp, alpha, f);
+  float dE[3], dH[3], nxdE[3], nxdH[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    dE[c] = qp[c] - qm[c];
+    dH[c] = qp[c + 3] - qm[c + 3];
+  }
+  cross3(n, dE, nxdE);
+  cross3(n, dH, nxdH);
+  const float zs = 1.f / (Zm + Zp), ys = 1.f / (Ym + Yp);
+  sZm = sZp = sYm = sYp = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    sZm += g[c] * (-f[c] * zs);
+    sZp += g[c] * ((nxdH[c] - f[c]) * zs);
+    sYm += g[c + 3] * (-f[c + 3] * ys);
+    sYp += g[c + 3] * ((-nxdE[c] - f[c + 3]) * ys);
+  }
+}
+
+// ---- 1. lr <- lr + b lu (own element) and g = Fscale * LIFT^T (W lr)
+template <int N>
+__global__ void __launch_bounds__(AdjCfg<N>::NT1) k_adj_lift(AdjArgs a) {
+  using D = Dims<N>;
+  using C = AdjCfg<N>;
+  constexpr int NP = D::NP, NPP = D::NPP, NQ = D::NQ, NFF = D::NFF, NFP = D::NFP, MQ = C::MQ, EB = C::EB1;
+  extern __shared__ float4 smem4[];
+  float *s_v = reinterpret_cast<float *>(smem4); // [6][EB][NPP]
+  const int tid = threadIdx.x;
+  const int64_t k0 = int64_t(blockIdx.x) * EB;
+  const int64_t KN = a.K * NPP;
+  for (int idx = tid; idx < 6 * EB * NQ; idx += C::NT1) {
+    const int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
+    const int e = rem / NQ, q = rem - e * NQ;
+    const int64_t k = k0 + e;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < a.K) {
+      const int64_t off = c * KN + k * NPP + 4 * q;
+      v = *reinterpret_cast<const float4 *>(a.lr_in + off);
+      if (a.lu_in) {
+        const float4 lu = *reinterpret_cast<const float4 *>(a.lu_in + off);
+        v.x = fmaf(a.b, lu.x, v.x), v.y = fmaf(a.b, lu.y, v.y), v.z = fmaf(a.b, lu.z, v.z), v.w = fmaf(a.b, lu.w, v.w);
+      }
+      if (4 * q + 3 >= NP) {
+        if (4 * q + 0 >= NP) v.x = 0.f;
+        if (4 * q + 1 >= NP) v.y = 0.f;
+        if (4 * q + 2 >= NP) v.z = 0.f;
+        if (4 * q + 3 >= NP) v.w = 0.f;
+      }
+      if (a.lr_out) *reinterpret_cast<float4 *>(a.lr_out + off) = v;
+      const float w = __ldg(a.geo + k * G_STRIDE + (c < 3 ? G_IEPS : G_IMU));
+      v.x *= w, v.y *= w, v.z *= w, v.w *= w;
+    }
+    reinterpret_cast<float4 *>(s_v)[(c * EB + e) * NQ + q] = v;
+  }
+  __syncthreads();
+  const int e = tid / MQ, mq = tid - (tid / MQ) * MQ;
+  const int64_t k = k0 + e;
+  if (tid >= EB * MQ || k >= a.K) return;
+  float acc[6][4];
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+#pragma unroll
+    for (int n = 0; n < 4; ++n) acc[c][n] = 0.f;
+#pragma unroll 4
+  for (int i = 0; i < NP; ++i) {
+    const float4 L = ldg4(a.LF + i * NFF + 4 * mq);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float v = s_v[(c * EB + e) * NPP + i];
+      acc[c][0] = fmaf(L.x, v, acc[c][0]);
+      acc[c][1] = fmaf(L.y, v, acc[c][1]);
+      acc[c][2] = fmaf(L.z, v, acc[c][2]);
+      acc[c][3] = fmaf(L.w, v, acc[c][3]);
+    }
+  }
+  float fs[4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) fs[n] = __ldg(a.fgeo + k * 4 + (4 * mq + n) / NFP).w;
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    *reinterpret_cast<float4 *>(a.g + (c * a.K + k) * NFF + 4 * mq) =
+        make_float4(fs[0] * acc[c][0], fs[1] * acc[c][1], fs[2] * acc[c][2], fs[3] * acc[c][3]);
+}
+
+// ---- 2. lu <- lu + dt A^T lr; lr <- a lr; grad += dt <lr, dA/deps u_s>
+template <int N, bool GRAD>
+__global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
+  using D = Dims<N>;
+  using C = AdjCfg<N>;
+  constexpr int NP = D::NP, NPP = D::NPP, NQ = D::NQ, NFF = D::NFF, NFP = D::NFP, EB = C::EB2, NT = C::NT2;
+  extern __shared__ float4 smem4[];
+  float *s_v = reinterpret_cast<float *>(smem4); // W lr   [6][EB][NPP]
+  float *s_w = s_v + 6 * EB * NPP;               // surface contributions [6][EB][NPP]
+  float *s_q = s_w + 6 * EB * NPP;               // contravariant combinations [18][EB][NPP]
+  float *s_gr = s_q + 18 * EB * NPP;             // gradient partial per element [EB]
+  uint8_t *s_fm = reinterpret_cast<uint8_t *>(s_gr + EB);
+  uint8_t *s_nb = s_fm + NFF, *s_nf = s_nb + kConnKinds * NFP;
+  const int tid = threadIdx.x;
+  const int64_t k0 = int64_t(blockIdx.x) * EB;
+  const int64_t KN = a.K * NPP;
+
+  for (int i = tid; i < NFF + 2 * kConnKinds * NFP; i += NT)
+    s_fm[i] = i < NFF ? a.fmask[i] : i < NFF + kConnKinds * NFP ? a.nbrtab[i - NFF] : a.nbrface[i - NFF - kConnKinds * NFP];
+  for (int i = tid; i < EB; i += NT) s_gr[i] = 0.f;
+  for (int idx = tid; idx < 6 * EB * NQ; idx += NT) {
+    const int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
+    const int e = rem / NQ, q = rem - e * NQ;
+    const int64_t k = k0 + e;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < a.K) {
+      v = *reinterpret_cast<const float4 *>(a.lr_in + c * KN + k * NPP + 4 * q);
+      const float w = __ldg(a.geo + k * G_STRIDE + (c < 3 ? G_IEPS : G_IMU));
+      v.x *= w, v.y *= w, v.z *= w, v.w *= w;
+      if (4 * q + 3 >= NP) {
+        if (4 * q + 0 >= NP) v.x = 0.f;
+        if (4 * q + 1 >= NP) v.y = 0.f;
+        if (4 * q + 2 >= NP) v.z = 0.f;
+        if (4 * q + 3 >= NP) v.w = 0.f;
+      }
+    }
+    reinterpret_cast<float4 *>(s_v)[(c * EB + e) * NQ + q] = v;
+    reinterpret_cast<float4 *>(s_w)[(c * EB + e) * NQ + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+
+  // -- eps gradient, term of the 1/eps factor: -(1/eps) <lr_E, rhs_E> = -<W lr_E, rhs_E>
+  if (GRAD) {
+    for (int idx = tid; idx < 3 * EB * NQ; idx += NT) {
+      const int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
+      const int e = rem / NQ, q = rem - e * NQ;
+      const int64_t k = k0 + e;
+      if (k >= a.K) continue;
+      const float4 r = *reinterpret_cast<const float4 *>(a.rhs_s + c * KN + k * NPP + 4 * q);
+      const float4 v = reinterpret_cast<const float4 *>(s_v)[(c * EB + e) * NQ + q];
+      atomicAdd(&s_gr[e], -(v.x * r.x + v.y * r.y + v.z * r.z + v.w * r.w));
+    }
+  }
+
+  // -- contravariant combinations q_{T,d} = sum_l (dr_d/dx_l) (+-W lr) of the transposed curl:
+  //    H_c <- d_{c+2}^T (W lr)_{E_{c+1}} - d_{c+1}^T (W lr)_{E_{c+2}}
+  //    E_c <- -d_{c+2}^T (W lr)_{H_{c+1}} + d_{c+1}^T (W lr)_{H_{c+2}}
+  for (int idx = tid; idx < EB * NPP; idx += NT) {
+    const int e = idx / NPP, i = idx - e * NPP;
+    const int64_t k = k0 + e;
+    float G[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) G[t] = k < a.K ? __ldg(a.geo + k * G_STRIDE + t) : 0.f;
+    float v[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[c] = s_v[(c * EB + e) * NPP + i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float g1 = G[3 * d + c1], g2 = G[3 * d + c2];
+        s_q[((3 + c) * 3 + d) * EB * NPP + e * NPP + i] = g2 * v[c1] - g1 * v[c2];
+        s_q[(c * 3 + d) * EB * NPP + e * NPP + i] = -g2 * v[3 + c1] + g1 * v[3 + c2];
+      }
+    }
+  }
+
+  // -- transposed flux Jacobians (interior side with own g, exterior side with
+  //    the neighbour's g at the matching face node) and the weight terms of the
+  //    eps gradient, one face node per item
+  for (int it = tid; it < EB * NFF; it += NT) {
+    const int e = it / NFF, fm = it - e * NFF, f = fm / NFP, m = fm - f * NFP;
+    const int64_t k = k0 + e;
+    if (k >= a.K) continue;
+    const int2 cn = __ldg(a.fconn + k * 4 + f);
+    const float4 nf = __ldg(a.fgeo + k * 4 + f);
+    const float n[3] = {nf.x, nf.y, nf.z};
+    const float Zk = __ldg(a.geo + k * G_STRIDE + G_Z), Yk = __ldg(a.geo + k * G_STRIDE + G_Y);
+    const bool wall = cn.y == kBoundaryConn;
+    const int64_t k2 = wall ? k : cn.x;
+    const float Z2 = wall ? Zk : __ldg(a.geo + k2 * G_STRIDE + G_Z), Y2 = wall ? Yk : __ldg(a.geo + k2 * G_STRIDE + G_Y);
+    float gk[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) gk[c] = a.g[(c * a.K + k) * NFF + fm];
+    float ep[3], hp[3], acc[6];
+    flux_transpose(n, gk, Zk, Z2, Yk, Y2, a.alpha, ep, hp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] = -ep[c];      // interior side: the E and H Jacobians are the negatives of the exterior ones
+      acc[c + 3] = -hp[c];
+    }
+    const int fm2 = wall ? 0 : s_nf[cn.y * NFP + m] + (cn.y / 6 % 4) * NFP;
+    float g2[6];
+    if (wall) {
+      // exterior state E+ = -E-, H+ = H- folds back onto the interior node
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[c] -= ep[c];
+        acc[c + 3] += hp[c];
+      }
+    } else {
+      // the neighbour's flux sees this element as its exterior side
+#pragma unroll
+      for (int c = 0; c < 6; ++c) g2[c] = a.g[(c * a.K + k2) * NFF + fm2];
+      const float n2[3] = {-n[0], -n[1], -n[2]};
+      float ep2[3], hp2[3];
+      flux_transpose(n2, g2, Z2, Zk, Y2, Yk, a.alpha, ep2, hp2);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[c] += ep2[c];
+        acc[c + 3] += hp2[c];
+      }
+    }
+    const int vm = s_fm[fm];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) atomicAdd(&s_w[(c * EB + e) * NPP + vm], acc[c]);
+    if (GRAD) {
+      const float ek = 1.f / __ldg(a.geo + k * G_STRIDE + G_IEPS);
+      const float dZ = -Zk / (2.f * ek), dY = Yk / (2.f * ek);
+      float qm[6], qp[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) qm[c] = __ldg(a.u_s + c * KN + k * NPP + vm);
+      if (wall) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          qp[c] = -qm[c];
+          qp[c + 3] = qm[c + 3];
+        }
+      } else {
+        const int vn = s_nb[cn.y * NFP + m];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) qp[c] = __ldg(a.u_s + c * KN + k2 * NPP + vn);
+      }
+      float sZm, sZp, sYm, sYp;
+      flux_weight_partials(n, qm, qp, Zk, Z2, Yk, Y2, a.alpha, gk, sZm, sZp, sYm, sYp);
+      float contrib = sZm * dZ + sYm * dY;
+      if (wall) {
+        contrib += sZp * dZ + sYp * dY; // the mirrored exterior carries the same weights
+      } else {
+        const float n2[3] = {-n[0], -n[1], -n[2]};
+        float tZm, tZp, tYm, tYp;
+        flux_weight_partials(n2, qp, qm, Z2, Zk, Y2, Yk, a.alpha, g2, tZm, tZp, tYm, tYp);
+        contrib += tZp * dZ + tYp * dY;
+      }
+      atomicAdd(&s_gr[e], contrib);
+    }
+  }
+  __syncthreads();
+
+  // -- transposed volume term: w_T[j] = sum_d sum_i D_d[i][j] q_{T,d}[i]
+  const int e = tid / NQ, q = tid - (tid / NQ) * NQ;
+  const int64_t k = k0 + e;
+  if (tid < EB * NQ && k < a.K) {
+    float acc[6][4];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) acc[c][n] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll 2
+      for (int i = 0; i < NP; ++i) {
+        const float4 Dv = ldg4(a.Dn + (d * NP + i) * NPP + 4 * q);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const float qv = s_q[(c * 3 + d) * EB * NPP + e * NPP + i];
+          acc[c][0] = fmaf(Dv.x, qv, acc[c][0]);
+          acc[c][1] = fmaf(Dv.y, qv, acc[c][1]);
+          acc[c][2] = fmaf(Dv.z, qv, acc[c][2]);
+          acc[c][3] = fmaf(Dv.w, qv, acc[c][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int64_t off = c * KN + k * NPP + 4 * q;
+      const float4 sw = reinterpret_cast<const float4 *>(s_w)[(c * EB + e) * NQ + q];
+      float4 lu = a.lu_in ? *reinterpret_cast<const float4 *>(a.lu_in + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float wv[4] = {acc[c][0] + sw.x, acc[c][1] + sw.y, acc[c][2] + sw.z, acc[c][3] + sw.w};
+      float o[4] = {lu.x, lu.y, lu.z, lu.w};
+#pragma unroll
+      for (int n = 0; n < 4; ++n) o[n] = (4 * q + n < NP) ? fmaf(a.dt, wv[n], o[n]) : 0.f;
+      *reinterpret_cast<float4 *>(a.lu_out + off) = make_float4(o[0], o[1], o[2], o[3]);
+      if (a.lr_out) {
+        const float4 lr = *reinterpret_cast<const float4 *>(a.lr_in + off);
+        *reinterpret_cast<float4 *>(a.lr_out + off) = make_float4(a.a * lr.x, a.a * lr.y, a.a * lr.z, a.a * lr.w);
+      }
+    }
+  }
+  if (GRAD && tid < EB && k0 + tid < a.K) a.grad[k0 + tid] += double(a.dt) * double(s_gr[tid]);
+}
+
+template <int N>
+cudaError_t launch_adj_order(int which, const AdjArgs &a, cudaStream_t s) {
+  using C = AdjCfg<N>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_lift<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM1));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_adj_vol<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_adj_vol<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (which == 0) {
+    k_adj_lift<N><<<unsigned((a.K + C::EB1 - 1) / C::EB1), C::NT1, C::SMEM1, s>>>(a);
+  } else {
+    const unsigned blocks = unsigned((a.K + C::EB2 - 1) / C::EB2);
+    if (a.u_s)
+      k_adj_vol<N, true><<<blocks, C::NT2, C::SMEM2, s>>>(a);
+    else
+      k_adj_vol<N, false><<<blocks, C::NT2, C::SMEM2, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj(int N, int which, const AdjArgs &a, cudaStream_t s) {
+  switch (N) {
+  case 1: return launch_adj_order<1>(which, a, s);
+  case 2: return launch_adj_order<2>(which, a, s);
+  case 3: return launch_adj_order<3>(which, a, s);
+  case 4: return launch_adj_order<4>(which, a, s);
+  case 5: return launch_adj_order<5>(which, a, s);
+  case 6: return launch_adj_order<6>(which, a, s);
+  case 7: return launch_adj_order<7>(which, a, s);
+  default: return cudaErrorInvalidValue;
+  }
+}
+
+// Receiver residual of one step: res_n = E(u)[recv] - Eref_n (FP32, stored) and
+// J += |res_n|^2 (FP64).
+__global__ void k_recv_residual(const float *u, int64_t K, int Np, int Npad, const int64_t *recv, int64_t R,
+                                const float *Eref, float *resid, double *J) {
+  double local = 0.0;
+  for (int64_t t = threadIdx.x + int64_t(blockIdx.x) * blockDim.x; t < 3 * R; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t / R);
+    const int64_t r = t - c * R, node = recv[r];
+    const int64_t k = node / Np, i = node - k * Np;
+    const float v = u[(c * K + k) * Npad + i] - (Eref ? Eref[t] : 0.f);
+    if (resid) resid[t] = v;
+    local += double(v) * double(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && J) atomicAdd(J, local);
+}
+
+// Adjoint source of one step: lu[E at recv] += 2 res_n (receivers are distinct).
+__global__ void k_recv_source(float *lu, int64_t K, int Np, int Npad, const int64_t *recv, int64_t R,
+                              const float *resid) {
+  for (int64_t t = threadIdx.x + int64_t(blockIdx.x) * blockDim.x; t < 3 * R; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t / R);
+    const int64_t r = t - c * R, node = recv[r];
+    const int64_t k = node / Np, i = node - k * Np;
+    lu[(c * K + k) * Npad + i] += 2.f * resid[t];
+  }
+}
+
+__global__ void k_recv_gather(const float *u, int64_t K, int Np, int Npad, const int64_t *recv, int64_t R, float *out) {
+  for (int64_t t = threadIdx.x + int64_t(blockIdx.x) * blockDim.x; t < 3 * R; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t / R);
+    const int64_t r = t - c * R, node = recv[r];
+    const int64_t k = node / Np, i = node - k * Np;
+    out[t] = u[(c * K + k) * Npad + i];
+  }
+}
+
+__global__ void k_check_recv(const int64_t *recv, int64_t R, int64_t nodes, int *bad) {
+  for (int64_t t = threadIdx.x + int64_t(blockIdx.x) * blockDim.x; t < R; t += int64_t(gridDim.x) * blockDim.x)
+    if (recv[t] < 0 || recv[t] >= nodes) atomicExch(bad, 1);
+}
+
+int fail(dg_ctx *ctx, int code, const std::string &msg) {
+  ctx->err = msg;
+  return code;
+}
+
+// Owns the temporary device buffers of one adjoint call.
+struct DevBufs {
+  std::vector<void *> ptrs;
+  ~DevBufs() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  T *get(size_t count) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T *>(p);
+  }
+};
+
+AdjArgs adj_base(const dg_ctx *c, float alpha) {
+  AdjArgs a{};
+  a.geo = c->d_geo;
+  a.fgeo = c->d_fgeo;
+  a.fconn = c->d_fconn;
+  a.Dn = c->d_Dn;
+  a.LF = c->d_LF;
+  a.fmask = c->d_tab;
+  a.nbrtab = c->d_tab + 4 * c->ops.Nfp;
+  a.nbrface = c->d_tab + 4 * c->ops.Nfp + kConnKinds * c->ops.Nfp;
+  a.K = c->K;
+  a.alpha = alpha;
+  return a;
+}
+
+StageArgs stage_base(const dg_ctx *c, float alpha, double dt) {
+  StageArgs a{};
+  a.geo = c->d_geo;
+  a.fgeo = c->d_fgeo;
+  a.fconn = c->d_fconn;
+  a.DT = c->d_DT;
+  a.LT = c->d_LT;
+  a.fmask = c->d_tab;
+  a.nbrtab = c->d_tab + 4 * c->ops.Nfp;
+  a.K = c->K;
+  a.alpha = alpha;
+  a.dt = float(dt);
+  return a;
+}
+
+int check_common(dg_ctx *ctx, const float *u0, double dt, int nsteps, float alpha, const int64_t *recv, int64_t R,
+                 const char *who) {
+  if (!ctx) return DG_ERR_ARG;
+  if (ctx->K <= 0) return fail(ctx, DG_ERR_ARG, std::string(who) + ": no mesh uploaded");
+  if (!u0 || (reinterpret_cast<uintptr_t>(u0) & 15u)) return fail(ctx, DG_ERR_ARG, std::string(who) + ": bad u0");
+  if (nsteps < 1 || !std::isfinite(dt) || !std::isfinite(alpha))
+    return fail(ctx, DG_ERR_ARG, std::string(who) + ": bad dt/nsteps/alpha");
+  if (R < 1 || !recv) return fail(ctx, DG_ERR_ARG, std::string(who) + ": need at least one receiver");
+  int *bad = ctx->d_flag + 2, hbad = 0;
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) {
+    k_check_recv<<<unsigned((R + 255) / 256), 256, 0, ctx->stream>>>(recv, R, ctx->K * ctx->ops.Np, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string(who) + ": " + cudaGetErrorString(e));
+  if (hbad) return fail(ctx, DG_ERR_ARG, std::string(who) + ": receiver index outside [0, K*Np)");
+  return DG_OK;
+}
+
+} // namespace
+} // namespace dgmx
+
+using namespace dgmx;
+
+extern "C" {
+
+int dg_rhs_transpose(dg_ctx *ctx, const float *v, float *w, float alpha) {
+  if (!ctx) return DG_ERR_ARG;
+  if (ctx->K <= 0) return fail(ctx, DG_ERR_ARG, "dg_rhs_transpose: no mesh uploaded");
+  if (!v || !w || ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(w)) & 15u))
+    return fail(ctx, DG_ERR_ARG, "dg_rhs_transpose: null or misaligned field");
+  const size_t bytes = size_t(6) * ctx->K * ctx->ops.Npad * sizeof(float);
+  const uintptr_t pv = reinterpret_cast<uintptr_t>(v), pw = reinterpret_cast<uintptr_t>(w);
+  if (pv < pw + bytes && pw < pv + bytes) return fail(ctx, DG_ERR_ARG, "dg_rhs_transpose: v and w overlap");
+  DevBufs buf;
+  float *g = buf.get<float>(size_t(6) * ctx->K * 4 * ctx->ops.Nfp);
+  if (!g) return fail(ctx, DG_ERR_OOM, "dg_rhs_transpose: device allocation failed");
+  AdjArgs a = adj_base(ctx, alpha);
+  a.lr_in = v;
+  a.g = g;
+  a.dt = 1.f;
+  a.lu_out = w;
+  cudaError_t e = launch_adj(ctx->N, 0, a, ctx->stream);
+  if (e == cudaSuccess) e = launch_adj(ctx->N, 1, a, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_rhs_transpose: ") + cudaGetErrorString(e));
+  return DG_OK;
+}
+
+int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, float alpha,
+                       const int64_t *recv, int64_t R, float *out) {
+  int rc = check_common(ctx, u0, dt, nsteps, alpha, recv, R, "dg_receiver_traces");
+  if (rc) return rc;
+  if (!out) return fail(ctx, DG_ERR_ARG, "dg_receiver_traces: null output");
+  if (eps && (rc = dg_set_eps(ctx, eps))) return rc;
+  const size_t fl = size_t(6) * ctx->K * ctx->ops.Npad;
+  DevBufs buf;
+  float *u = buf.get<float>(fl), *nxt = buf.get<float>(fl), *res = buf.get<float>(fl);
+  if (!u || !nxt || !res) return fail(ctx, DG_ERR_OOM, "dg_receiver_traces: device allocation failed");
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(u, u0, fl * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(res, 0, fl * 4, s);
+  StageArgs a = stage_base(ctx, alpha, dt);
+  a.res = res;
+  const unsigned rb = unsigned((3 * R + 255) / 256);
+  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+      a.u = u;
+      a.u_out = nxt;
+      a.rk_a = float(kLserkA[st]);
+      a.rk_b = float(kLserkB[st]);
+      e = launch_stage_simt(ctx->N, MODE_LSERK, a, s);
+      std::swap(u, nxt);
+    }
+    if (e == cudaSuccess) {
+      k_recv_gather<<<rb, 256, 0, s>>>(u, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, out + int64_t(n) * 3 * R);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_receiver_traces: ") + cudaGetErrorString(e));
+  return DG_OK;
+}
+
+int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, int ckpt_every,
+                    float alpha, const int64_t *recv, int64_t R, const float *Eref, double *J, double *dJ_deps,
+                    float *dJ_du0) {
+  int rc = check_common(ctx, u0, dt, nsteps, alpha, recv, R, "dg_adjoint_step");
+  if (rc) return rc;
+  if (!Eref) return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: null Eref");
+  if (ckpt_every < 1) return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: ckpt_every must be >= 1");
+  if (dJ_du0 && (reinterpret_cast<uintptr_t>(dJ_du0) & 15u))
+    return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: dJ_du0 must be 16-byte aligned");
+  if (eps && (rc = dg_set_eps(ctx, eps))) return rc;
+  const int C = ckpt_every < nsteps ? ckpt_every : nsteps;
+  const int nseg = (nsteps + C - 1) / C;
+  const size_t fl = size_t(6) * ctx->K * ctx->ops.Npad;
+  const size_t gfl = size_t(6) * ctx->K * 4 * ctx->ops.Nfp;
+  cudaStream_t s = ctx->stream;
+
+  DevBufs buf;
+  float *u = buf.get<float>(fl), *nxt = buf.get<float>(fl), *res = buf.get<float>(fl);
+  float *lu = buf.get<float>(fl), *lr = buf.get<float>(fl), *g = buf.get<float>(gfl);
+  float *resid = buf.get<float>(size_t(nsteps) * 3 * R);
+  double *Jd = buf.get<double>(1), *grad = buf.get<double>(ctx->K);
+  float *ck = buf.get<float>(fl * nseg);
+  // stage states u_s and stage right-hand sides A u_s of one segment
+  float *US = buf.get<float>(fl * 5 * C), *RS = buf.get<float>(fl * 5 * C);
+  if (!u || !nxt || !res || !lu || !lr || !g || !resid || !Jd || !grad || !ck || !US || !RS)
+    return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed (checkpoints and one segment of stage "
+                                 "states are kept in device memory)");
+  cudaError_t e = cudaMemcpyAsync(u, u0, fl * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(res, 0, fl * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Jd, 0, sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, ctx->K * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lu, 0, fl * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lr, 0, fl * 4, s);
+  StageArgs sa = stage_base(ctx, alpha, dt);
+  const unsigned rb = unsigned((3 * R + 255) / 256);
+
+  // ---- forward sweep with checkpoints every C steps and the receiver residuals
+  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    if (n % C == 0) e = cudaMemcpyAsync(ck + fl * (n / C), u, fl * 4, cudaMemcpyDeviceToDevice, s);
+    sa.res = res;
+    for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+      sa.u = u;
+      sa.u_out = nxt;
+      sa.rk_a = float(kLserkA[st]);
+      sa.rk_b = float(kLserkB[st]);
+      e = launch_stage_simt(ctx->N, MODE_LSERK, sa, s);
+      std::swap(u, nxt);
+    }
+    if (e == cudaSuccess) {
+      k_recv_residual<<<rb, 256, 0, s>>>(u, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, Eref + int64_t(n) * 3 * R,
+                                         resid + int64_t(n) * 3 * R, Jd);
+      e = cudaGetLastError();
+    }
+  }
+
+  // ---- reverse sweep, segment by segment
+  AdjArgs aa = adj_base(ctx, alpha);
+  aa.g = g;
+  aa.grad = grad;
+  aa.dt = float(dt);
+  for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
+    const int n0 = seg * C, n1 = (n0 + C < nsteps) ? n0 + C : nsteps;
+    // recompute the segment, storing every stage state and its right-hand side
+    sa.res = res;
+    for (int n = n0; n < n1 && e == cudaSuccess; ++n)
+      for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+        const size_t j = size_t(n - n0) * 5 + st;
+        sa.u = j == 0 ? ck + fl * seg : US + fl * j;
+        sa.u_out = (j + 1 < size_t(5) * C) ? US + fl * (j + 1) : nxt;
+        sa.rhs = RS + fl * j;
+        sa.rk_a = float(kLserkA[st]);
+        sa.rk_b = float(kLserkB[st]);
+        e = launch_stage_simt(ctx->N, MODE_LSERK_STORE, sa, s);
+      }
+    for (int n = n1 - 1; n >= n0 && e == cudaSuccess; --n) {
+      k_recv_source<<<rb, 256, 0, s>>>(lu, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, resid + int64_t(n) * 3 * R);
+      e = cudaGetLastError();
+      for (int st = 4; st >= 0 && e == cudaSuccess; --st) {
+        const size_t j = size_t(n - n0) * 5 + st;
+        aa.lr_in = lr;
+        aa.lr_out = lr;
+        aa.lu_in = lu;
+        aa.b = float(kLserkB[st]);
+        e = launch_adj(ctx->N, 0, aa, s); // lr += b lu; g = Fscale LIFT^T W lr
+        if (e != cudaSuccess) break;
+        aa.lu_out = lu;
+        aa.a = float(kLserkA[st]);
+        aa.u_s = j == 0 ? ck + fl * seg : US + fl * j;
+        aa.rhs_s = RS + fl * j;
+        e = launch_adj(ctx->N, 1, aa, s); // lu += dt A^T lr; grad; lr *= a
+      }
+    }
+  }
+  double Jh = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&Jh, Jd, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && dJ_deps) e = cudaMemcpyAsync(dJ_deps, grad, ctx->K * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && dJ_du0) e = cudaMemcpyAsync(dJ_du0, lu, fl * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_adjoint_step: ") + cudaGetErrorString(e));
+  if (J) *J = Jh;
+  if (!std::isfinite(Jh)) return fail(ctx, DG_ERR_NONFINITE, "dg_adjoint_step: misfit is not finite");
+  return DG_OK;
+}
+
+} // extern "C"

@@ -52,6 +52,8 @@ void free_mesh(dg_ctx *c) {
   dfree(c->d_DT);
   dfree(c->d_LT);
   dfree(c->d_tab);
+  dfree(c->d_Dn);
+  dfree(c->d_LF);
   dfree(c->d_M);
   dfree(c->d_scratch);
   dfree(c->d_red);
@@ -187,9 +189,16 @@ int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, 
       for (int i = 0; i < Np; ++i) DT[(size_t(d) * Np + j) * Npad + i] = float((*Ds[d])[i * Np + j]);
   for (int m = 0; m < 4 * Nfp; ++m)
     for (int i = 0; i < Np; ++i) LT[size_t(m) * Npad + i] = float(o.LIFT[i * 4 * Nfp + m]);
-  std::vector<uint8_t> tab(4 * Nfp + kConnKinds * Nfp);
+  std::vector<uint8_t> tab(4 * Nfp + 2 * kConnKinds * Nfp);
   for (int q = 0; q < 4 * Nfp; ++q) tab[q] = uint8_t(o.Fmask[q]);
   std::memcpy(tab.data() + 4 * Nfp, o.nbr_node.data(), o.nbr_node.size());
+  std::memcpy(tab.data() + 4 * Nfp + kConnKinds * Nfp, o.nbr_fnode.data(), o.nbr_fnode.size());
+  std::vector<float> Dn(size_t(3) * Np * Npad, 0.f), LF(size_t(Np) * 4 * Nfp, 0.f);
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < Np; ++i)
+      for (int j = 0; j < Np; ++j) Dn[(size_t(d) * Np + i) * Npad + j] = float((*Ds[d])[i * Np + j]);
+  for (int i = 0; i < Np; ++i)
+    for (int m = 0; m < 4 * Nfp; ++m) LF[size_t(i) * 4 * Nfp + m] = float(o.LIFT[i * 4 * Nfp + m]);
   std::vector<int2> fconn(K * 4);
   for (int64_t q = 0; q < K * 4; ++q) fconn[q] = make_int2(con.nbr_elem[q], con.conn[q]);
 
@@ -208,6 +217,7 @@ int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, 
             alloc((void **)&ctx->d_fconn, size_t(K) * 4 * sizeof(int2)) &&
             alloc((void **)&ctx->d_DT, DT.size() * sizeof(float)) &&
             alloc((void **)&ctx->d_LT, LT.size() * sizeof(float)) && alloc((void **)&ctx->d_tab, tab.size()) &&
+            alloc((void **)&ctx->d_Dn, Dn.size() * sizeof(float)) && alloc((void **)&ctx->d_LF, LF.size() * sizeof(float)) &&
             alloc((void **)&ctx->d_M, size_t(Np) * Np * sizeof(double)) &&
             alloc((void **)&ctx->d_scratch, size_t(6) * K * Npad * sizeof(float)) &&
             alloc((void **)&ctx->d_red, 16 * sizeof(double)) && alloc((void **)&ctx->d_flag, 16 * sizeof(int)) &&
@@ -230,6 +240,8 @@ int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, 
   h2d(ctx->d_DT, DT.data(), DT.size() * sizeof(float));
   h2d(ctx->d_LT, LT.data(), LT.size() * sizeof(float));
   h2d(ctx->d_tab, tab.data(), tab.size());
+  h2d(ctx->d_Dn, Dn.data(), Dn.size() * sizeof(float));
+  h2d(ctx->d_LF, LF.data(), LF.size() * sizeof(float));
   h2d(ctx->d_M, o.M.data(), o.M.size() * sizeof(double));
   h2d(ctx->d_fconn, fconn.data(), fconn.size() * sizeof(int2));
   h2d(d_vert, VX, Nv * sizeof(double));

@@ -17,7 +17,7 @@ enum GeoSlot {
 };
 
 // Stage kinds of the fused kernels.
-enum StageMode { MODE_RHS = 0, MODE_LSERK = 1 };
+enum StageMode { MODE_RHS = 0, MODE_LSERK = 1, MODE_LSERK_STORE = 2 }; // STORE: LSERK update that also writes rhs
 
 // Arguments of one fused right-hand-side / LSERK-stage launch.
 struct StageArgs {
@@ -79,7 +79,9 @@ struct dg_ctx {
   int2 *d_fconn = nullptr;
   float *d_DT = nullptr;
   float *d_LT = nullptr;
-  uint8_t *d_tab = nullptr;  // fmask (4Nfp) followed by the neighbour-node table (96 Nfp)
+  uint8_t *d_tab = nullptr;  // fmask (4Nfp), neighbour volume-node table (96 Nfp), neighbour face-node table (96 Nfp)
+  float *d_Dn = nullptr;     // [3][Np][Npad] D_d[i][j] row-major (transposed-operator kernels)
+  float *d_LF = nullptr;     // [Np][4Nfp] LIFT row-major (transposed-operator kernels)
   double *d_M = nullptr;
   float *d_scratch = nullptr;  // field vector for the LSERK stage ping-pong
   double *d_red = nullptr;     // reduction outputs

@@ -395,6 +395,7 @@ bool build_refops(int N, RefOps &o, std::string &err) {
                                  (1.0 + o.t[n]) / 2.0};
   };
   o.nbr_node.assign(kConnKinds * Nfp, 0);
+  o.nbr_fnode.assign(kConnKinds * Nfp, 0);
   for (int f = 0; f < 4; ++f)
     for (int f2 = 0; f2 < 4; ++f2)
       for (int p = 0; p < 6; ++p)
@@ -402,18 +403,22 @@ bool build_refops(int N, RefOps &o, std::string &err) {
           auto l = bary(o.Fmask[f * Nfp + a]);
           double want[3];
           for (int v = 0; v < 3; ++v) want[perms[p][v]] = l[kFaceVerts[f][v]];
-          int found = -1;
+          int found = -1, found_b = -1;
           for (int b = 0; b < Nfp && found < 0; ++b) {
             auto l2 = bary(o.Fmask[f2 * Nfp + b]);
             double d = 0.0;
             for (int v = 0; v < 3; ++v) d += std::fabs(l2[kFaceVerts[f2][v]] - want[v]);
-            if (d < 1e-9) found = o.Fmask[f2 * Nfp + b];
+            if (d < 1e-9) {
+              found = o.Fmask[f2 * Nfp + b];
+              found_b = b;
+            }
           }
           if (found < 0) {
             err = "face nodes are not symmetric under vertex permutations";
             return false;
           }
           o.nbr_node[((f * 4 + f2) * 6 + p) * Nfp + a] = static_cast<uint8_t>(found);
+          o.nbr_fnode[((f * 4 + f2) * 6 + p) * Nfp + a] = static_cast<uint8_t>(found_b);
         }
   return true;
 }

@@ -28,6 +28,8 @@ struct RefOps {
   // For connection kind (f*4 + f2)*6 + perm and own face node m: the volume
   // node of the neighbour holding the same physical point.
   std::vector<uint8_t> nbr_node;  // kConnKinds x Nfp
+  // Same connection kinds: index of that node within the neighbour's face.
+  std::vector<uint8_t> nbr_fnode; // kConnKinds x Nfp
 };
 
 // Builds every reference operator for order N (1..kMaxOrder). Returns false

@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
       }
       *reinterpret_cast<float4 *>(a.res + off) = make_float4(rv[0], rv[1], rv[2], rv[3]);
       *reinterpret_cast<float4 *>(a.u_out + off) = make_float4(uv[0], uv[1], uv[2], uv[3]);
+      if (MODE == MODE_LSERK_STORE) *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
     }
   }
 }
@@ -202,13 +203,18 @@ cudaError_t launch_simt_order(int mode, const StageArgs &a, cudaStream_t s) {
                                           int(Cfg::SMEM));
     if (e1 != cudaSuccess) return e1;
     if (e2 != cudaSuccess) return e2;
+    cudaError_t e3 = cudaFuncSetAttribute(k_stage_simt<N, MODE_LSERK_STORE>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::SMEM));
+    if (e3 != cudaSuccess) return e3;
     configured = true;
   }
   unsigned blocks = unsigned((a.K + Cfg::EB - 1) / Cfg::EB);
   if (mode == MODE_RHS)
     k_stage_simt<N, MODE_RHS><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
-  else
+  else if (mode == MODE_LSERK)
     k_stage_simt<N, MODE_LSERK><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
+  else
+    k_stage_simt<N, MODE_LSERK_STORE><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
