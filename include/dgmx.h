@@ -144,6 +144,43 @@ int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alph
  * those of dg_step. */
 int dg_step_noalloc(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);
 
+/* Ensembles of independent meshes (uneven sizes, own materials, own time
+ * steps) advanced together. Upload (HOST arrays): M meshes; Nv[i] and K[i]
+ * their vertex and element counts; VX/VY/VZ the vertices of all meshes
+ * concatenated; EToV all element tables concatenated with each mesh's own
+ * 0-based vertex numbering; eps all elements' permittivities concatenated
+ * (NULL = 1); dt[i] the time step of mesh i. The meshes are stored as one
+ * disjoint union, so a field vector is [6][sum K][Np_pad] with mesh i owning
+ * elements [offsets[i], offsets[i+1]) (dg_ensemble_layout). Replaces any mesh.
+ * Errors as dg_mesh_upload. */
+int dg_ensemble_upload(dg_ctx *ctx, int M, const int64_t *Nv, const double *VX, const double *VY, const double *VZ,
+                       const int64_t *K, const int32_t *EToV, const float *eps, const double *dt);
+
+/* Number of meshes and the M+1 element offsets (HOST outputs, may be NULL). */
+int dg_ensemble_layout(const dg_ctx *ctx, int *M, int64_t *offsets);
+
+/* Advance every mesh of the ensemble by nsteps LSERK4 steps of its own dt in
+ * ONE persistent cooperative kernel launch (FP32 CUDA cores; a grid-wide
+ * barrier with a bounded wait separates the stages; a wait that runs out sets
+ * the flag reported by dg_sync), replayed from a CUDA graph captured on the
+ * first call with these arguments. u and res are DEVICE field vectors (in/out).
+ * The first call autotunes the elements per block unless dg_ensemble_tune ran. */
+int dg_ensemble_step(dg_ctx *ctx, float *u, float *res, int nsteps, float alpha);
+
+/* Autotuner: time every elements-per-block candidate of the persistent
+ * launch on the uploaded ensemble (2 steps, best of 3) and keep the fastest;
+ * the choice is cached in a text file (environment DGMX_TUNE_CACHE, default
+ * $HOME/.cache/dgmx_ensemble_tune.txt) keyed by GPU name, N and total element
+ * count, and reused unless force is nonzero. Synchronises the stream. */
+int dg_ensemble_tune(dg_ctx *ctx, int force);
+
+/* Tuning log: the chosen elements per block, and for each of the 4 candidates
+ * its elements per block and measured ms per step (0 = not timed). HOST outputs. */
+int dg_ensemble_tuning(const dg_ctx *ctx, int *best_eb, int *eb, float *ms_per_step);
+
+/* 1 if the last dg_ensemble_step was replayed from a captured CUDA graph. */
+int dg_ensemble_graph_used(const dg_ctx *ctx);
+
 /* Wait for all work enqueued on the context's stream and report device-side
  * failures: returns DG_ERR_TIMEOUT (and clears the flag) if a tensor-core
  * kernel gave up waiting for its matrix units after its iteration limit

@@ -59,6 +59,12 @@ def lib():
             L.dg_sync.argtypes = [vp]
             L.dg_step_noalloc.argtypes = [vp, vp, vp, dbl, i32, flt]
             L.dg_rhs_transpose.argtypes = [vp, vp, vp, flt]
+            L.dg_ensemble_upload.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.dg_ensemble_layout.argtypes = [vp, C.POINTER(i32), vp]
+            L.dg_ensemble_step.argtypes = [vp, vp, vp, i32, flt]
+            L.dg_ensemble_tune.argtypes = [vp, i32]
+            L.dg_ensemble_tuning.argtypes = [vp, C.POINTER(i32), vp, vp]
+            L.dg_ensemble_graph_used.argtypes = [vp]
             L.dg_receiver_traces.argtypes = [vp, vp, vp, dbl, i32, flt, vp, i64, vp]
             L.dg_adjoint_step.argtypes = [vp, vp, vp, dbl, i32, i32, flt, vp, i64, vp, C.POINTER(dbl), vp, vp]
             _lib = L
@@ -183,6 +189,48 @@ class Solver:
                                           int(nsteps), int(ckpt_every), float(alpha), _t_ptr(recv), recv.numel(),
                                           _t_ptr(Eref), C.byref(J), _t_ptr(g_eps), _t_ptr(g_u0)))
         return J.value, g_eps, g_u0
+
+    # ---------------------------------------------------------------- ensembles
+    def upload_ensemble(self, meshes, eps=None, dt=None):
+        """meshes: list of (VX, VY, VZ, EToV); eps: list of per-element arrays or None;
+        dt: per-mesh time steps."""
+        M = len(meshes)
+        Nv = np.array([m[0].size for m in meshes], dtype=np.int64)
+        Ks = np.array([m[3].shape[0] for m in meshes], dtype=np.int64)
+        VX = np.ascontiguousarray(np.concatenate([m[0] for m in meshes]), dtype=np.float64)
+        VY = np.ascontiguousarray(np.concatenate([m[1] for m in meshes]), dtype=np.float64)
+        VZ = np.ascontiguousarray(np.concatenate([m[2] for m in meshes]), dtype=np.float64)
+        EToV = np.ascontiguousarray(np.concatenate([m[3] for m in meshes]), dtype=np.int32)
+        e = None if eps is None else np.ascontiguousarray(np.concatenate(eps), dtype=np.float32)
+        dts = np.ascontiguousarray(dt, dtype=np.float64)
+        self._check(lib().dg_ensemble_upload(self._h, M, _np_ptr(Nv), _np_ptr(VX), _np_ptr(VY), _np_ptr(VZ),
+                                             _np_ptr(Ks), _np_ptr(EToV), _np_ptr(e), _np_ptr(dts)))
+        self.K = int(Ks.sum())
+        return self
+
+    def ensemble_layout(self):
+        M = C.c_int()
+        self._check(lib().dg_ensemble_layout(self._h, C.byref(M), None))
+        off = np.zeros(M.value + 1, dtype=np.int64)
+        self._check(lib().dg_ensemble_layout(self._h, C.byref(M), _np_ptr(off)))
+        return off
+
+    def ensemble_step(self, u, res, nsteps: int, alpha: float = 1.0):
+        self._check(lib().dg_ensemble_step(self._h, _t_ptr(u), _t_ptr(res), int(nsteps), float(alpha)))
+        return u, res
+
+    def ensemble_tune(self, force: bool = False):
+        self._check(lib().dg_ensemble_tune(self._h, 1 if force else 0))
+
+    def ensemble_tuning(self):
+        best = C.c_int()
+        eb = np.zeros(4, dtype=np.int32)
+        ms = np.zeros(4, dtype=np.float32)
+        self._check(lib().dg_ensemble_tuning(self._h, C.byref(best), _np_ptr(eb), _np_ptr(ms)))
+        return best.value, eb.tolist(), ms.tolist()
+
+    def ensemble_graph_used(self) -> bool:
+        return bool(lib().dg_ensemble_graph_used(self._h))
 
     def sync(self):
         self._check(lib().dg_sync(self._h))

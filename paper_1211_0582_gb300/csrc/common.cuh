@@ -7,12 +7,14 @@
 
 #include "refops.h"
 
+struct dg_ctx;
+
 namespace dgmx {
 
 // Per-element FP32 record (64 bytes): metric terms, material factors, Jacobian.
 enum GeoSlot {
   G_RX = 0, G_RY, G_RZ, G_SX, G_SY, G_SZ, G_TX, G_TY, G_TZ,
-  G_IEPS = 9, G_IMU = 10, G_Z = 11, G_Y = 12, G_J = 13,
+  G_IEPS = 9, G_IMU = 10, G_Z = 11, G_Y = 12, G_J = 13, G_DT = 14, // G_DT: per-element step (ensembles)
   G_STRIDE = 16
 };
 
@@ -35,6 +37,7 @@ struct StageArgs {
   int64_t K;
   float alpha;         // 1 upwind, 0 central
   float rk_a, rk_b, dt;
+  int dt_geo;          // 1: take the time step of each element from geo[k][G_DT] instead of dt
 };
 
 // Launchers, one per kernel family (defined in the .cu files).
@@ -53,6 +56,7 @@ struct GeometryArgs {
 };
 cudaError_t launch_geometry(const GeometryArgs &a, cudaStream_t s);
 cudaError_t launch_set_eps(int64_t K, const float *eps, float *geo, int *bad, cudaStream_t s);
+void ensemble_free(dg_ctx *ctx);
 cudaError_t launch_energy(int N, int64_t K, int Npad, const float *u, const float *geo, const double *M,
                           double *out, cudaStream_t s);
 
@@ -87,6 +91,7 @@ struct dg_ctx {
   double *d_red = nullptr;     // reduction outputs
   int *d_flag = nullptr;
   void *tc = nullptr;          // tensor-core operator buffers (precision != DG_FP32)
+  void *ens = nullptr;         // ensemble state (dg_ensemble_upload)
   std::vector<double> host_vert;   // VX, VY, VZ (kept for node coordinates)
   std::vector<int32_t> host_EToV;
 };

@@ -1,0 +1,136 @@
+// Persistent multi-step form of the FP32 fused stage, for ensembles of meshes.
+//
+// An ensemble of independent meshes is stored as one disjoint union (elements
+// of mesh i contiguous, neighbours always inside the same mesh, each element
+// carrying its mesh's time step in geo[k][G_DT]). One cooperative launch then
+// advances every mesh by `nsteps` LSERK4 steps: each block loops over
+// element tiles of EB elements (EB is picked by the autotuner), and a
+// grid-wide barrier separates the five stages of every step, because a stage
+// reads the neighbours' states written by the previous stage. Field loads go
+// through L2 (the L1 of another SM may hold a stale copy from two stages ago).
+#pragma once
+#include "simt_stage.cuh"
+
+namespace dgmx {
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Sense-free generation barrier over all blocks of a cooperative launch.
+// Gives up after about 2^31 cycles (~1 s) and returns false.
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *vgen = &gb->gen;
+    const unsigned int my_gen = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&gb->count, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      gb->count = 0u;
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == my_gen) {
+        if (clock64() - t0 > (1ll << 31)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct StageCoeffs {
+  float a[5], b[5];
+};
+
+// u_a holds the state at entry; stages alternate u_a -> u_b -> u_a ...
+template <int N, int EB>
+__global__ void __launch_bounds__(SimtCfg<N, EB>::NT)
+    k_ensemble_persistent(StageArgs a, StageCoeffs rk, float *u_a, float *u_b, int nsteps, GridBarrier *gb,
+                          int *err_flag) {
+  extern __shared__ float4 smem4[];
+  const int64_t ntiles = (a.K + EB - 1) / EB;
+  bool flip = false;
+  for (int step = 0; step < nsteps; ++step)
+    for (int st = 0; st < 5; ++st) {
+      a.u = flip ? u_b : u_a;
+      a.u_out = flip ? u_a : u_b;
+      a.rk_a = rk.a[st];
+      a.rk_b = rk.b[st];
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        __syncthreads(); // shared memory of the previous tile is no longer read
+        simt_stage_tile<N, MODE_LSERK, EB, true>(a, t * EB, smem4);
+      }
+      if (!grid_barrier(gb)) {
+        if (threadIdx.x == 0) atomicExch(err_flag, 1);
+        return;
+      }
+      flip = !flip;
+    }
+}
+
+} // namespace dgmx
+
+namespace dgmx {
+
+// Elements-per-block candidates of the autotuner for order N (0 = unused slot).
+template <int N>
+struct EnsembleCandidates {
+  static constexpr int NQ = Dims<N>::NQ;
+  static constexpr int c(int i) {
+    const int v = (i == 0 ? 240 : i == 1 ? 176 : i == 2 ? 128 : 80) / NQ;
+    return v < 1 ? 1 : v;
+  }
+};
+
+template <int N, int EB>
+cudaError_t launch_ensemble_eb(const StageArgs &a, const StageCoeffs &rk, float *ua, float *ub, int nsteps,
+                               GridBarrier *gb, int *flag, cudaStream_t s, int sms) {
+  using Cfg = SimtCfg<N, EB>;
+  auto kern = k_ensemble_persistent<N, EB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::SMEM));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::SMEM);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t ntiles = (a.K + EB - 1) / EB;
+  const int64_t cap = int64_t(per_sm) * sms;
+  const unsigned grid = unsigned(ntiles < cap ? ntiles : cap);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(Cfg::NT);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a, rk, ua, ub, nsteps, gb, flag);
+}
+
+template <int N>
+cudaError_t launch_ensemble_order(int cand, const StageArgs &a, const StageCoeffs &rk, float *ua, float *ub,
+                                  int nsteps, GridBarrier *gb, int *flag, cudaStream_t s, int sms) {
+  using C = EnsembleCandidates<N>;
+  switch (cand) {
+  case 0: return launch_ensemble_eb<N, C::c(0)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  case 1: return launch_ensemble_eb<N, C::c(1)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  case 2: return launch_ensemble_eb<N, C::c(2)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  default: return launch_ensemble_eb<N, C::c(3)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  }
+}
+
+} // namespace dgmx

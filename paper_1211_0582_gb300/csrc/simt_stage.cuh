@@ -22,36 +22,49 @@
 
 namespace dgmx {
 
-template <int N>
+template <int N, int EB_ = 240 / Dims<N>::NQ>
 struct SimtCfg {
   using D = Dims<N>;
-  static constexpr int EB = 240 / D::NQ;                 // elements per block
+  static constexpr int EB = EB_;                         // elements per block
   static constexpr int NT = (EB * D::NQ + 31) / 32 * 32; // threads per block
   static constexpr size_t SMEM =
       (size_t(6) * EB * D::NPP + size_t(6) * EB * D::NFF) * 4 + ((100 * D::NFP + 15) / 16) * 16;
 };
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
+// Field loads: through the read-only path for single-stage launches, or from
+// L2 (bypassing the non-coherent L1) when other blocks of the same launch wrote
+// the data in an earlier stage (persistent multi-stage kernels).
+template <bool COHERENT>
+__device__ __forceinline__ float4 load_field4(const float *p) {
+  if constexpr (COHERENT) return __ldcg(reinterpret_cast<const float4 *>(p));
+  else return ldg4(p);
+}
+template <bool COHERENT>
+__device__ __forceinline__ float load_field(const float *p) {
+  if constexpr (COHERENT) return __ldcg(p);
+  else return __ldg(p);
+}
+
+// One block-tile of EB elements starting at k0 (all threads of the block call it).
+template <int N, int MODE, int EB, bool COHERENT>
+__device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, float4 *smem4) {
   using D = Dims<N>;
-  using Cfg = SimtCfg<N>;
+  using Cfg = SimtCfg<N, EB>;
   constexpr int NP = D::NP, NFP = D::NFP, NPP = D::NPP, NQ = D::NQ, NFF = D::NFF;
-  constexpr int EB = Cfg::EB, NT = Cfg::NT;
-  extern __shared__ float4 smem4[];
+  constexpr int NT = Cfg::NT;
   float *s_u = reinterpret_cast<float *>(smem4);             // [6][EB][NPP]
   float *s_fl = s_u + 6 * EB * NPP;                          // [6][EB][NFF]
   uint8_t *s_fm = reinterpret_cast<uint8_t *>(s_fl + 6 * EB * NFF); // [NFF]
   uint8_t *s_nb = s_fm + NFF;                                // [96][NFP]
 
   const int tid = threadIdx.x;
-  const int64_t k0 = int64_t(blockIdx.x) * EB;
   const int64_t KN = a.K * NPP;
 
   for (int idx = tid; idx < 6 * EB * NQ; idx += NT) {
     int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
     int e = rem / NQ, q = rem - e * NQ;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k0 + e < a.K) v = ldg4(a.u + c * KN + (k0 + e) * NPP + 4 * q);
+    if (k0 + e < a.K) v = load_field4<COHERENT>(a.u + c * KN + (k0 + e) * NPP + 4 * q);
     reinterpret_cast<float4 *>(s_u)[(c * EB + e) * NQ + q] = v;
   }
   for (int idx = tid; idx < NFF + kConnKinds * NFP; idx += NT)
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
         int vn = s_nb[cn.y * NFP + mm];
         const float *up = a.u + int64_t(cn.x) * NPP + vn;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) qp[c] = __ldg(up + c * KN);
+        for (int c = 0; c < 6; ++c) qp[c] = load_field<COHERENT>(up + c * KN);
         Zp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Z);
         Yp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Y);
       }
@@ -166,6 +179,7 @@ __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
   if (!live) return;
   // ---- material scaling and output / operator assembly
   const float ie = __ldg(a.geo + k * G_STRIDE + G_IEPS), im = __ldg(a.geo + k * G_STRIDE + G_IMU);
+  const float dtk = a.dt_geo ? __ldg(a.geo + k * G_STRIDE + G_DT) : a.dt;
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     const float w = c < 3 ? ie : im;
@@ -176,13 +190,14 @@ __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
     if (MODE == MODE_RHS) {
       *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
     } else {
-      float4 rs = *reinterpret_cast<const float4 *>(a.res + off);
+      float4 rs = COHERENT ? __ldcg(reinterpret_cast<const float4 *>(a.res + off))
+                           : *reinterpret_cast<const float4 *>(a.res + off);
       float4 uo = reinterpret_cast<const float4 *>(s_u)[(c * EB + e) * NQ + q];
       float rv[4] = {rs.x, rs.y, rs.z, rs.w}, uv[4] = {uo.x, uo.y, uo.z, uo.w};
 #pragma unroll
       for (int n = 0; n < 4; ++n) {
         bool pad = 4 * q + n >= NP;
-        rv[n] = pad ? 0.f : fmaf(a.rk_a, rv[n], a.dt * r4[n]);
+        rv[n] = pad ? 0.f : fmaf(a.rk_a, rv[n], dtk * r4[n]);
         uv[n] = pad ? 0.f : fmaf(a.rk_b, rv[n], uv[n]);
       }
       *reinterpret_cast<float4 *>(a.res + off) = make_float4(rv[0], rv[1], rv[2], rv[3]);
@@ -190,6 +205,12 @@ __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
       if (MODE == MODE_LSERK_STORE) *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
     }
   }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
+  extern __shared__ float4 smem4[];
+  simt_stage_tile<N, MODE, SimtCfg<N>::EB, false>(a, int64_t(blockIdx.x) * SimtCfg<N>::EB, smem4);
 }
 
 template <int N>

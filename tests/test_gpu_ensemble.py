@@ -1,0 +1,95 @@
+"""GPU checks of the ensemble form: many meshes of uneven size, own materials
+and own time steps, advanced together in one persistent launch (replayed from
+a CUDA graph) must reproduce what each mesh does alone, and the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1211_0582_gb300 as dg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def members(ns, N, seed0=10):
+    out = []
+    for i, n in enumerate(ns):
+        VX, VY, VZ, EToV = W.kuhn_cube(int(n), jitter=0.1, seed=seed0 + i)
+        eps = W.element_eps(EToV.shape[0], seed=100 + i)
+        dt = 0.5 / n / N ** 2
+        out.append(((VX, VY, VZ, EToV), eps, dt))
+    return out
+
+
+def initial(s_single, i):
+    x, y, z = s_single.node_coords()
+    return W.gaussian_pulse(x, y, z, seed=7, index=i) + 0.1 * W.cavity_mode(x, y, z, 0.0)
+
+
+def run_pair(N, ns, steps):
+    mem = members(ns, N)
+    ens = dg.Solver(N).upload_ensemble([m[0] for m in mem], [m[1] for m in mem], [m[2] for m in mem])
+    off = ens.ensemble_layout()
+    singles = [dg.Solver(N).upload(*m[0], eps=m[1]) for m in mem]
+    u0 = [initial(s, i) for i, s in enumerate(singles)]
+    u = torch.cat([s.to_device(u) for s, u in zip(singles, u0)], dim=1).contiguous()
+    res = torch.zeros_like(u)
+    ens.ensemble_step(u, res, steps)
+    ens.sync()
+    outs = []
+    for i, s in enumerate(singles):
+        ud, rd = s.to_device(u0[i]), s.zeros()
+        s.step(ud, rd, mem[i][2], steps)
+        outs.append(ud)
+    torch.cuda.synchronize()
+    return ens, off, u, singles, outs, u0, mem
+
+
+@pytest.mark.parametrize("steps", [3, 2])
+def test_ensemble_matches_separate_runs(steps):
+    N = 3
+    ens, off, u, singles, outs, u0, mem = run_pair(N, [2, 4, 3], steps)
+    for i, s in enumerate(singles):
+        got = u[:, off[i]:off[i + 1]]
+        err = float((got - outs[i]).norm() / outs[i].norm())
+        assert err < 1e-6, (i, err)
+    assert ens.ensemble_graph_used()
+    best, eb, ms = ens.ensemble_tuning()
+    assert best in eb and max(ms) > 0
+
+
+def test_ensemble_member_matches_oracle():
+    N, steps = 3, 2
+    ens, off, u, singles, outs, u0, mem = run_pair(N, [3, 2], steps)
+    (VX, VY, VZ, EToV), eps, dt = mem[0]
+    m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps.astype(np.float64))
+    ref, _ = m.lserk(u0[0], dt, steps)
+    got = u[:, off[0]:off[1], :m.Np].double().cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_ensemble_full_size_sampled_members():
+    # 64 meshes of n^3 x 6 jittered tets, n uniform in {8..20}, N=4
+    N, steps = 4, 2
+    ns = W.ensemble_sizes(64, seed=3)
+    mem = members(ns, N)
+    ens = dg.Solver(N).upload_ensemble([m[0] for m in mem], [m[1] for m in mem], [m[2] for m in mem])
+    off = ens.ensemble_layout()
+    assert off[-1] == sum(6 * int(n) ** 3 for n in ns)
+    pick = [int(np.argmin(ns)), int(np.argmax(ns)), 31]
+    singles = {i: dg.Solver(N).upload(*mem[i][0], eps=mem[i][1]) for i in pick}
+    u = torch.zeros((6, int(off[-1]), ens.Npad), dtype=torch.float32, device="cuda")
+    u0 = {}
+    for i in pick:
+        u0[i] = initial(singles[i], i)
+        u[:, off[i]:off[i + 1]] = singles[i].to_device(u0[i])
+    res = torch.zeros_like(u)
+    ens.ensemble_step(u, res, steps)
+    ens.sync()
+    for i in pick:
+        s = singles[i]
+        ud, rd = s.to_device(u0[i]), s.zeros()
+        s.step(ud, rd, mem[i][2], steps)
+        err = float((u[:, off[i]:off[i + 1]] - ud).norm() / ud.norm())
+        assert err < 1e-6, (i, err)
