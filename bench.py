@@ -61,6 +61,12 @@ def bytes_per_element(N: int, Npad: int) -> float:
     return 4 * 6 * Npad * 4 + 64 + 64 + 32
 
 
+# DRAM bytes per launch of the dominant stage kernel from one ncu capture of the
+# default workload (profiles/k_stage_tc_fp16x3_n5_24cube.md); None where the
+# kernel changed since its counters were taken or none were taken.
+NCU_TRAFFIC = {("fp16x3", 5, 24): 236.589056e6 + 170.816768e6}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -287,13 +293,14 @@ def run_ours(args):
         peak_tf = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         achieved = flops_per_element(N) * K / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": args.traffic,
+                "frac": achieved / peak_tf, "traffic": args.traffic or NCU_TRAFFIC.get((args.precision, N, n)),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
     else:
         peak = peaks["hbm_gbs"]
         achieved = bytes_per_element(N, Npad) * K / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": args.traffic, "peak_source": f"hbm_gbs ({peak_kind})"}
+                "traffic": args.traffic or NCU_TRAFFIC.get((args.precision, N, n)),
+                "algorithmic_bytes": bytes_per_element(N, Npad) * K, "peak_source": f"hbm_gbs ({peak_kind})"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -316,6 +323,185 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _timed(fn, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_precision(args):
+    """Split-precision tensor-core forms vs the FP32 CUDA-core form: speed on
+    the workload mesh and relative l2 error against the FP64 oracle on a small
+    version of it (same N, same materials rule, fewer steps)."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import paper_1211_0582_gb300 as dg
+    import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    N, n = args.order, args.n
+    eps_rule = args.order >= 7
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    eps = W.element_eps(K, seed=2) if eps_rule else None
+    # error reference: the same setup on a 3^3 mesh, 10 steps, against the oracle
+    sVX, sVY, sVZ, sE = W.kuhn_cube(3, jitter=0.1, seed=1)
+    seps = W.element_eps(sE.shape[0], seed=2) if eps_rule else None
+    m = O.Mesh(N, sVX, sVY, sVZ, sE, eps=None if seps is None else seps.astype(np.float64))
+    x, y, z = m.coords()
+    su0 = W.cavity_mode(x, y, z, 0.0)
+    sdt = 0.5 / 3 / N ** 2
+    ref, _ = m.lserk(su0, sdt, 10)
+    out = {}
+    for prec in ("fp32", "bf16x3", "fp16x3"):
+        try:
+            s = dg.Solver(N, precision=prec, stream=stream).upload(VX, VY, VZ, EToV, eps=eps)
+        except dg.DGError as e:
+            out[prec] = {"unsupported": str(e)}
+            continue
+        xx, yy, zz = s.node_coords()
+        u = s.to_device(W.cavity_mode(xx, yy, zz, 0.0))
+        res = s.zeros()
+        dt = 0.5 / n / N ** 2
+        s.step(u, res, dt, args.warmup)
+        ms = _timed(lambda: s.step(u, res, dt, args.steps), stream)
+        ss = dg.Solver(N, precision=prec, stream=stream).upload(sVX, sVY, sVZ, sE, eps=seps)
+        su, sr = ss.to_device(su0), ss.zeros()
+        ss.step(su, sr, sdt, 10)
+        err = float(np.linalg.norm(ss.from_device(su) - ref) / np.linalg.norm(ref))
+        dof = 6 * s.Np * K
+        out[prec] = {"gdof_s": STAGES * dof * args.steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / args.steps,
+                     "rel_l2_vs_fp64": err}
+    fp32 = out["fp32"]["gdof_s"]
+    best = max((v["gdof_s"], k) for k, v in out.items() if "gdof_s" in v)
+    line = {"metric": METRIC, "value": best[0], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": best[1], "data": "synthetic",
+            "config": {"workload": f"precision form, {n}^3x6 jittered tets, N={N}, "
+                                   f"{'eps U[1,4] per element' if eps_rule else 'eps=mu=1'}, LSERK4",
+                       "K": K, "error_reference": "FP64 oracle, 3^3x6 version, 10 steps"},
+            "precisions": out, "speedup_vs_fp32": {k: v["gdof_s"] / fp32 for k, v in out.items() if "gdof_s" in v}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ensemble(args):
+    """64 meshes (n^3 x 6, n uniform in {8..20}), N=4, own eps and dt each,
+    Gaussian-pulse initial data: one persistent launch per call from a CUDA
+    graph vs one dg_step per mesh."""
+    import numpy as np
+    import torch
+
+    import paper_1211_0582_gb300 as dg
+    import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    N = 4
+    ns = W.ensemble_sizes(64, seed=3)
+    meshes, epss, dts = [], [], []
+    for i, n in enumerate(ns):
+        VX, VY, VZ, EToV = W.kuhn_cube(int(n), jitter=0.1, seed=10 + i)
+        meshes.append((VX, VY, VZ, EToV))
+        epss.append(W.element_eps(EToV.shape[0], seed=100 + i))
+        dts.append(0.5 / int(n) / N ** 2)
+    ens = dg.Solver(N, stream=stream).upload_ensemble(meshes, epss, dts)
+    off = ens.ensemble_layout()
+    Ktot = int(off[-1])
+    u = torch.zeros((6, Ktot, ens.Npad), dtype=torch.float32, device="cuda")
+    singles = []
+    for i, mesh in enumerate(meshes):
+        sgl = dg.Solver(N, stream=stream).upload(*mesh, eps=epss[i])
+        x, y, z = sgl.node_coords()
+        u[:, off[i]:off[i + 1]] = sgl.to_device(W.gaussian_pulse(x, y, z, seed=7, index=i))
+        singles.append(sgl)
+    res = torch.zeros_like(u)
+    ens.ensemble_tune(force=True)
+    best, ebs, tms = ens.ensemble_tuning()
+    steps = args.steps
+    ens.ensemble_step(u, res, 1)
+    ms = _timed(lambda: ens.ensemble_step(u, res, steps), stream)
+    graph = ens.ensemble_graph_used()
+    dof = 6 * ens.Np * Ktot
+    value = STAGES * dof * steps / (ms * 1e-3) / 1e9
+    # per-mesh launches of the ordinary stage kernel, same total work
+    us = [u[:, off[i]:off[i + 1]].contiguous() for i in range(len(meshes))]
+    rs = [torch.zeros_like(x) for x in us]
+    def per_mesh():
+        for i, sgl in enumerate(singles):
+            sgl.step(us[i], rs[i], dts[i], steps)
+    ms2 = _timed(per_mesh, stream)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 1,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble of 64 jittered cube meshes, n^3x6 with n in {8..20}, N=4, "
+                                   "eps U[1,4] per element, Gaussian pulse, LSERK4 with per-mesh dt",
+                       "meshes": len(meshes), "K_total": Ktot, "dof": dof},
+            "persistent_graph": {"gdof_s": value, "ms_per_step": ms / steps, "graph_replay": graph,
+                                 "launches_per_call": 1},
+            "per_mesh_launches": {"gdof_s": STAGES * dof * steps / (ms2 * 1e-3) / 1e9, "ms_per_step": ms2 / steps,
+                                  "launches_per_step": 5 * len(meshes)},
+            "autotune": {"elements_per_block": ebs, "ms_per_step": tms, "chosen": best}}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    """Adjoint workload: 20^3 x 6 jittered tets, N=4, FP32, 256 receivers,
+    checkpoints every 20 steps; adjoint-to-forward cost ratio and a finite
+    difference check along 4 directions."""
+    import numpy as np
+    import torch
+
+    import paper_1211_0582_gb300 as dg
+    import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    N, n, steps, ck = 4, 20, args.steps, 20
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    eps = W.element_eps(K, seed=2)
+    s = dg.Solver(N, stream=stream).upload(VX, VY, VZ, EToV, eps=eps)
+    x, y, z = s.node_coords()
+    u0 = s.to_device(W.gaussian_pulse(x, y, z, seed=7))
+    recv = torch.as_tensor(W.receivers(K, s.Np, 256, seed=4), device="cuda")
+    dt = 0.5 / n / N ** 2
+    epsd = torch.as_tensor(eps, device="cuda")
+    Eref = s.receiver_traces(u0, recv, dt, steps, eps=torch.as_tensor(W.element_eps(K, seed=6), device="cuda"))
+    s.set_eps(epsd)
+    uf, rf = u0.clone(), s.zeros()
+    s.step(uf, rf, dt, 3)
+    uf, rf = u0.clone(), s.zeros()
+    fwd_ms = _timed(lambda: s.step(uf, rf, dt, steps), stream)
+    out = {}
+    adj_ms = _timed(lambda: out.setdefault("r", s.adjoint(u0, recv, Eref, dt, steps, ck, eps=epsd)), stream)
+    J, g_eps, g_u0 = out["r"]
+    h = 1e-3
+    dirs = 2.0 * W.uniform(5, 4 * K).reshape(4, K) - 1.0
+    rels = []
+    for d in dirs:
+        dd = torch.as_tensor(d, dtype=torch.float64, device="cuda")
+        ep, em = (epsd.double() + h * dd).float(), (epsd.double() - h * dd).float()
+        Jp = float(((s.receiver_traces(u0, recv, dt, steps, eps=ep).double() - Eref.double()) ** 2).sum())
+        Jm = float(((s.receiver_traces(u0, recv, dt, steps, eps=em).double() - Eref.double()) ** 2).sum())
+        fd, ad = Jp - Jm, float((g_eps * (ep.double() - em.double())).sum())
+        rels.append(abs(fd - ad) / abs(fd))
+    dof = 6 * s.Np * K
+    line = {"metric": METRIC, "value": adj_ms / fwd_ms, "unit": "adjoint/forward time", "n_gpus": 1,
+            "steps": steps, "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adjoint, 20^3x6 jittered tets, N=4, 256 receivers, checkpoints every 20",
+                       "K": K, "dof": dof},
+            "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "J": J,
+            "forward_gdof_s": STAGES * dof * steps / (fwd_ms * 1e-3) / 1e9,
+            "fd_check": {"step": h, "directions": 4, "rel_diff": rels}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,6 +514,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-sample", type=int, default=50000, help="elements in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["cavity", "precision", "ensemble", "adjoint"], default="cavity",
+                    help="cavity: 24^3 N=5 LSERK4 (headline); precision: split vs FP32 error and speed; "
+                         "ensemble: 64 meshes in one persistent launch; adjoint: gradient cost and check")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the stage kernel (from a capture), if known")
     args = ap.parse_args()
@@ -335,8 +524,14 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "cavity":
         run_ours(args)
+    elif args.workload == "precision":
+        run_precision(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
+    else:
+        run_adjoint(args)
 
 
 if __name__ == "__main__":

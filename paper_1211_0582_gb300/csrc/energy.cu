@@ -1,6 +1,8 @@
 // Discrete electromagnetic energy 1/2 sum_k J_k (eps_k E^T M E + mu_k H^T M H),
 // reduced in FP64 on the device (one warp per element and field, the mass
 // matrix in shared memory, warp-shuffle reduction, one FP64 atomic per warp).
+// The row products (M q)_i are formed in FP32 (the fields are FP32); every
+// sum over nodes, fields and elements is carried in FP64.
 #include "common.cuh"
 
 namespace dgmx {
@@ -9,8 +11,8 @@ namespace {
 
 __global__ void k_energy(int Np, int Npad, int64_t K, const float *__restrict__ u, const float *__restrict__ geo,
                          const double *__restrict__ M, double *out) {
-  extern __shared__ double s_M[];
-  for (int i = threadIdx.x; i < Np * Np; i += blockDim.x) s_M[i] = M[i];
+  extern __shared__ float s_M[];
+  for (int i = threadIdx.x; i < Np * Np; i += blockDim.x) s_M[i] = float(M[i]);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
@@ -22,9 +24,9 @@ __global__ void k_energy(int Np, int Npad, int64_t K, const float *__restrict__ 
     const float *q = u + (int64_t(c) * K + k) * Npad;
     double acc = 0.0;
     for (int i = lane; i < Np; i += 32) {
-      double mi = 0.0;
-      for (int j = 0; j < Np; ++j) mi += s_M[i * Np + j] * double(q[j]);
-      acc += mi * double(q[i]);
+      float mi = 0.f;
+      for (int j = 0; j < Np; ++j) mi = fmaf(s_M[i * Np + j], __ldg(q + j), mi);
+      acc += double(mi) * double(q[i]);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const float *g = geo + k * G_STRIDE;
@@ -39,7 +41,7 @@ __global__ void k_energy(int Np, int Npad, int64_t K, const float *__restrict__ 
 cudaError_t launch_energy(int N, int64_t K, int Npad, const float *u, const float *geo, const double *M, double *out,
                           cudaStream_t s) {
   int Np = num_nodes(N);
-  size_t smem = size_t(Np) * Np * sizeof(double);
+  size_t smem = size_t(Np) * Np * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(out, 0, sizeof(double), s);
