@@ -507,6 +507,7 @@ StageArgs stage_base(const dg_ctx *c, float alpha, double dt) {
   a.geo = c->d_geo;
   a.fgeo = c->d_fgeo;
   a.fconn = c->d_fconn;
+  a.fmat = c->d_fmat;
   a.DT = c->d_DT;
   a.LT = c->d_LT;
   a.fmask = c->d_tab;

@@ -48,6 +48,7 @@ void dfree(T *&p) {
 void free_mesh(dg_ctx *c) {
   dfree(c->d_geo);
   dfree(c->d_fgeo);
+  dfree(c->d_fmat);
   dfree(c->d_fconn);
   dfree(c->d_DT);
   dfree(c->d_LT);
@@ -83,6 +84,7 @@ StageArgs base_args(const dg_ctx *c) {
   a.geo = c->d_geo;
   a.fgeo = c->d_fgeo;
   a.fconn = c->d_fconn;
+  a.fmat = c->d_fmat;
   a.DT = c->d_DT;
   a.LT = c->d_LT;
   a.fmask = c->d_tab;
@@ -215,6 +217,7 @@ int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, 
   auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
   bool ok = alloc((void **)&ctx->d_geo, size_t(K) * G_STRIDE * sizeof(float)) &&
             alloc((void **)&ctx->d_fgeo, size_t(K) * 4 * sizeof(float4)) &&
+            alloc((void **)&ctx->d_fmat, size_t(K) * 4 * sizeof(float4)) &&
             alloc((void **)&ctx->d_fconn, size_t(K) * 4 * sizeof(int2)) &&
             alloc((void **)&ctx->d_DT, DT.size() * sizeof(float)) &&
             alloc((void **)&ctx->d_LT, LT.size() * sizeof(float)) && alloc((void **)&ctx->d_tab, tab.size()) &&
@@ -257,6 +260,7 @@ int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, 
     GeometryArgs g{K, d_vert, d_vert + Nv, d_vert + 2 * Nv, d_EToV, d_eps, d_mu, ctx->d_geo, ctx->d_fgeo,
                    ctx->d_flag};
     e = launch_geometry(g, s);
+    if (e == cudaSuccess) e = launch_face_weights(K, ctx->d_geo, ctx->d_fgeo, ctx->d_fconn, ctx->d_fmat, s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_scratch, 0, field_bytes(ctx), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag + 1, 0, 15 * sizeof(int), s);
@@ -315,6 +319,8 @@ int dg_set_eps(dg_ctx *ctx, const float *eps_dev) {
   int bad_init = int(ctx->K < 0x7fffffff ? ctx->K : 0x7fffffff), bad = 0;
   cudaError_t e = cudaMemcpyAsync(ctx->d_flag, &bad_init, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = launch_set_eps(ctx->K, eps_dev, ctx->d_geo, ctx->d_flag, ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_face_weights(ctx->K, ctx->d_geo, ctx->d_fgeo, ctx->d_fconn, ctx->d_fmat, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_err(ctx, e, "dg_set_eps");

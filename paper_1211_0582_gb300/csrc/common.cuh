@@ -30,6 +30,7 @@ struct StageArgs {
   const float *geo;    // [K][16]
   const float4 *fgeo;  // [K][4] {nx, ny, nz, Fscale}
   const int2 *fconn;   // [K][4] {neighbour element, connection kind}
+  const float4 *fmat;  // [K][4] {Fscale/(Z-+Z+), -Fscale/(Y-+Y+), Z+, Y+} flux weights per face
   const float *DT;     // [3][Np][Npad]  transposed Dr, Ds, Dt
   const float *LT;     // [4Nfp][Npad]   transposed LIFT
   const uint8_t *fmask;  // [4Nfp]  volume node of each face node
@@ -56,6 +57,8 @@ struct GeometryArgs {
 };
 cudaError_t launch_geometry(const GeometryArgs &a, cudaStream_t s);
 cudaError_t launch_set_eps(int64_t K, const float *eps, float *geo, int *bad, cudaStream_t s);
+cudaError_t launch_face_weights(int64_t K, const float *geo, const float4 *fgeo, const int2 *fconn, float4 *fmat,
+                                cudaStream_t s);
 void ensemble_free(dg_ctx *ctx);
 cudaError_t launch_energy(int N, int64_t K, int Npad, const float *u, const float *geo, const double *M,
                           double *out, cudaStream_t s);
@@ -80,6 +83,7 @@ struct dg_ctx {
   // device data owned by the context
   float *d_geo = nullptr;
   float4 *d_fgeo = nullptr;
+  float4 *d_fmat = nullptr;
   int2 *d_fconn = nullptr;
   float *d_DT = nullptr;
   float *d_LT = nullptr;

@@ -127,6 +127,7 @@ StageArgs ens_args(const dg_ctx *c, float alpha) {
   a.geo = c->d_geo;
   a.fgeo = c->d_fgeo;
   a.fconn = c->d_fconn;
+  a.fmat = c->d_fmat;
   a.DT = c->d_DT;
   a.LT = c->d_LT;
   a.fmask = c->d_tab;

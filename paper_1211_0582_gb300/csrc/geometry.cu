@@ -91,7 +91,28 @@ __global__ void k_set_eps(int64_t K, const float *eps, float *geo, int *bad) {
   g[G_Y] = float(1.0 / Z);
 }
 
+__global__ void k_face_weights(int64_t K, const float *geo, const float4 *fgeo, const int2 *fconn, float4 *fmat) {
+  int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= K * 4) return;
+  const int64_t k = q >> 2;
+  const int2 cn = fconn[q];
+  const float zm = geo[k * G_STRIDE + G_Z], ym = geo[k * G_STRIDE + G_Y];
+  float zp = zm, yp = ym;
+  if (cn.y != kBoundaryConn) {
+    zp = geo[int64_t(cn.x) * G_STRIDE + G_Z];
+    yp = geo[int64_t(cn.x) * G_STRIDE + G_Y];
+  }
+  const float fs = fgeo[q].w;
+  fmat[q] = make_float4(fs / (zm + zp), -fs / (ym + yp), zp, yp);
+}
+
 } // namespace
+
+cudaError_t launch_face_weights(int64_t K, const float *geo, const float4 *fgeo, const int2 *fconn, float4 *fmat,
+                                cudaStream_t s) {
+  k_face_weights<<<unsigned((K * 4 + 255) / 256), 256, 0, s>>>(K, geo, fgeo, fconn, fmat);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_geometry(const GeometryArgs &a, cudaStream_t s) {
   unsigned blocks = unsigned((a.K + 127) / 128);

@@ -64,11 +64,14 @@ struct TC {
   static constexpr int OFF_B2H = OFF_B1L + B1B, OFF_B2L = OFF_B2H + B2B;
   static constexpr int OPS_BYTES = 2 * B1B + 2 * B2B; // contiguous from OFF_B1H
   static constexpr int OFF_U = OFF_B2L + B2B;          // fp32 [kRows][NPP]
-  static constexpr int OFF_FL = OFF_U + kRows * NPP * 4; // fp32 [kRows][NFF]
+  static constexpr int OFF_FL = OFF_U + (kRows * NPP + 24) * 4; // fp32 [kRows][NFF]
   static constexpr int OFF_TAB = OFF_FL + kRows * NFF * 4;
   static constexpr int OFF_SC = OFF_TAB + rup(NFF + kConnKinds * NFP, 16); // float [4][128]
-  static constexpr int OFF_BAR = OFF_SC + 4 * 128 * 4;
-  static constexpr int SMEM = OFF_BAR + 16;
+  static constexpr int OFF_BAR = OFF_SC + 4 * 128 * 4;   // mbarriers: MMA done, residual landed; TMEM slot
+  static constexpr int OFF_FACE = OFF_BAR + 32;          // per-tile face table [80] x 12 words
+  static constexpr int SMEM = OFF_FACE + kTileElems * 4 * 48;
+  // the residual tile [6][kTileElems * NPP + 4] reuses the flux staging
+  static_assert(6 * (kTileElems * NPP + 4) <= kRows * NFF, "residual tile does not fit in the flux staging");
 };
 
 struct TcState {
@@ -106,13 +109,20 @@ __device__ __forceinline__ int compact_row(int r) {
   return l < 30 ? (r >> 5) * 30 + l : -1;
 }
 
-// Split the FP32 staging rows [120][ld] (first `cols` columns) into the hi/lo
-// K-major operands, scaled per row. Work items are ordered so that each
-// half-warp writes one 128-byte core matrix (8 rows x 16 bytes): conflict-free
-// shared stores. Padding positions are never written (they stay zero).
-template <bool BF16>
+// Compact row (6 e + f) -> float offset of that row in the field-major
+// staging, whose field blocks are padded by 4 floats so that the six field
+// rows of one element fall in different shared-memory banks.
+template <int NPP>
+__device__ __forceinline__ int staged_off(int cr) { return (cr % 6) * (kTileElems * NPP + 4) + (cr / 6) * NPP; }
+
+// Split the FP32 staging rows (compact rows 0..119; row-major with stride ld,
+// or the field-major staging) into the hi/lo K-major operands, scaled per row.
+// Work items are ordered so that each half-warp writes one 128-byte core matrix
+// (8 rows x 16 bytes): conflict-free shared stores. Padding positions are never
+// written (they stay zero).
+template <bool BF16, bool FIELD_MAJOR, int NPP = 4>
 __device__ __forceinline__ void convert_rows(const float *src, int ld, int cols, int Kp, const float *scale,
-                                             uint8_t *dst_hi, uint8_t *dst_lo, int tid) {
+                                             uint8_t *dst_hi, uint8_t *dst_lo, int tid, int valid) {
   const int kgroups = Kp / 8;
   const int units = 128 * kgroups * 2;
   for (int u = tid; u < units; u += kThreads) {
@@ -122,9 +132,16 @@ __device__ __forceinline__ void convert_rows(const float *src, int ld, int cols,
     const int r = 8 * g + rr, k = 8 * kg + 4 * qh;
     const int cr = compact_row(r);
     if (cr < 0 || k >= cols) continue;
-    float4 v = *reinterpret_cast<const float4 *>(src + cr * ld + k);
+    const int sr = cr; // scales are indexed by compact row
+    float4 v = *reinterpret_cast<const float4 *>(src + (FIELD_MAJOR ? staged_off<NPP>(cr) : cr * ld) + k);
+    if (k + 3 >= valid) {
+      if (k + 0 >= valid) v.x = 0.f;
+      if (k + 1 >= valid) v.y = 0.f;
+      if (k + 2 >= valid) v.z = 0.f;
+      if (k + 3 >= valid) v.w = 0.f;
+    }
     if constexpr (!BF16) {
-      const float sc = scale[cr];
+      const float sc = scale[sr];
       v.x *= sc, v.y *= sc, v.z *= sc, v.w *= sc;
     }
     uint2 hi, lo;
@@ -187,20 +204,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   using T = TC<N>;
   constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, NQ = T::NQ;
   extern __shared__ __align__(1024) uint8_t smem[];
+  // field-major staging [6][kTileElems][NPP]: the tile's fields, updated in place
   float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);
+  // flux staging [120][NFF] (compact rows), then the residual (or rhs) tile [6][kTileElems][NPP]
   float *s_fl = reinterpret_cast<float *>(smem + T::OFF_FL);
+  float *s_res = s_fl;
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
-  float *s_sc1 = reinterpret_cast<float *>(smem + T::OFF_SC); // [128] scale, inverse at +128
-  float *s_sc2 = s_sc1 + 256;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 8);
+  float *s_sc1 = reinterpret_cast<float *>(smem + T::OFF_SC); // staged rows: scale, inverse at +128
+  float *s_sc2 = s_sc1 + 256;                                 // compact rows
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // MMA completion
+  uint64_t *barR = bar + 1;                                        // residual tile landed
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 16);
+  float4 *s_face = reinterpret_cast<float4 *>(smem + T::OFF_FACE); // [80][3]: {n, Fs}, {wE, wH, Z+, Y+}, {k2, conn}
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t KN = a.K * NPP;
   const uint32_t sbase = umma::smem_u32(smem);
 
-  // warm L2 with everything a tile streams from HBM (fields, residual, geometry)
   auto prefetch_tile = [&](int t) {
     if (t >= ntiles) return;
     const int64_t kb = int64_t(t) * kTileElems;
@@ -212,11 +233,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     prefetch_l2(a.fconn + kb * 4, uint32_t(ne * 4 * sizeof(int2)));
     prefetch_l2(a.fgeo + kb * 4, uint32_t(ne * 4 * sizeof(float4)));
+    prefetch_l2(a.fmat + kb * 4, uint32_t(ne * 4 * sizeof(float4)));
     prefetch_l2(a.geo + kb * G_STRIDE, uint32_t(ne * G_STRIDE * 4));
   };
 
-  // ---- one-time setup: zero the A operands (padding rows/columns stay zero),
-  // load the resident operators and the face tables, allocate TMEM.
+  // ---- one-time setup
   for (int i = tid; i < (2 * T::A1B + 2 * T::A2B) / 16; i += kThreads)
     reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < T::OPS_BYTES / 16; i += kThreads)
@@ -226,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int i = tid; i < 512; i += kThreads) s_sc1[i] = 1.f;
   if (tid == 0) {
     umma::mbar_init(bar, 1);
+    umma::mbar_init(barR, 1);
     umma::fence_mbar_init();
     prefetch_tile(blockIdx.x);
   }
@@ -236,7 +258,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
 
-  // epilogue roles: TMEM lane quarter (warp % 4) and node-chunk part (warp / 4)
   const int quarter = warp & 3, part = warp >> 2;
   const bool lane_used = lane < 30;
   const int ep = lane_used ? lane / 6 : 4;
@@ -248,19 +269,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int dl1 = (comp + 2) % 3, dl2 = (comp + 1) % 3;
   const int e_loc = quarter * 5 + ep;
   const int ridx = e_loc * 6 + fld;
+  constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staging
+  const int soff = fld * FS + e_loc * NPP; // this lane's row in the staging
   const uint32_t lane_taddr = tmem + (uint32_t(quarter * 32) << 16);
-  constexpr int NCH = (NP + 7) / 8; // 8-node chunks per row
-  constexpr int CPP = (NCH + 3) / 4; // chunks per part
+  constexpr int NCH = (NP + 7) / 8;
+  constexpr int CPP = (NCH + 3) / 4;
   const int ch0 = part * CPP;
   const int ch1 = (part + 1) * CPP < NCH ? (part + 1) * CPP : NCH;
 
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t k0 = int64_t(tile) * kTileElems;
+    const int ne = int(a.K - k0 < kTileElems ? a.K - k0 : kTileElems);
     if (tid == 0) prefetch_tile(tile + gridDim.x);
 
-    // ---- 1. stage the tile's fields in shared memory (FP32, pads zeroed);
-    // all loads of a thread are issued before any store
+    // ---- 1. face table and fields of the tile (loads first, then, once the
+    // previous tile's bulk stores have read shared memory, the stores)
     {
       constexpr int TOT = 6 * kTileElems * NQ;
       constexpr int IT = (TOT + kThreads - 1) / kThreads;
@@ -272,15 +296,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (idx < TOT) {
           const int f = idx / (kTileElems * NQ), rem = idx - f * (kTileElems * NQ);
           const int e = rem / NQ, q = rem - e * NQ;
-          if (k0 + e < a.K) v[s] = ldg4(a.u + f * KN + (k0 + e) * NPP + 4 * q);
+          if (e < ne) v[s] = ldg4(a.u + f * KN + (k0 + e) * NPP + 4 * q);
         }
+      }
+      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(0.f, 0.f, 1.f, 1.f);
+      int2 cn = make_int2(0, kBoundaryConn);
+      if (tid < kTileElems * 4 && (tid >> 2) < ne) {
+        const int64_t q = (k0 + (tid >> 2)) * 4 + (tid & 3);
+        cn = __ldg(a.fconn + q);
+        r0 = __ldg(a.fgeo + q);
+        r1 = __ldg(a.fmat + q);
+      }
+      if (tid == 0) umma::bulk_wait_read_all();
+      __syncthreads();
+      if (tid < kTileElems * 4) {
+        s_face[tid * 3 + 0] = r0;
+        s_face[tid * 3 + 1] = r1;
+        s_face[tid * 3 + 2] = make_float4(__int_as_float(cn.x), __int_as_float(cn.y), 0.f, 0.f);
       }
 #pragma unroll
       for (int s = 0; s < IT; ++s) {
         const int idx = tid + s * kThreads;
         if (idx < TOT) {
-          const int f = idx / (kTileElems * NQ), rem = idx - f * (kTileElems * NQ);
-          const int e = rem / NQ, q = rem - e * NQ;
+          const int q = idx % NQ;
           float4 w = v[s];
           if (4 * q + 3 >= NP) {
             if (4 * q + 0 >= NP) w.x = 0.f;
@@ -288,7 +326,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (4 * q + 2 >= NP) w.z = 0.f;
             if (4 * q + 3 >= NP) w.w = 0.f;
           }
-          reinterpret_cast<float4 *>(s_u)[(e * 6 + f) * NQ + q] = w;
+          const int f = idx / (kTileElems * NQ), eq = idx - f * (kTileElems * NQ);
+          *reinterpret_cast<float4 *>(s_u + f * FS + 4 * eq) = w;
         }
       }
     }
@@ -296,11 +335,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // ---- 2. split into the A1 operand (hi/lo), row-scaled for FP16
     if constexpr (!BF16) {
-      const float mx = row_absmax4(s_u, NPP, NP, tid);
-      if ((tid & 3) == 0 && (tid >> 2) < kRows) row_scale(mx, s_sc1[tid >> 2], s_sc1[128 + (tid >> 2)]);
+      const int r = tid >> 2, pt = tid & 3;
+      float mx = 0.f;
+      if (r < kRows)
+        for (int j = pt; j < NP; j += 4) mx = fmaxf(mx, fabsf(s_u[staged_off<NPP>(r) + j]));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      if (pt == 0 && r < kRows) row_scale(mx, s_sc1[r], s_sc1[128 + r]);
       __syncthreads();
     }
-    convert_rows<BF16>(s_u, NPP, NPP, T::K1, s_sc1, smem + T::OFF_A1H, smem + T::OFF_A1L, tid);
+    convert_rows<BF16, true, NPP>(s_u, NPP, NPP, T::K1, s_sc1, smem + T::OFF_A1H, smem + T::OFF_A1L, tid, NP);
     umma::fence_proxy_async();
     __syncthreads();
 
@@ -311,67 +355,60 @@ __global__ void __launch_bounds__(kThreads, 1)
                              T::K1, T::N1);
     }
 
-    // ---- 4. flux gather (overlaps GEMM1): interior trace from shared memory,
-    // exterior trace from the neighbour's row, PEC mirror on walls. Loads of
-    // all items of a thread are issued before the arithmetic.
+    // ---- 4. flux gather (overlaps GEMM1)
     {
       constexpr int TOT = kTileElems * NFF;
       constexpr int IT = (TOT + kThreads - 1) / kThreads;
-      int2 cn[IT];
-      float4 nf[IT];
-      float zm[IT], ym[IT];
-#pragma unroll
-      for (int s = 0; s < IT; ++s) {
-        const int it = tid + s * kThreads;
-        const int e = it / NFF, fm = it - e * NFF, f = fm / NFP;
-        const int64_t k = k0 + e;
-        cn[s] = make_int2(0, kBoundaryConn);
-        nf[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        zm[s] = 1.f, ym[s] = 1.f;
-        if (it < TOT && k < a.K) {
-          cn[s] = __ldg(a.fconn + k * 4 + f);
-          nf[s] = __ldg(a.fgeo + k * 4 + f);
-          zm[s] = __ldg(a.geo + k * G_STRIDE + G_Z);
-          ym[s] = __ldg(a.geo + k * G_STRIDE + G_Y);
-        }
-      }
-      float qp[IT][6], zp[IT], yp[IT];
+      float qp[IT][6];
 #pragma unroll
       for (int s = 0; s < IT; ++s) {
         const int it = tid + s * kThreads;
         const int e = it / NFF, fm = it - e * NFF, f = fm / NFP, mm = fm - f * NFP;
-        zp[s] = zm[s], yp[s] = ym[s];
-        if (it < TOT && k0 + e < a.K && cn[s].y != kBoundaryConn) {
-          const int vn = s_nb[cn[s].y * NFP + mm];
-          const float *up = a.u + int64_t(cn[s].x) * NPP + vn;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) qp[s][c] = __ldg(up + c * KN);
-          zp[s] = __ldg(a.geo + int64_t(cn[s].x) * G_STRIDE + G_Z);
-          yp[s] = __ldg(a.geo + int64_t(cn[s].x) * G_STRIDE + G_Y);
-        } else {
+        for (int c = 0; c < 6; ++c) qp[s][c] = 0.f;
+        if (it < TOT && e < ne) {
+          const float4 r2 = s_face[(e * 4 + f) * 3 + 2];
+          const int conn = __float_as_int(r2.y);
+          if (conn != kBoundaryConn) {
+            const float *up = a.u + int64_t(__float_as_int(r2.x)) * NPP + s_nb[conn * NFP + mm];
 #pragma unroll
-          for (int c = 0; c < 6; ++c) qp[s][c] = 0.f;
+            for (int c = 0; c < 6; ++c) qp[s][c] = __ldg(up + c * KN);
+          }
         }
       }
 #pragma unroll
       for (int s = 0; s < IT; ++s) {
         const int it = tid + s * kThreads;
         if (it >= TOT) continue;
-        const int e = it / NFF, fm = it - e * NFF;
+        const int e = it / NFF, fm = it - e * NFF, f = fm / NFP;
         float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (k0 + e < a.K) {
+        if (e < ne) {
+          const float4 r0 = s_face[(e * 4 + f) * 3 + 0], r1 = s_face[(e * 4 + f) * 3 + 1];
+          const bool wall = __float_as_int(s_face[(e * 4 + f) * 3 + 2].y) == kBoundaryConn;
           const int vm = s_fm[fm];
           float qm[6];
 #pragma unroll
-          for (int c = 0; c < 6; ++c) qm[c] = s_u[(e * 6 + c) * NPP + vm];
-          if (cn[s].y == kBoundaryConn) {
+          for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
+          if (wall) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               qp[s][c] = -qm[c];
               qp[s][c + 3] = qm[c + 3];
             }
           }
-          maxwell_flux(nf[s], qm, qp[s], zm[s], zp[s], ym[s], yp[s], a.alpha, fl);
+          const float nx = r0.x, ny = r0.y, nz = r0.z;
+          const float dEx = qp[s][0] - qm[0], dEy = qp[s][1] - qm[1], dEz = qp[s][2] - qm[2];
+          const float dHx = qp[s][3] - qm[3], dHy = qp[s][4] - qm[4], dHz = qp[s][5] - qm[5];
+          const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
+          const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
+          float vx = r1.z * dHx - a.alpha * cEx, vy = r1.z * dHy - a.alpha * cEy, vz = r1.z * dHz - a.alpha * cEz;
+          fl[0] = r1.x * (ny * vz - nz * vy);
+          fl[1] = r1.x * (nz * vx - nx * vz);
+          fl[2] = r1.x * (nx * vy - ny * vx);
+          vx = r1.w * dEx + a.alpha * cHx, vy = r1.w * dEy + a.alpha * cHy, vz = r1.w * dEz + a.alpha * cHz;
+          fl[3] = r1.y * (ny * vz - nz * vy);
+          fl[4] = r1.y * (nz * vx - nx * vz);
+          fl[5] = r1.y * (nx * vy - ny * vx);
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) s_fl[(e * 6 + c) * NFF + fm] = fl[c];
@@ -385,9 +422,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if ((tid & 3) == 0 && (tid >> 2) < kRows) row_scale(mx, s_sc2[tid >> 2], s_sc2[128 + (tid >> 2)]);
       __syncthreads();
     }
-    convert_rows<BF16>(s_fl, NFF, NFF, T::K2, s_sc2, smem + T::OFF_A2H, smem + T::OFF_A2L, tid);
+    convert_rows<BF16, false>(s_fl, NFF, NFF, T::K2, s_sc2, smem + T::OFF_A2H, smem + T::OFF_A2L, tid, NFF);
     umma::fence_proxy_async();
     __syncthreads();
+    // the flux staging is free: the residual tile lands there during GEMM2
+    if (MODE == MODE_LSERK && tid == 0) {
+      const uint32_t rowbytes = uint32_t(ne * NPP * 4);
+      umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
+      for (int f = 0; f < 6; ++f)
+        umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
+    }
 
     // ---- 6. flux lifting on the tensor cores, then wait for both products
     if (tid == 0) {
@@ -396,38 +440,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                              sbase + T::OFF_B2L, T::K2, T::N2);
       umma::commit(bar);
     }
-    // residual of this thread's chunks, loaded while the products run
     const int64_t k = k0 + e_loc;
-    const bool live = lane_used && k < a.K;
-    float4 rres[2 * CPP];
-#pragma unroll
-    for (int c = 0; c < CPP; ++c)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        rres[2 * c + h] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int i = (ch0 + c) * 8 + 4 * h;
-        if (MODE == MODE_LSERK && live && ch0 + c < ch1 && i < NPP)
-          rres[2 * c + h] = *reinterpret_cast<const float4 *>(a.res + fld * KN + k * NPP + i);
-      }
+    const bool live = lane_used && e_loc < ne;
     float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f;
     if (live) {
       const float *g = a.geo + k * G_STRIDE;
-      // d/dx_l = (dr/dx_l) d/dr + (ds/dx_l) d/ds + (dt/dx_l) d/dt
       g1r = __ldg(g + G_RX + dl1), g1s = __ldg(g + G_SX + dl1), g1t = __ldg(g + G_TX + dl1);
       g2r = __ldg(g + G_RX + dl2), g2s = __ldg(g + G_SX + dl2), g2t = __ldg(g + G_TX + dl2);
       w = __ldg(g + (isE ? G_IEPS : G_IMU));
     }
     const float inv1 = BF16 ? 1.f : s_sc1[128 + (lane_used ? ridx : 0)];
     const float inv2 = BF16 ? 1.f : s_sc2[128 + (lane_used ? ridx : 0)];
-    const bool ok = umma::mbar_wait_bounded(bar, phase);
+    bool ok = umma::mbar_wait_bounded(bar, phase);
+    if (MODE == MODE_LSERK) ok = umma::mbar_wait_bounded(barR, phase) && ok;
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicExch(err_flag, 1);
+      if (tid == 0) {
+        atomicExch(err_flag, 1);
+        // give the products and the residual copy in flight one more bounded
+        // wait before tensor and shared memory are released
+        umma::mbar_wait_bounded(bar, phase ^ 1u);
+        if (MODE == MODE_LSERK) umma::mbar_wait_bounded(barR, phase ^ 1u);
+      }
       break;
     }
     umma::fence_after_sync();
 
-    // ---- 7. epilogue: chain rule, curls, lifting, material scale, update
+    // ---- 7. epilogue: chain rule, curls, lifting, material scale; the update
+    // is written in place into the staged tiles
 #pragma unroll
     for (int c = 0; c < CPP; ++c) {
       const int ch = ch0 + c;
@@ -458,12 +498,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             float r4[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? rv[4 * h + q] : 0.f;
-            const int64_t off = fld * KN + k * NPP + i;
+            float4 *rp = reinterpret_cast<float4 *>(s_res + soff + i);
             if (MODE == MODE_RHS) {
-              *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+              *rp = make_float4(r4[0], r4[1], r4[2], r4[3]);
             } else {
-              const float4 rs = rres[2 * c + h];
-              const float4 uo = *reinterpret_cast<const float4 *>(s_u + ridx * NPP + i);
+              float4 *up = reinterpret_cast<float4 *>(s_u + soff + i);
+              const float4 rs = *rp, uo = *up;
               const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
               float nr[4], nu[4];
 #pragma unroll
@@ -472,16 +512,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[q], a.dt * r4[q]);
                 nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
               }
-              *reinterpret_cast<float4 *>(a.res + off) = make_float4(nr[0], nr[1], nr[2], nr[3]);
-              *reinterpret_cast<float4 *>(a.u_out + off) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+              *rp = make_float4(nr[0], nr[1], nr[2], nr[3]);
+              *up = make_float4(nu[0], nu[1], nu[2], nu[3]);
             }
           }
         }
       }
     }
+    umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
+    // ---- 8. write the tile back with asynchronous bulk stores
+    if (tid == 0) {
+      const uint32_t rowbytes = uint32_t(ne * NPP * 4);
+      for (int f = 0; f < 6; ++f) {
+        if (MODE == MODE_RHS) {
+          umma::bulk_s2g(a.rhs + f * KN + k0 * NPP, s_res + f * FS, rowbytes);
+        } else {
+          umma::bulk_s2g(a.res + f * KN + k0 * NPP, s_res + f * FS, rowbytes);
+          umma::bulk_s2g(a.u_out + f * KN + k0 * NPP, s_u + f * FS, rowbytes);
+        }
+      }
+      umma::bulk_commit();
+    }
   }
+  if (tid == 0) umma::bulk_wait_all();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, T::TCOLS);
 }
