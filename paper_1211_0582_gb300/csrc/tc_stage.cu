@@ -39,7 +39,6 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kTileElems = 20; // 4 TMEM lane quarters x 5 elements
-constexpr int kRows = 120;     // (element, field) rows actually used per tile
 constexpr int kMaxTcOrder = 5;
 
 __host__ __device__ constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
@@ -50,28 +49,39 @@ __host__ __device__ constexpr int tmem_cols(int x) {
 template <int N>
 struct TC {
   using D = Dims<N>;
-  static constexpr int NP = D::NP, NFP = D::NFP, NPP = D::NPP, NFF = D::NFF, NQ = D::NQ;
+  static constexpr int NP = D::NP, NFP = D::NFP, NPP = D::NPP, NFF = D::NFF;
   static constexpr int K1 = rup(NP, 16);  // GEMM1 reduction length (input nodes)
   static constexpr int NB = rup(NP, 16);  // output columns per derivative direction
   static constexpr int N1 = 3 * NB;       // GEMM1 output columns
   static constexpr int K2 = rup(NFF, 16); // GEMM2 reduction length (face nodes)
   static constexpr int N2 = NB;           // GEMM2 output columns
   static constexpr int TCOLS = tmem_cols(N1 + N2);
+  static constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staged tiles
   static constexpr int A1B = 128 * K1 * 2, A2B = 128 * K2 * 2, B1B = N1 * K1 * 2, B2B = N2 * K2 * 2;
+  // A1 hi/lo; between the differentiation GEMM of one tile and the field
+  // split of the next, the same bytes receive the next tile's fields
   static constexpr int OFF_A1H = 0, OFF_A1L = OFF_A1H + A1B;
+  // A2 hi/lo; between the lifting GEMM of one tile and the flux split of the
+  // next, the same bytes hold the tile's results [2][6][FS] for the bulk stores
+  static constexpr int OUTB = 12 * FS * 4;
+  static constexpr int A2R = 2 * A2B > OUTB ? 2 * A2B : OUTB;
   static constexpr int OFF_A2H = OFF_A1L + A1B, OFF_A2L = OFF_A2H + A2B;
-  static constexpr int OFF_B1H = OFF_A2L + A2B, OFF_B1L = OFF_B1H + B1B;
+  static constexpr int OFF_B1H = OFF_A2H + A2R, OFF_B1L = OFF_B1H + B1B;
   static constexpr int OFF_B2H = OFF_B1L + B1B, OFF_B2L = OFF_B2H + B2B;
   static constexpr int OPS_BYTES = 2 * B1B + 2 * B2B; // contiguous from OFF_B1H
-  static constexpr int OFF_U = OFF_B2L + B2B;          // fp32 [kRows][NPP]
-  static constexpr int OFF_FL = OFF_U + (kRows * NPP + 24) * 4; // fp32 [kRows][NFF]
-  static constexpr int OFF_TAB = OFF_FL + kRows * NFF * 4;
-  static constexpr int OFF_SC = OFF_TAB + rup(NFF + kConnKinds * NFP, 16); // float [4][128]
-  static constexpr int OFF_BAR = OFF_SC + 4 * 128 * 4;   // mbarriers: MMA done, residual landed; TMEM slot
-  static constexpr int OFF_FACE = OFF_BAR + 32;          // per-tile face table [80] x 12 words
-  static constexpr int SMEM = OFF_FACE + kTileElems * 4 * 48;
-  // the residual tile [6][kTileElems * NPP + 4] reuses the flux staging
-  static_assert(6 * (kTileElems * NPP + 4) <= kRows * NFF, "residual tile does not fit in the flux staging");
+  static constexpr int OFF_U = OFF_B2L + B2B;          // fp32 [6][FS]: fields of the tile
+  static constexpr int OFF_RES = OFF_U + 6 * FS * 4;   // fp32 [6][FS]: residual of the tile
+  // face and element data of a tile, two slots (current tile, next tile):
+  // float4 fgeo[80] {n, Fscale}, float4 fmat[80] flux weights,
+  // float geo[20][G_STRIDE], int2 fconn[80]
+  static constexpr int FGEO = 0, FMAT = kTileElems * 4 * 16, FELEM = 2 * kTileElems * 4 * 16;
+  static constexpr int FCONN = FELEM + kTileElems * G_STRIDE * 4, FSLOT = FCONN + kTileElems * 4 * 8;
+  static constexpr int OFF_FACE = OFF_RES + 6 * FS * 4;
+  static constexpr int OFF_TAB = OFF_FACE + 2 * FSLOT;
+  static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16); // [128] A1 row inverse scales, [8] A2 field maxima
+  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32; // mbarriers: GEMM1, GEMM2, residual, next tile; TMEM slot
+  static constexpr int SMEM = OFF_BAR + 48;
+  static_assert(6 * FS * 4 <= 2 * A1B, "the staged fields do not fit in the A1 operand");
 };
 
 struct TcState {
@@ -79,80 +89,42 @@ struct TcState {
   int sms = 0;
 };
 
-template <bool BF16>
-__device__ __forceinline__ void split4(float4 v, uint2 &hi, uint2 &lo) {
-  if constexpr (BF16) {
-    __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
-    float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-    __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y), l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
-    hi = make_uint2(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1));
-    lo = make_uint2(*reinterpret_cast<uint32_t *>(&l0), *reinterpret_cast<uint32_t *>(&l1));
-  } else {
-    __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
-    float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-    __half2 l0 = __floats2half2_rn(v.x - f0.x, v.y - f0.y), l1 = __floats2half2_rn(v.z - f1.x, v.w - f1.y);
-    hi = make_uint2(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1));
-    lo = make_uint2(*reinterpret_cast<uint32_t *>(&l0), *reinterpret_cast<uint32_t *>(&l1));
-  }
+// Round-to-nearest-even of a finite FP32 bit pattern to 23 - DROP explicit
+// mantissa bits (low DROP bits cleared), by integer arithmetic on the
+// sign-magnitude encoding; a carry into the exponent is the correct rounding.
+template <int DROP>
+__device__ __forceinline__ uint32_t rne_bits(uint32_t u) {
+  return (u + ((1u << (DROP - 1)) - 1u) + ((u >> DROP) & 1u)) & ~((1u << DROP) - 1u);
 }
 
-// Warm L2 with [p, p + bytes) (bytes a multiple of 16, p 16-byte aligned).
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-  if (bytes == 0) return;
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+// hi/lo split of two FP32 values into packed 16-bit pairs (x0 in the low half).
+// BF16: hi by a rounding conversion, widened back by a shift (BF16 is the top
+// half of FP32); lo = x - hi is exact in FP32 and converted with rounding.
+// FP16: hi is rounded to 11 significant bits (exact in FP16 for |x| >= 2^-14;
+// below that the conversion rounds it to the subnormal grid, an error of at
+// most 2^-25), lo = x - hi is exact in FP32 and converted with rounding.
+template <bool BF16>
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  if constexpr (BF16) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
+    hi = *reinterpret_cast<const uint32_t *>(&hh);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - h0, x1 - h1);
+    lo = *reinterpret_cast<const uint32_t *>(&ll);
+  } else {
+    const float h0 = __uint_as_float(rne_bits<13>(__float_as_uint(x0)));
+    const float h1 = __uint_as_float(rne_bits<13>(__float_as_uint(x1)));
+    const __half2 hh = __floats2half2_rn(h0, h1), ll = __floats2half2_rn(x0 - h0, x1 - h1);
+    hi = *reinterpret_cast<const uint32_t *>(&hh);
+    lo = *reinterpret_cast<const uint32_t *>(&ll);
+  }
 }
 
 // Operand row (32 * quarter + lane) -> compact row (6 e + f), or -1 for the
 // two unused lanes of each quarter.
-__device__ __forceinline__ int compact_row(int r) {
-  const int l = r & 31;
-  return l < 30 ? (r >> 5) * 30 + l : -1;
-}
+__host__ __device__ constexpr int compact_row(int r) { return (r & 31) < 30 ? (r >> 5) * 30 + (r & 31) : -1; }
 
-// Compact row (6 e + f) -> float offset of that row in the field-major
-// staging, whose field blocks are padded by 4 floats so that the six field
-// rows of one element fall in different shared-memory banks.
-template <int NPP>
-__device__ __forceinline__ int staged_off(int cr) { return (cr % 6) * (kTileElems * NPP + 4) + (cr / 6) * NPP; }
-
-// Split the FP32 staging rows (compact rows 0..119; row-major with stride ld,
-// or the field-major staging) into the hi/lo K-major operands, scaled per row.
-// Work items are ordered so that each half-warp writes one 128-byte core matrix
-// (8 rows x 16 bytes): conflict-free shared stores. Padding positions are never
-// written (they stay zero).
-template <bool BF16, bool FIELD_MAJOR, int NPP = 4>
-__device__ __forceinline__ void convert_rows(const float *src, int ld, int cols, int Kp, const float *scale,
-                                             uint8_t *dst_hi, uint8_t *dst_lo, int tid, int valid) {
-  const int kgroups = Kp / 8;
-  const int units = 128 * kgroups * 2;
-  for (int u = tid; u < units; u += kThreads) {
-    const int rr = u & 7, qh = (u >> 3) & 1;
-    const int rest = u >> 4;
-    const int kg = rest % kgroups, g = rest / kgroups;
-    const int r = 8 * g + rr, k = 8 * kg + 4 * qh;
-    const int cr = compact_row(r);
-    if (cr < 0 || k >= cols) continue;
-    const int sr = cr; // scales are indexed by compact row
-    float4 v = *reinterpret_cast<const float4 *>(src + (FIELD_MAJOR ? staged_off<NPP>(cr) : cr * ld) + k);
-    if (k + 3 >= valid) {
-      if (k + 0 >= valid) v.x = 0.f;
-      if (k + 1 >= valid) v.y = 0.f;
-      if (k + 2 >= valid) v.z = 0.f;
-      if (k + 3 >= valid) v.w = 0.f;
-    }
-    if constexpr (!BF16) {
-      const float sc = scale[sr];
-      v.x *= sc, v.y *= sc, v.z *= sc, v.w *= sc;
-    }
-    uint2 hi, lo;
-    split4<BF16>(v, hi, lo);
-    const uint32_t off = umma::kmajor_offset(uint32_t(r), uint32_t(k), uint32_t(Kp));
-    *reinterpret_cast<uint2 *>(dst_hi + off) = hi;
-    *reinterpret_cast<uint2 *>(dst_lo + off) = lo;
-  }
-}
-
-// Power-of-two scale bringing a row maximum mx (>= 0) into [0.5, 1) and its
+// Power-of-two scale bringing a maximum mx (>= 0) into [0.5, 1) and its
 // inverse, from the exponent field of mx (FP16 range guard). Zero, subnormal
 // or non-finite maxima give scale 1.
 __device__ __forceinline__ void row_scale(float mx, float &scale, float &inv) {
@@ -166,34 +138,30 @@ __device__ __forceinline__ void row_scale(float mx, float &scale, float &inv) {
   inv = __uint_as_float((ex + 1u) << 23);
 }
 
-// Maximum of |row| over `len` FP32 values, 4 threads per row (row = tid / 4
-// for tid < 4 * kRows), combined with shuffles inside the 4-lane group.
-__device__ __forceinline__ float row_absmax4(const float *rows, int ld, int len, int tid) {
-  const int r = tid >> 2, part = tid & 3;
-  float mx = 0.f;
-  if (r < kRows)
-    for (int j = part; j < len; j += 4) mx = fmaxf(mx, fabsf(rows[r * ld + j]));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-  return mx;
+__device__ __forceinline__ float absmax4(float m, float4 v) {
+  return fmaxf(fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
 }
 
 // Three split products per K step: hi*hi, hi*lo, lo*hi, FP32 accumulation.
-template <bool BF16>
+// Fully unrolled; the operand descriptors are formed once and advanced along K
+// by adding to their start-address field (256 bytes = 16 in units of 16 bytes;
+// shared-memory addresses stay below 2^18, so the field never carries out).
+template <bool BF16, int KP, int NR>
 __device__ __forceinline__ void issue_split_gemm(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                                 uint32_t b_lo, int Kp, int Nrows) {
-  const uint32_t sbo = uint32_t(Kp) * 16u;
-  for (int n0 = 0; n0 < Nrows; n0 += 256) {
-    const int nl = Nrows - n0 < 256 ? Nrows - n0 : 256;
-    const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(nl));
+                                                 uint32_t b_lo) {
+  constexpr uint32_t sbo = uint32_t(KP) * 16u;
+  const uint64_t dah = umma::make_desc(a_hi, 128, sbo), dal = umma::make_desc(a_lo, 128, sbo);
+#pragma unroll
+  for (int n0 = 0; n0 < NR; n0 += 256) {
+    const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NR - n0 < 256 ? NR - n0 : 256));
     const uint32_t boff = uint32_t(n0 / 8) * sbo;
-    for (int kk = 0; kk < Kp / 16; ++kk) {
-      const uint32_t ko = uint32_t(kk) * 256u;
-      const uint64_t ah = umma::make_desc(a_hi + ko, 128, sbo), al = umma::make_desc(a_lo + ko, 128, sbo);
-      const uint64_t bh = umma::make_desc(b_hi + boff + ko, 128, sbo), bl = umma::make_desc(b_lo + boff + ko, 128, sbo);
-      umma::mma_f16(d_tmem + uint32_t(n0), ah, bh, idesc, kk > 0 ? 1u : 0u);
-      umma::mma_f16(d_tmem + uint32_t(n0), ah, bl, idesc, 1u);
-      umma::mma_f16(d_tmem + uint32_t(n0), al, bh, idesc, 1u);
+    const uint64_t dbh = umma::make_desc(b_hi + boff, 128, sbo), dbl = umma::make_desc(b_lo + boff, 128, sbo);
+#pragma unroll
+    for (int kk = 0; kk < KP / 16; ++kk) {
+      const uint64_t ko = uint64_t(kk) * 16u;
+      umma::mma_f16(d_tmem + uint32_t(n0), dah + ko, dbh + ko, idesc, kk > 0 ? 1u : 0u);
+      umma::mma_f16(d_tmem + uint32_t(n0), dah + ko, dbl + ko, idesc, 1u);
+      umma::mma_f16(d_tmem + uint32_t(n0), dal + ko, dbh + ko, idesc, 1u);
     }
   }
 }
@@ -202,54 +170,62 @@ template <int N, int MODE, bool BF16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stage_tc(StageArgs a, const uint4 *__restrict__ ops, int ntiles, int *err_flag) {
   using T = TC<N>;
-  constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, NQ = T::NQ;
+  constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, FS = T::FS;
   extern __shared__ __align__(1024) uint8_t smem[];
-  // field-major staging [6][kTileElems][NPP]: the tile's fields, updated in place
-  float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);
-  // flux staging [120][NFF] (compact rows), then the residual (or rhs) tile [6][kTileElems][NPP]
-  float *s_fl = reinterpret_cast<float *>(smem + T::OFF_FL);
-  float *s_res = s_fl;
+  float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);       // [6][FS]: fields of the tile
+  float *s_res = reinterpret_cast<float *>(smem + T::OFF_RES);   // [6][FS]: residual of the tile
+  float *s_stage = reinterpret_cast<float *>(smem + T::OFF_A1H); // [6][FS]: next tile's fields (in A1)
+  float *s_out = reinterpret_cast<float *>(smem + T::OFF_A2H);   // [2][6][FS]: results (in A2)
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
-  float *s_sc1 = reinterpret_cast<float *>(smem + T::OFF_SC); // staged rows: scale, inverse at +128
-  float *s_sc2 = s_sc1 + 256;                                 // compact rows
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // MMA completion
-  uint64_t *barR = bar + 1;                                        // residual tile landed
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 16);
-  float4 *s_face = reinterpret_cast<float4 *>(smem + T::OFF_FACE); // [80][3]: {n, Fs}, {wE, wH, Z+, Y+}, {k2, conn}
+  float *s_inv1 = reinterpret_cast<float *>(smem + T::OFF_MX);  // A1 row inverse scales (compact rows)
+  uint32_t *s_mx2 = reinterpret_cast<uint32_t *>(s_inv1 + 128); // A2 maxima per field component (float bits)
+  uint64_t *bar1 = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // GEMM1 done
+  uint64_t *bar2 = bar1 + 1;                                        // GEMM2 (and all earlier MMAs) done
+  uint64_t *barR = bar1 + 2;                                        // residual tile landed
+  uint64_t *barU = bar1 + 3;                                        // fields and face data of a tile landed
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // single-thread roles sit in the last four warps, which have the least flux
+  // and epilogue work (issuing a tcgen05.mma or a bulk copy stalls the thread):
+  // MMA issue, staging of the next tile, residual load, bulk stores
+  const bool issuer = tid == kThreads - 32;
+  const bool stager = tid == kThreads - 64;
+  const bool rloader = tid == kThreads - 96;
+  const bool storer = tid == kThreads - 128;
   const int64_t KN = a.K * NPP;
   const uint32_t sbase = umma::smem_u32(smem);
 
-  auto prefetch_tile = [&](int t) {
-    if (t >= ntiles) return;
+  // fields of tile t into the A1 bytes, its face and element data into a
+  // slot (one thread; completes on barU)
+  auto stage_tile = [&](int t, int slot) {
     const int64_t kb = int64_t(t) * kTileElems;
-    const int64_t ne = a.K - kb < kTileElems ? a.K - kb : kTileElems;
-    const uint32_t rowbytes = uint32_t(ne * NPP * 4);
-    for (int f = 0; f < 6; ++f) {
-      prefetch_l2(a.u + f * KN + kb * NPP, rowbytes);
-      if (MODE == MODE_LSERK) prefetch_l2(a.res + f * KN + kb * NPP, rowbytes);
-    }
-    prefetch_l2(a.fconn + kb * 4, uint32_t(ne * 4 * sizeof(int2)));
-    prefetch_l2(a.fgeo + kb * 4, uint32_t(ne * 4 * sizeof(float4)));
-    prefetch_l2(a.fmat + kb * 4, uint32_t(ne * 4 * sizeof(float4)));
-    prefetch_l2(a.geo + kb * G_STRIDE, uint32_t(ne * G_STRIDE * 4));
+    const uint32_t nb = uint32_t(a.K - kb < kTileElems ? a.K - kb : kTileElems);
+    const uint32_t rb = nb * NPP * 4;
+    uint8_t *fs = smem + T::OFF_FACE + slot * T::FSLOT;
+    umma::mbar_arrive_expect_tx(barU, 6u * rb + nb * (64u + 64u + G_STRIDE * 4u + 32u));
+    for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_stage + f * FS, a.u + f * KN + kb * NPP, rb, barU);
+    umma::bulk_g2s(fs + T::FGEO, a.fgeo + kb * 4, nb * 64u, barU);
+    umma::bulk_g2s(fs + T::FMAT, a.fmat + kb * 4, nb * 64u, barU);
+    umma::bulk_g2s(fs + T::FELEM, a.geo + kb * G_STRIDE, nb * G_STRIDE * 4u, barU);
+    umma::bulk_g2s(fs + T::FCONN, a.fconn + kb * 4, nb * 32u, barU);
   };
 
   // ---- one-time setup
-  for (int i = tid; i < (2 * T::A1B + 2 * T::A2B) / 16; i += kThreads)
+  for (int i = tid; i < (2 * T::A1B + T::A2R) / 16; i += kThreads)
     reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < T::OPS_BYTES / 16; i += kThreads)
     reinterpret_cast<uint4 *>(smem + T::OFF_B1H)[i] = __ldg(ops + i);
   for (int i = tid; i < NFF + kConnKinds * NFP; i += kThreads)
     s_fm[i] = i < NFF ? a.fmask[i] : a.nbrtab[i - NFF];
-  for (int i = tid; i < 512; i += kThreads) s_sc1[i] = 1.f;
+  for (int i = tid; i < 136; i += kThreads) s_inv1[i] = i < 128 ? 1.f : 0.f;
   if (tid == 0) {
-    umma::mbar_init(bar, 1);
+    umma::mbar_init(bar1, 1);
+    umma::mbar_init(bar2, 1);
     umma::mbar_init(barR, 1);
+    umma::mbar_init(barU, 1);
     umma::fence_mbar_init();
-    prefetch_tile(blockIdx.x);
   }
   if (warp == 0) umma::tmem_alloc(tslot, T::TCOLS);
   umma::fence_proxy_async();
@@ -257,7 +233,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
+  if (stager && int(blockIdx.x) < ntiles) stage_tile(blockIdx.x, 0);
 
+  // field split: warp w owns operand rows 8w..8w+7 of A1; lane -> (row, half of
+  // a K group of 8), so one row's maximum is a reduction over 4 lanes and every
+  // half-warp writes one 128-byte core matrix; the padding columns are written
+  // as zeros (the staging overwrote them)
+  constexpr int KG1 = T::K1 / 8;
+  constexpr int R1 = (KG1 + 1) / 2;
+  const int r1 = warp * 8 + (lane & 7);
+  const int cr1 = compact_row(r1);
+  const int e1 = cr1 >= 0 ? cr1 / 6 : 0, f1 = cr1 >= 0 ? cr1 % 6 : 0;
+  const int kq1 = 4 * ((lane >> 3) & 1) + 8 * (lane >> 4); // + 16 s
+  // flux: blocks of 4 elements x 8 face-node columns of A2 (padding columns
+  // included, written as zeros), lane -> (element, column); block b goes to
+  // warp b % 16, so the last warp gets the fewest
+  constexpr int KGF = T::K2 / 8;
+  constexpr int NBLK = (kTileElems / 4) * KGF;
+  constexpr int R2 = (NBLK + 15) / 16;
+  const int eo = lane >> 3, kk = lane & 7;
+
+  // epilogue: one thread per (element, field) row of the accumulators
   const int quarter = warp & 3, part = warp >> 2;
   const bool lane_used = lane < 30;
   const int ep = lane_used ? lane / 6 : 4;
@@ -269,8 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int dl1 = (comp + 2) % 3, dl2 = (comp + 1) % 3;
   const int e_loc = quarter * 5 + ep;
   const int ridx = e_loc * 6 + fld;
-  constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staging
-  const int soff = fld * FS + e_loc * NPP; // this lane's row in the staging
+  const int soff = fld * FS + e_loc * NPP; // this lane's row in the staged tiles
   const uint32_t lane_taddr = tmem + (uint32_t(quarter * 32) << 16);
   constexpr int NCH = (NP + 7) / 8;
   constexpr int CPP = (NCH + 3) / 4;
@@ -281,114 +276,128 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t k0 = int64_t(tile) * kTileElems;
     const int ne = int(a.K - k0 < kTileElems ? a.K - k0 : kTileElems);
-    if (tid == 0) prefetch_tile(tile + gridDim.x);
+    const uint32_t rowbytes = uint32_t(ne * NPP * 4);
+    const int slot = int(phase);
+    const uint8_t *fslot = smem + T::OFF_FACE + slot * T::FSLOT;
+    const float4 *s_fgeo = reinterpret_cast<const float4 *>(fslot + T::FGEO);
+    const float4 *s_fmat = reinterpret_cast<const float4 *>(fslot + T::FMAT);
+    const float *s_geo = reinterpret_cast<const float *>(fslot + T::FELEM);
+    const int2 *s_fconn = reinterpret_cast<const int2 *>(fslot + T::FCONN);
 
-    // ---- 1. face table and fields of the tile (loads first, then, once the
-    // previous tile's bulk stores have read shared memory, the stores)
-    {
-      constexpr int TOT = 6 * kTileElems * NQ;
-      constexpr int IT = (TOT + kThreads - 1) / kThreads;
-      float4 v[IT];
+    // ---- 1. the staged fields into registers; once the previous tile's bulk
+    // stores have read shared memory, the residual copy starts and the fields
+    // go to the tile staging and (split) to the A1 operand
+    const bool okU = umma::mbar_wait_bounded(barU, phase);
+    float4 v[R1];
+    float mx = 0.f;
 #pragma unroll
-      for (int s = 0; s < IT; ++s) {
-        const int idx = tid + s * kThreads;
-        v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < TOT) {
-          const int f = idx / (kTileElems * NQ), rem = idx - f * (kTileElems * NQ);
-          const int e = rem / NQ, q = rem - e * NQ;
-          if (e < ne) v[s] = ldg4(a.u + f * KN + (k0 + e) * NPP + 4 * q);
+    for (int s = 0; s < R1; ++s) {
+      const int k = kq1 + 16 * s;
+      v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (cr1 >= 0 && k < NPP && e1 < ne) {
+        v[s] = *reinterpret_cast<const float4 *>(s_stage + f1 * FS + e1 * NPP + k);
+        if (k + 3 >= NP) {
+          if (k + 0 >= NP) v[s].x = 0.f;
+          if (k + 1 >= NP) v[s].y = 0.f;
+          if (k + 2 >= NP) v[s].z = 0.f;
+          if (k + 3 >= NP) v[s].w = 0.f;
         }
       }
-      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(0.f, 0.f, 1.f, 1.f);
-      int2 cn = make_int2(0, kBoundaryConn);
-      if (tid < kTileElems * 4 && (tid >> 2) < ne) {
-        const int64_t q = (k0 + (tid >> 2)) * 4 + (tid & 3);
-        cn = __ldg(a.fconn + q);
-        r0 = __ldg(a.fgeo + q);
-        r1 = __ldg(a.fmat + q);
-      }
-      if (tid == 0) umma::bulk_wait_read_all();
-      __syncthreads();
-      if (tid < kTileElems * 4) {
-        s_face[tid * 3 + 0] = r0;
-        s_face[tid * 3 + 1] = r1;
-        s_face[tid * 3 + 2] = make_float4(__int_as_float(cn.x), __int_as_float(cn.y), 0.f, 0.f);
-      }
-#pragma unroll
-      for (int s = 0; s < IT; ++s) {
-        const int idx = tid + s * kThreads;
-        if (idx < TOT) {
-          const int q = idx % NQ;
-          float4 w = v[s];
-          if (4 * q + 3 >= NP) {
-            if (4 * q + 0 >= NP) w.x = 0.f;
-            if (4 * q + 1 >= NP) w.y = 0.f;
-            if (4 * q + 2 >= NP) w.z = 0.f;
-            if (4 * q + 3 >= NP) w.w = 0.f;
-          }
-          const int f = idx / (kTileElems * NQ), eq = idx - f * (kTileElems * NQ);
-          *reinterpret_cast<float4 *>(s_u + f * FS + 4 * eq) = w;
-        }
-      }
+      if constexpr (!BF16) mx = absmax4(mx, v[s]);
     }
-    __syncthreads();
-
-    // ---- 2. split into the A1 operand (hi/lo), row-scaled for FP16
+    float sc1 = 1.f, inv1r = 1.f;
     if constexpr (!BF16) {
-      const int r = tid >> 2, pt = tid & 3;
-      float mx = 0.f;
-      if (r < kRows)
-        for (int j = pt; j < NP; j += 4) mx = fmaxf(mx, fabsf(s_u[staged_off<NPP>(r) + j]));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-      if (pt == 0 && r < kRows) row_scale(mx, s_sc1[r], s_sc1[128 + r]);
-      __syncthreads();
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+      row_scale(mx, sc1, inv1r);
     }
-    convert_rows<BF16, true, NPP>(s_u, NPP, NPP, T::K1, s_sc1, smem + T::OFF_A1H, smem + T::OFF_A1L, tid, NP);
+    if (__syncthreads_or(!okU)) {
+      if (tid == 0) {
+        atomicExch(err_flag, 1);
+        umma::mbar_wait_bounded(barU, phase);
+      }
+      break;
+    }
+    if (MODE == MODE_LSERK && rloader) {
+      umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
+      for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
+    }
+    if (!BF16 && cr1 >= 0 && lane < 8) s_inv1[cr1] = inv1r;
+#pragma unroll
+    for (int s = 0; s < R1; ++s) {
+      const int k = kq1 + 16 * s;
+      if (cr1 >= 0 && k < T::K1) {
+        if (k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[s];
+        float4 w = v[s];
+        if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+        uint2 hi, lo;
+        split2<BF16>(w.x, w.y, hi.x, lo.x);
+        split2<BF16>(w.z, w.w, hi.y, lo.y);
+        const uint32_t off = umma::kmajor_offset(uint32_t(r1), uint32_t(k), uint32_t(T::K1));
+        *reinterpret_cast<uint2 *>(smem + T::OFF_A1H + off) = hi;
+        *reinterpret_cast<uint2 *>(smem + T::OFF_A1L + off) = lo;
+      }
+    }
     umma::fence_proxy_async();
     __syncthreads();
 
     // ---- 3. local differentiation on the tensor cores (asynchronous)
-    if (tid == 0) {
+    if (issuer) {
       umma::fence_after_sync();
-      issue_split_gemm<BF16>(tmem, sbase + T::OFF_A1H, sbase + T::OFF_A1L, sbase + T::OFF_B1H, sbase + T::OFF_B1L,
-                             T::K1, T::N1);
+      issue_split_gemm<BF16, T::K1, T::N1>(tmem, sbase + T::OFF_A1H, sbase + T::OFF_A1L, sbase + T::OFF_B1H,
+                                           sbase + T::OFF_B1L);
+      umma::commit(bar1);
     }
+    bool ok = true;
 
-    // ---- 4. flux gather (overlaps GEMM1)
+    // ---- 4. neighbour traces and upwind flux (overlaps GEMM1), in registers;
+    // neighbours inside the tile are read from the staged fields
+    float fl[R2][6];
+    uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
     {
-      constexpr int TOT = kTileElems * NFF;
-      constexpr int IT = (TOT + kThreads - 1) / kThreads;
-      float qp[IT][6];
+      float qp[R2][6];
+      int lidx[R2];
 #pragma unroll
-      for (int s = 0; s < IT; ++s) {
-        const int it = tid + s * kThreads;
-        const int e = it / NFF, fm = it - e * NFF, f = fm / NFP, mm = fm - f * NFP;
+      for (int s = 0; s < R2; ++s) {
+        const int blk = warp + 16 * s;
+        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk;
+        lidx[s] = -1;
 #pragma unroll
         for (int c = 0; c < 6; ++c) qp[s][c] = 0.f;
-        if (it < TOT && e < ne) {
-          const float4 r2 = s_face[(e * 4 + f) * 3 + 2];
-          const int conn = __float_as_int(r2.y);
-          if (conn != kBoundaryConn) {
-            const float *up = a.u + int64_t(__float_as_int(r2.x)) * NPP + s_nb[conn * NFP + mm];
+        if (blk < NBLK && fm < NFF && e < ne) {
+          const int f = fm / NFP, mm = fm - f * NFP;
+          const int2 cn = s_fconn[e * 4 + f];
+          if (cn.y != kBoundaryConn) {
+            const int node = s_nb[cn.y * NFP + mm];
+            const int64_t el = int64_t(cn.x) - k0;
+            if (el >= 0 && el < ne) {
+              lidx[s] = int(el) * NPP + node;
+            } else {
+              const float *up = a.u + int64_t(cn.x) * NPP + node;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) qp[s][c] = __ldg(up + c * KN);
+              for (int c = 0; c < 6; ++c) qp[s][c] = __ldg(up + c * KN);
+            }
           }
         }
       }
 #pragma unroll
-      for (int s = 0; s < IT; ++s) {
-        const int it = tid + s * kThreads;
-        if (it >= TOT) continue;
-        const int e = it / NFF, fm = it - e * NFF, f = fm / NFP;
-        float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (e < ne) {
-          const float4 r0 = s_face[(e * 4 + f) * 3 + 0], r1 = s_face[(e * 4 + f) * 3 + 1];
-          const bool wall = __float_as_int(s_face[(e * 4 + f) * 3 + 2].y) == kBoundaryConn;
+      for (int s = 0; s < R2; ++s) {
+        const int blk = warp + 16 * s;
+        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) fl[s][c] = 0.f;
+        if (blk < NBLK && fm < NFF && e < ne) {
+          const int f = fm / NFP;
+          const float4 g0 = s_fgeo[e * 4 + f], w1 = s_fmat[e * 4 + f];
+          const bool wall = s_fconn[e * 4 + f].y == kBoundaryConn;
           const int vm = s_fm[fm];
           float qm[6];
 #pragma unroll
           for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
+          if (lidx[s] >= 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) qp[s][c] = s_u[c * FS + lidx[s]];
+          }
           if (wall) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -396,90 +405,114 @@ __global__ void __launch_bounds__(kThreads, 1)
               qp[s][c + 3] = qm[c + 3];
             }
           }
-          const float nx = r0.x, ny = r0.y, nz = r0.z;
+          const float nx = g0.x, ny = g0.y, nz = g0.z;
           const float dEx = qp[s][0] - qm[0], dEy = qp[s][1] - qm[1], dEz = qp[s][2] - qm[2];
           const float dHx = qp[s][3] - qm[3], dHy = qp[s][4] - qm[4], dHz = qp[s][5] - qm[5];
           const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
           const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
-          float vx = r1.z * dHx - a.alpha * cEx, vy = r1.z * dHy - a.alpha * cEy, vz = r1.z * dHz - a.alpha * cEz;
-          fl[0] = r1.x * (ny * vz - nz * vy);
-          fl[1] = r1.x * (nz * vx - nx * vz);
-          fl[2] = r1.x * (nx * vy - ny * vx);
-          vx = r1.w * dEx + a.alpha * cHx, vy = r1.w * dEy + a.alpha * cHy, vz = r1.w * dEz + a.alpha * cHz;
-          fl[3] = r1.y * (ny * vz - nz * vy);
-          fl[4] = r1.y * (nz * vx - nx * vz);
-          fl[5] = r1.y * (nx * vy - ny * vx);
+          float vx = w1.z * dHx - a.alpha * cEx, vy = w1.z * dHy - a.alpha * cEy, vz = w1.z * dHz - a.alpha * cEz;
+          fl[s][0] = w1.x * (ny * vz - nz * vy);
+          fl[s][1] = w1.x * (nz * vx - nx * vz);
+          fl[s][2] = w1.x * (nx * vy - ny * vx);
+          vx = w1.w * dEx + a.alpha * cHx, vy = w1.w * dEy + a.alpha * cHy, vz = w1.w * dEz + a.alpha * cHz;
+          fl[s][3] = w1.y * (ny * vz - nz * vy);
+          fl[s][4] = w1.y * (nz * vx - nx * vz);
+          fl[s][5] = w1.y * (nx * vy - ny * vx);
         }
+        if constexpr (!BF16) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s_fl[(e * 6 + c) * NFF + fm] = fl[c];
+          for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][c])));
+        }
       }
     }
+    // once GEMM1 has read A1, the next tile's fields and face data are staged
+    if (stager) {
+      ok = umma::mbar_wait_bounded(bar1, phase);
+      if (ok && tile + int(gridDim.x) < ntiles) stage_tile(tile + gridDim.x, slot ^ 1);
+    }
+    if constexpr (!BF16) {
+      // one FP16 scale per field component of the tile: |x| as float bits
+      // orders like |x|
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, fmx[c]);
+        if (lane == 0) atomicMax(s_mx2 + c, m);
+      }
+    }
+    // the previous tile's bulk stores must have read the A2 bytes
+    if (storer) umma::bulk_wait_read_all();
     __syncthreads();
 
     // ---- 5. split the face fluxes into the A2 operand
-    if constexpr (!BF16) {
-      const float mx = row_absmax4(s_fl, NFF, NFF, tid);
-      if ((tid & 3) == 0 && (tid >> 2) < kRows) row_scale(mx, s_sc2[tid >> 2], s_sc2[128 + (tid >> 2)]);
-      __syncthreads();
+    {
+      float sc2[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        sc2[c] = 1.f;
+        if constexpr (!BF16) {
+          float inv;
+          row_scale(__uint_as_float(s_mx2[c]), sc2[c], inv);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < R2; ++s) {
+        const int blk = warp + 16 * s;
+        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk;
+        if (blk < NBLK) {
+          // the six rows of element e lie in one TMEM lane quarter
+          const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
+#pragma unroll
+          for (int c = 0; c < 6; c += 2) {
+            uint32_t hi, lo;
+            split2<BF16>(fl[s][c] * sc2[c], fl[s][c + 1] * sc2[c + 1], hi, lo);
+            const uint32_t o0 = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
+            const uint32_t o1 = umma::kmajor_offset(r0 + uint32_t(c + 1), uint32_t(fm), uint32_t(T::K2));
+            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2H + o0) = uint16_t(hi);
+            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2H + o1) = uint16_t(hi >> 16);
+            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2L + o0) = uint16_t(lo);
+            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2L + o1) = uint16_t(lo >> 16);
+          }
+        }
+      }
     }
-    convert_rows<BF16, false>(s_fl, NFF, NFF, T::K2, s_sc2, smem + T::OFF_A2H, smem + T::OFF_A2L, tid, NFF);
     umma::fence_proxy_async();
     __syncthreads();
-    // the flux staging is free: the residual tile lands there during GEMM2
-    if (MODE == MODE_LSERK && tid == 0) {
-      const uint32_t rowbytes = uint32_t(ne * NPP * 4);
-      umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
-      for (int f = 0; f < 6; ++f)
-        umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
-    }
 
-    // ---- 6. flux lifting on the tensor cores, then wait for both products
-    if (tid == 0) {
+    // ---- 6. flux lifting on the tensor cores; meanwhile the volume terms
+    // from GEMM1: chain rule (eq. dg-reference-matrices) and curls
+    if (issuer) {
       umma::fence_after_sync();
-      issue_split_gemm<BF16>(tmem + uint32_t(T::N1), sbase + T::OFF_A2H, sbase + T::OFF_A2L, sbase + T::OFF_B2H,
-                             sbase + T::OFF_B2L, T::K2, T::N2);
-      umma::commit(bar);
+      issue_split_gemm<BF16, T::K2, T::N2>(tmem + uint32_t(T::N1), sbase + T::OFF_A2H, sbase + T::OFF_A2L,
+                                           sbase + T::OFF_B2H, sbase + T::OFF_B2L);
+      umma::commit(bar2);
     }
-    const int64_t k = k0 + e_loc;
     const bool live = lane_used && e_loc < ne;
     float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f;
     if (live) {
-      const float *g = a.geo + k * G_STRIDE;
-      g1r = __ldg(g + G_RX + dl1), g1s = __ldg(g + G_SX + dl1), g1t = __ldg(g + G_TX + dl1);
-      g2r = __ldg(g + G_RX + dl2), g2s = __ldg(g + G_SX + dl2), g2t = __ldg(g + G_TX + dl2);
-      w = __ldg(g + (isE ? G_IEPS : G_IMU));
+      const float *g = s_geo + e_loc * G_STRIDE;
+      g1r = g[G_RX + dl1], g1s = g[G_SX + dl1], g1t = g[G_TX + dl1];
+      g2r = g[G_RX + dl2], g2s = g[G_SX + dl2], g2t = g[G_TX + dl2];
+      w = g[isE ? G_IEPS : G_IMU];
     }
-    const float inv1 = BF16 ? 1.f : s_sc1[128 + (lane_used ? ridx : 0)];
-    const float inv2 = BF16 ? 1.f : s_sc2[128 + (lane_used ? ridx : 0)];
-    bool ok = umma::mbar_wait_bounded(bar, phase);
-    if (MODE == MODE_LSERK) ok = umma::mbar_wait_bounded(barR, phase) && ok;
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicExch(err_flag, 1);
-        // give the products and the residual copy in flight one more bounded
-        // wait before tensor and shared memory are released
-        umma::mbar_wait_bounded(bar, phase ^ 1u);
-        if (MODE == MODE_LSERK) umma::mbar_wait_bounded(barR, phase ^ 1u);
-      }
-      break;
+    float inv1 = 1.f, inv2 = 1.f;
+    if constexpr (!BF16) {
+      float sc;
+      inv1 = s_inv1[lane_used ? ridx : 0];
+      row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
     }
+    ok = umma::mbar_wait_bounded(bar1, phase) && ok;
     umma::fence_after_sync();
-
-    // ---- 7. epilogue: chain rule, curls, lifting, material scale; the update
-    // is written in place into the staged tiles
+    float vol[CPP][8];
 #pragma unroll
     for (int c = 0; c < CPP; ++c) {
       const int ch = ch0 + c;
       if (ch >= ch1) break;
       const int i0 = ch * 8;
-      float ur[8], us[8], ut[8], lf[8];
+      float ur[8], us[8], ut[8];
       umma::tmem_ld8(lane_taddr + uint32_t(i0), ur);
       umma::tmem_ld8(lane_taddr + uint32_t(T::NB + i0), us);
       umma::tmem_ld8(lane_taddr + uint32_t(2 * T::NB + i0), ut);
-      umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
       umma::tmem_wait_ld();
-      float rv[8];
 #pragma unroll
       for (int n = 0; n < 8; ++n) {
         const float dr = ur[n] * inv1, ds = us[n] * inv1, dt = ut[n] * inv1;
@@ -487,9 +520,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float p2 = g2r * dr + g2s * ds + g2t * dt;
         const float v1 = __shfl_sync(0xffffffffu, p1, src1);
         const float v2 = __shfl_sync(0xffffffffu, p2, src2);
-        const float vol = isE ? (v1 - v2) : (v2 - v1);
-        rv[n] = (vol + lf[n] * inv2) * w;
+        vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
       }
+    }
+    ok = umma::mbar_wait_bounded(bar2, phase) && ok;
+    if (MODE == MODE_LSERK) ok = umma::mbar_wait_bounded(barR, phase) && ok;
+    // this slot's face and element data are rewritten by the staging after next
+    umma::fence_proxy_async();
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(err_flag, 1);
+        // give the products and the copies in flight one more bounded wait
+        // before tensor and shared memory are released
+        umma::mbar_wait_bounded(bar2, phase);
+        if (MODE == MODE_LSERK) umma::mbar_wait_bounded(barR, phase);
+        if (tile + int(gridDim.x) < ntiles) umma::mbar_wait_bounded(barU, phase ^ 1u);
+      }
+      break;
+    }
+    umma::fence_after_sync();
+
+    // ---- 7. epilogue: lifted flux, material scale, update; results go to the
+    // A2 bytes
+#pragma unroll
+    for (int c = 0; c < CPP; ++c) {
+      const int ch = ch0 + c;
+      if (ch >= ch1) break;
+      const int i0 = ch * 8;
+      float lf[8];
+      umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
+      umma::tmem_wait_ld();
       if (live) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -497,13 +557,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (i < NPP) {
             float r4[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? rv[4 * h + q] : 0.f;
-            float4 *rp = reinterpret_cast<float4 *>(s_res + soff + i);
+            for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? (vol[c][4 * h + q] + lf[4 * h + q] * inv2) * w : 0.f;
+            float4 *op = reinterpret_cast<float4 *>(s_out + soff + i);
             if (MODE == MODE_RHS) {
-              *rp = make_float4(r4[0], r4[1], r4[2], r4[3]);
+              *op = make_float4(r4[0], r4[1], r4[2], r4[3]);
             } else {
-              float4 *up = reinterpret_cast<float4 *>(s_u + soff + i);
-              const float4 rs = *rp, uo = *up;
+              const float4 rs = *reinterpret_cast<const float4 *>(s_res + soff + i);
+              const float4 uo = *reinterpret_cast<const float4 *>(s_u + soff + i);
               const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
               float nr[4], nu[4];
 #pragma unroll
@@ -512,8 +572,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[q], a.dt * r4[q]);
                 nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
               }
-              *rp = make_float4(nr[0], nr[1], nr[2], nr[3]);
-              *up = make_float4(nu[0], nu[1], nu[2], nu[3]);
+              op[0] = make_float4(nr[0], nr[1], nr[2], nr[3]);
+              op[6 * FS / 4] = make_float4(nu[0], nu[1], nu[2], nu[3]);
             }
           }
         }
@@ -522,21 +582,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
-    // ---- 8. write the tile back with asynchronous bulk stores
-    if (tid == 0) {
-      const uint32_t rowbytes = uint32_t(ne * NPP * 4);
+    // ---- 8. write the tile back with asynchronous bulk stores; clear the
+    // flux maxima for the next tile
+    if (storer) {
       for (int f = 0; f < 6; ++f) {
         if (MODE == MODE_RHS) {
-          umma::bulk_s2g(a.rhs + f * KN + k0 * NPP, s_res + f * FS, rowbytes);
+          umma::bulk_s2g(a.rhs + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
         } else {
-          umma::bulk_s2g(a.res + f * KN + k0 * NPP, s_res + f * FS, rowbytes);
-          umma::bulk_s2g(a.u_out + f * KN + k0 * NPP, s_u + f * FS, rowbytes);
+          umma::bulk_s2g(a.res + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
+          umma::bulk_s2g(a.u_out + f * KN + k0 * NPP, s_out + (6 + f) * FS, rowbytes);
         }
       }
       umma::bulk_commit();
     }
+    if (!BF16 && tid < 8) s_mx2[tid] = 0u;
+    phase ^= 1u;
   }
-  if (tid == 0) umma::bulk_wait_all();
+  if (storer) umma::bulk_wait_all();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, T::TCOLS);
 }
