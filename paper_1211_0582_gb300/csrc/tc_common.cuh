@@ -1,0 +1,86 @@
+// Shared pieces of the tensor-core (split-precision) stage kernels: operand
+// splitting, FP16 range scaling and the TMEM row layout of an element tile.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dgmx {
+namespace tcc {
+
+__host__ __device__ constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ constexpr int tmem_cols(int x) {
+  return x <= 32 ? 32 : x <= 64 ? 64 : x <= 128 ? 128 : x <= 256 ? 256 : 512;
+}
+
+
+struct TcState {
+  void *d_ops = nullptr;
+  int sms = 0;
+};
+
+// Round-to-nearest-even of a finite FP32 bit pattern to 23 - DROP explicit
+// mantissa bits (low DROP bits cleared), by integer arithmetic on the
+// sign-magnitude encoding; a carry into the exponent is the correct rounding.
+template <int DROP>
+__device__ __forceinline__ uint32_t rne_bits(uint32_t u) {
+  return (u + ((1u << (DROP - 1)) - 1u) + ((u >> DROP) & 1u)) & ~((1u << DROP) - 1u);
+}
+
+// hi/lo split of two FP32 values into packed 16-bit pairs (x0 in the low half).
+// BF16: hi by a rounding conversion, widened back by a shift (BF16 is the top
+// half of FP32); lo = x - hi is exact in FP32 and converted with rounding.
+// FP16: hi is rounded to 11 significant bits (exact in FP16 for |x| >= 2^-14;
+// below that the conversion rounds it to the subnormal grid, an error of at
+// most 2^-25), lo = x - hi is exact in FP32 and converted with rounding.
+template <bool BF16>
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  if constexpr (BF16) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
+    hi = *reinterpret_cast<const uint32_t *>(&hh);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - h0, x1 - h1);
+    lo = *reinterpret_cast<const uint32_t *>(&ll);
+  } else {
+    const float h0 = __uint_as_float(rne_bits<13>(__float_as_uint(x0)));
+    const float h1 = __uint_as_float(rne_bits<13>(__float_as_uint(x1)));
+    const __half2 hh = __floats2half2_rn(h0, h1), ll = __floats2half2_rn(x0 - h0, x1 - h1);
+    hi = *reinterpret_cast<const uint32_t *>(&hh);
+    lo = *reinterpret_cast<const uint32_t *>(&ll);
+  }
+}
+
+// Operand row (32 * quarter + lane) -> compact row (6 e + f), or -1 for the
+// two unused lanes of each quarter.
+__host__ __device__ constexpr int compact_row(int r) { return (r & 31) < 30 ? (r >> 5) * 30 + (r & 31) : -1; }
+
+// Power-of-two scale bringing a maximum mx (>= 0) into [0.5, 1) and its
+// inverse, from the exponent field of mx (FP16 range guard). Zero, subnormal
+// or non-finite maxima give scale 1.
+__device__ __forceinline__ void row_scale(float mx, float &scale, float &inv) {
+  const uint32_t ex = (__float_as_uint(mx) >> 23) & 0xFFu;
+  if (ex == 0u || ex >= 253u) {
+    scale = 1.f;
+    inv = 1.f;
+    return;
+  }
+  scale = __uint_as_float((253u - ex) << 23);
+  inv = __uint_as_float((ex + 1u) << 23);
+}
+
+__device__ __forceinline__ float absmax4(float m, float4 v) {
+  return fmaxf(fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
+}
+
+// Orders 6 and 7: the operator slices in stream order (hi/lo), and the
+// launch of the streamed-operator stage kernel.
+std::vector<uint8_t> build_streamed_operators(int N, const RefOps &o, bool bf16);
+cudaError_t launch_tc_streamed(int N, int mode, bool bf16, const StageArgs &a, const TcState &st, int *flag,
+                               cudaStream_t s);
+
+} // namespace tcc
+} // namespace dgmx

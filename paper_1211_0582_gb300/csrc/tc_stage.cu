@@ -20,8 +20,8 @@
 // form curl H and -curl E, adds the lifted flux, scales by 1/eps, 1/mu and
 // either stores the right-hand side or applies the LSERK update.
 //
-// Supported orders: N = 1..5 (the operators of N >= 6 do not fit in shared
-// memory next to the tiles; those orders use the CUDA-core kernel).
+// Orders N = 1..5 (the operators of N = 6, 7 do not fit in shared memory next
+// to a tile; those orders stream them, see tc_stage_streamed.cu).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -31,20 +31,19 @@
 #include "../../include/dgmx.h"
 #include "flux.cuh"
 #include "tc_api.h"
+#include "tc_common.cuh"
 #include "umma.cuh"
 
 namespace dgmx {
 
 namespace {
 
+using namespace tcc;
+
 constexpr int kThreads = 512;
 constexpr int kTileElems = 20; // 4 TMEM lane quarters x 5 elements
-constexpr int kMaxTcOrder = 5;
-
-__host__ __device__ constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
-__host__ __device__ constexpr int tmem_cols(int x) {
-  return x <= 32 ? 32 : x <= 64 ? 64 : x <= 128 ? 128 : x <= 256 ? 256 : 512;
-}
+constexpr int kMaxResidentOrder = 5; // operators resident in shared memory up to here
+constexpr int kMaxTcOrder = 7;
 
 template <int N>
 struct TC {
@@ -83,64 +82,6 @@ struct TC {
   static constexpr int SMEM = OFF_BAR + 48;
   static_assert(6 * FS * 4 <= 2 * A1B, "the staged fields do not fit in the A1 operand");
 };
-
-struct TcState {
-  void *d_ops = nullptr;
-  int sms = 0;
-};
-
-// Round-to-nearest-even of a finite FP32 bit pattern to 23 - DROP explicit
-// mantissa bits (low DROP bits cleared), by integer arithmetic on the
-// sign-magnitude encoding; a carry into the exponent is the correct rounding.
-template <int DROP>
-__device__ __forceinline__ uint32_t rne_bits(uint32_t u) {
-  return (u + ((1u << (DROP - 1)) - 1u) + ((u >> DROP) & 1u)) & ~((1u << DROP) - 1u);
-}
-
-// hi/lo split of two FP32 values into packed 16-bit pairs (x0 in the low half).
-// BF16: hi by a rounding conversion, widened back by a shift (BF16 is the top
-// half of FP32); lo = x - hi is exact in FP32 and converted with rounding.
-// FP16: hi is rounded to 11 significant bits (exact in FP16 for |x| >= 2^-14;
-// below that the conversion rounds it to the subnormal grid, an error of at
-// most 2^-25), lo = x - hi is exact in FP32 and converted with rounding.
-template <bool BF16>
-__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
-  if constexpr (BF16) {
-    const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
-    hi = *reinterpret_cast<const uint32_t *>(&hh);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
-    const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - h0, x1 - h1);
-    lo = *reinterpret_cast<const uint32_t *>(&ll);
-  } else {
-    const float h0 = __uint_as_float(rne_bits<13>(__float_as_uint(x0)));
-    const float h1 = __uint_as_float(rne_bits<13>(__float_as_uint(x1)));
-    const __half2 hh = __floats2half2_rn(h0, h1), ll = __floats2half2_rn(x0 - h0, x1 - h1);
-    hi = *reinterpret_cast<const uint32_t *>(&hh);
-    lo = *reinterpret_cast<const uint32_t *>(&ll);
-  }
-}
-
-// Operand row (32 * quarter + lane) -> compact row (6 e + f), or -1 for the
-// two unused lanes of each quarter.
-__host__ __device__ constexpr int compact_row(int r) { return (r & 31) < 30 ? (r >> 5) * 30 + (r & 31) : -1; }
-
-// Power-of-two scale bringing a maximum mx (>= 0) into [0.5, 1) and its
-// inverse, from the exponent field of mx (FP16 range guard). Zero, subnormal
-// or non-finite maxima give scale 1.
-__device__ __forceinline__ void row_scale(float mx, float &scale, float &inv) {
-  const uint32_t ex = (__float_as_uint(mx) >> 23) & 0xFFu;
-  if (ex == 0u || ex >= 253u) {
-    scale = 1.f;
-    inv = 1.f;
-    return;
-  }
-  scale = __uint_as_float((253u - ex) << 23);
-  inv = __uint_as_float((ex + 1u) << 23);
-}
-
-__device__ __forceinline__ float absmax4(float m, float4 v) {
-  return fmaxf(fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
-}
 
 // Three split products per K step: hi*hi, hi*lo, lo*hi, FP32 accumulation.
 // Fully unrolled; the operand descriptors are formed once and advanced along K
@@ -513,6 +454,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       umma::tmem_ld8(lane_taddr + uint32_t(T::NB + i0), us);
       umma::tmem_ld8(lane_taddr + uint32_t(2 * T::NB + i0), ut);
       umma::tmem_wait_ld();
+      umma::reg_fence8(ur);
+      umma::reg_fence8(us);
+      umma::reg_fence8(ut);
 #pragma unroll
       for (int n = 0; n < 8; ++n) {
         const float dr = ur[n] * inv1, ds = us[n] * inv1, dt = ut[n] * inv1;
@@ -550,6 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       float lf[8];
       umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
       umma::tmem_wait_ld();
+      umma::reg_fence8(lf);
       if (live) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -660,7 +605,7 @@ cudaError_t launch_tc_order(int mode, bool bf16, const StageArgs &a, const TcSta
 
 int tc_prepare(dg_ctx *ctx) {
   if (ctx->N > kMaxTcOrder) {
-    ctx->err = "tensor-core precisions support N <= 5 (operators of higher orders do not fit in shared memory)";
+    ctx->err = "tensor-core precisions support N <= 7";
     return DG_ERR_UNSUPPORTED;
   }
   int dev = 0;
@@ -680,7 +625,8 @@ int tc_prepare(dg_ctx *ctx) {
   case 2: blk = build_operand_block<2>(ctx->ops, bf16); break;
   case 3: blk = build_operand_block<3>(ctx->ops, bf16); break;
   case 4: blk = build_operand_block<4>(ctx->ops, bf16); break;
-  default: blk = build_operand_block<5>(ctx->ops, bf16); break;
+  case 5: blk = build_operand_block<5>(ctx->ops, bf16); break;
+  default: blk = build_streamed_operators(ctx->N, ctx->ops, bf16); break;
   }
   TcState *st = new TcState();
   st->sms = prop.multiProcessorCount;
@@ -719,7 +665,7 @@ cudaError_t launch_stage_tc(dg_ctx *ctx, int mode, const StageArgs &a) {
   case 3: return launch_tc_order<3>(mode, bf16, a, *st, flag, ctx->stream);
   case 4: return launch_tc_order<4>(mode, bf16, a, *st, flag, ctx->stream);
   case 5: return launch_tc_order<5>(mode, bf16, a, *st, flag, ctx->stream);
-  default: return cudaErrorNotSupported;
+  default: return launch_tc_streamed(ctx->N, mode, bf16, a, *st, flag, ctx->stream);
   }
 }
 

@@ -1,0 +1,601 @@
+// Tensor-core form of the fused right-hand side / LSERK stage for N = 6, 7
+// (sm_103a), with the operators streamed from L2.
+//
+// Same tile (20 elements x 6 fields = 120 accumulator rows) and the same split
+// precision as the kernel for N <= 5: hi*hi + hi*lo + lo*hi products with FP32
+// accumulation in tensor memory (Section 2, Fig. el-local-ops: local
+// differentiation and lifting as matrix-matrix products over many elements).
+// At these orders the hi/lo operators (188 KB at N = 6, 264 KB at N = 7) do
+// not fit in shared memory beside a tile, so the paper's "keep the matrices
+// on chip, stream the field data" (Section 3) is turned around for them: the
+// host stores every 16-wide K slice of [Dr; Ds; Dt] and of LIFT contiguously in
+// the canonical operand layout, and a dedicated warp copies the slices from
+// L2 (where the few hundred KB stay resident) into a three-slot shared-memory
+// ring, one slice ahead of the MMAs that read them (full/empty mbarriers; the
+// MMA completion itself releases a slot). The same warp issues all MMAs.
+//
+// Per tile: GEMM1 takes K1/16 slices, each feeding three MMAs per split
+// product (one per derivative direction, N = NB columns); GEMM2 takes K2/16
+// slices. TMEM holds [ur | us | ut | lifted flux] = 4 NB columns (all 512 at
+// N = 7). A1 and A2 share one shared-memory region: A2 is written once GEMM1
+// has completed. The residual is read and the results are written directly
+// between registers and global memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "../../include/dgmx.h"
+#include "flux.cuh"
+#include "tc_common.cuh"
+#include "umma.cuh"
+
+namespace dgmx {
+
+namespace {
+
+using namespace tcc;
+
+constexpr int kThreadsS = 512;
+constexpr int kMmaWarp = 15;   // MMA issue and operator stream (after the field split)
+constexpr int kFluxWarps = 15; // warps 0..14
+constexpr int kTileS = 20;     // 4 TMEM lane quarters x 5 elements
+constexpr int kSlots = 3;      // operator ring depth
+
+template <int N>
+struct TS {
+  using D = Dims<N>;
+  static constexpr int NP = D::NP, NFP = D::NFP, NPP = D::NPP, NFF = D::NFF;
+  static constexpr int K1 = rup(NP, 16), NB = K1, K2 = rup(NFF, 16);
+  static constexpr int KS1 = K1 / 16, KS2 = K2 / 16, PER = KS1 + KS2; // K slices per tile
+  static constexpr int SL1 = 2 * 3 * NB * 32;                         // GEMM1 slice: hi, lo
+  static constexpr int SL2 = 2 * NB * 32;                             // GEMM2 slice: hi, lo
+  static constexpr int STREAM = KS1 * SL1 + KS2 * SL2;
+  static constexpr int TCOLS = tmem_cols(4 * NB);
+  static constexpr int FS = kTileS * NPP + 4; // padded field-block stride of the staged fields
+  static constexpr int A1B = 128 * K1 * 2, A2B = 128 * K2 * 2;
+  static constexpr int AREG = 2 * (A1B > A2B ? A1B : A2B); // A1 hi/lo, later A2 hi/lo
+  static constexpr int OFF_RING = AREG;
+  static constexpr int OFF_U = OFF_RING + kSlots * SL1;          // fp32 [6][FS]
+  static constexpr int OFF_FACE = OFF_U + 6 * FS * 4;            // float4 [80][3]
+  static constexpr int OFF_TAB = OFF_FACE + kTileS * 4 * 48;
+  static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16); // [128] A1 inverse scales, [8] A2 maxima
+  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32; // GEMM1, GEMM2, full[3], empty[3]; TMEM slot
+  static constexpr int SMEM = OFF_BAR + 8 * 8 + 16;
+  static_assert(4 * NB <= 512, "accumulators exceed tensor memory");
+  static_assert(SMEM <= 232448, "tile does not fit in shared memory");
+};
+
+// Byte offset of stream step st (0 .. PER-1) in the operator stream.
+template <int N>
+__host__ __device__ constexpr uint32_t slice_offset(int st) {
+  using T = TS<N>;
+  return st < T::KS1 ? uint32_t(st) * T::SL1 : uint32_t(T::KS1) * T::SL1 + uint32_t(st - T::KS1) * T::SL2;
+}
+
+template <int N, int MODE, bool BF16>
+__global__ void __launch_bounds__(kThreadsS, 1)
+    k_stage_tc_streamed(StageArgs a, const uint8_t *__restrict__ stream, int ntiles, int *err_flag) {
+  using T = TS<N>;
+  constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, FS = T::FS, NB = T::NB;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);
+  float4 *s_face = reinterpret_cast<float4 *>(smem + T::OFF_FACE); // {n, Fs}, {wE, wH, Z+, Y+}, {k2, conn}
+  uint8_t *s_fm = smem + T::OFF_TAB;
+  uint8_t *s_nb = s_fm + NFF;
+  float *s_inv1 = reinterpret_cast<float *>(smem + T::OFF_MX);
+  uint32_t *s_mx2 = reinterpret_cast<uint32_t *>(s_inv1 + 128);
+  uint64_t *bar1 = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // GEMM1 done
+  uint64_t *bar2 = bar1 + 1;                                        // GEMM2 done
+  uint64_t *full = bar1 + 2;                                        // ring slot filled
+  uint64_t *empty = bar1 + 2 + kSlots;                              // ring slot read by its MMAs
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 64);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool worker = warp != kMmaWarp;
+  const bool issuer = warp == kMmaWarp && lane == 0;
+  const int64_t KN = a.K * NPP;
+  const uint32_t sbase = umma::smem_u32(smem);
+
+  // ---- one-time setup
+  for (int i = tid; i < T::AREG / 16; i += kThreadsS) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < NFF + kConnKinds * NFP; i += kThreadsS) s_fm[i] = i < NFF ? a.fmask[i] : a.nbrtab[i - NFF];
+  for (int i = tid; i < 136; i += kThreadsS) s_inv1[i] = i < 128 ? 1.f : 0.f;
+  if (tid == 0) {
+    umma::mbar_init(bar1, 1);
+    umma::mbar_init(bar2, 1);
+    for (int s = 0; s < kSlots; ++s) {
+      umma::mbar_init(full + s, 1);
+      umma::mbar_init(empty + s, 1);
+    }
+    umma::fence_mbar_init();
+  }
+  if (warp == 0) umma::tmem_alloc(tslot, T::TCOLS);
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  // operator stream (issuer only): step j of the periodic slice sequence
+  // goes to slot j % kSlots
+  uint32_t jstep = 0;
+  auto produce = [&](uint32_t j) {
+    const int st = int(j % uint32_t(T::PER)), slot = int(j % uint32_t(kSlots));
+    const uint32_t bytes = st < T::KS1 ? uint32_t(T::SL1) : uint32_t(T::SL2);
+    umma::mbar_arrive_expect_tx(full + slot, bytes);
+    umma::bulk_g2s(smem + T::OFF_RING + slot * T::SL1, stream + slice_offset<N>(st), bytes, full + slot);
+  };
+  // wait for step jstep's slice, issue its MMAs, release the slot when they
+  // complete, and refill the previous step's slot with the step kSlots ahead;
+  // after a timed-out wait nothing more is waited for or issued
+  bool stream_ok = true;
+  auto consume = [&](auto &&issue) -> bool {
+    const int slot = int(jstep % uint32_t(kSlots));
+    if (!stream_ok) {
+      ++jstep;
+      return false;
+    }
+    bool ok = umma::mbar_wait_bounded(full + slot, (jstep / uint32_t(kSlots)) & 1u);
+    umma::fence_after_sync();
+    if (ok) issue(sbase + uint32_t(T::OFF_RING + slot * T::SL1));
+    umma::commit(empty + slot);
+    if (jstep >= 1u) {
+      const uint32_t pj = jstep - 1u;
+      ok = umma::mbar_wait_bounded(empty + pj % uint32_t(kSlots), (pj / uint32_t(kSlots)) & 1u) && ok;
+      if (ok) produce(pj + uint32_t(kSlots));
+    }
+    ++jstep;
+    stream_ok = ok;
+    return ok;
+  };
+  if (issuer && int(blockIdx.x) < ntiles)
+    for (int j = 0; j < kSlots; ++j) produce(uint32_t(j));
+
+  // field split (all 16 warps): warp w owns operand rows 8w..8w+7 (lane ->
+  // row, half of a K group of 8; padding columns written as zeros)
+  constexpr int KG1 = T::K1 / 8;
+  constexpr int R1 = (KG1 + 1) / 2;
+  const int r1 = warp * 8 + (lane & 7);
+  const int cr1 = compact_row(r1);
+  const int e1 = cr1 >= 0 ? cr1 / 6 : 0, f1 = cr1 >= 0 ? cr1 % 6 : 0;
+  const int kq1 = 4 * ((lane >> 3) & 1) + 8 * (lane >> 4);
+  // flux: blocks of 4 elements x 8 face-node columns of A2, lane -> (element, column)
+  constexpr int KGF = T::K2 / 8;
+  constexpr int NBLK = (kTileS / 4) * KGF;
+  constexpr int R2 = (NBLK + kFluxWarps - 1) / kFluxWarps;
+  constexpr int BATCH = 2; // neighbour gathers in flight per thread
+  const int eo = lane >> 3, kk8 = lane & 7;
+  // epilogue: one thread per (element, field) row of the accumulators; a
+  // warp reads the TMEM lane quarter warp % 4, quarter 3 without the MMA warp
+  // has three warps
+  const int quarter = warp & 3, part = warp >> 2;
+  const int nparts = quarter == 3 ? 3 : 4;
+  const bool lane_used = worker && lane < 30;
+  const int ep = lane < 30 ? lane / 6 : 4;
+  const int fld = lane < 30 ? lane % 6 : 5;
+  const int comp = fld % 3;
+  const bool isE = fld < 3;
+  const int src1 = ep * 6 + (isE ? 3 : 0) + (comp + 2) % 3;
+  const int src2 = ep * 6 + (isE ? 3 : 0) + (comp + 1) % 3;
+  const int dl1 = (comp + 2) % 3, dl2 = (comp + 1) % 3;
+  const int e_loc = quarter * 5 + ep;
+  const int ridx = e_loc * 6 + fld;
+  const int soff = fld * FS + e_loc * NPP;
+  const uint32_t lane_taddr = tmem + (uint32_t(quarter * 32) << 16);
+  constexpr int NCH = (NP + 7) / 8;
+  constexpr int CPP = (NCH + 2) / 3; // chunks of a warp of quarter 3 (the most)
+  const int cpp = (NCH + nparts - 1) / nparts;
+  const int ch0 = part * cpp;
+  const int ch1 = !worker ? ch0 : ch0 + cpp < NCH ? ch0 + cpp : NCH;
+
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t k0 = int64_t(tile) * kTileS;
+    const int ne = int(a.K - k0 < kTileS ? a.K - k0 : kTileS);
+    bool ok = true;
+
+    // ---- 1. fields and face table of the tile; staging and A1 (the previous
+    // tile's last barrier ordered every earlier read of these bytes)
+    {
+      float4 v[R1];
+      float mx = 0.f;
+#pragma unroll
+      for (int s = 0; s < R1; ++s) {
+        const int k = kq1 + 16 * s;
+        v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cr1 >= 0 && k < NPP && e1 < ne) {
+          v[s] = ldg4(a.u + f1 * KN + (k0 + e1) * NPP + k);
+          if (k + 3 >= NP) {
+            if (k + 0 >= NP) v[s].x = 0.f;
+            if (k + 1 >= NP) v[s].y = 0.f;
+            if (k + 2 >= NP) v[s].z = 0.f;
+            if (k + 3 >= NP) v[s].w = 0.f;
+          }
+        }
+        if constexpr (!BF16) mx = absmax4(mx, v[s]);
+      }
+      if (tid < kTileS * 4) {
+        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 1.f, 1.f);
+        int2 cn = make_int2(0, kBoundaryConn);
+        if ((tid >> 2) < ne) {
+          const int64_t q = (k0 + (tid >> 2)) * 4 + (tid & 3);
+          cn = __ldg(a.fconn + q);
+          g0 = __ldg(a.fgeo + q);
+          g1 = __ldg(a.fmat + q);
+        }
+        s_face[tid * 3 + 0] = g0;
+        s_face[tid * 3 + 1] = g1;
+        s_face[tid * 3 + 2] = make_float4(__int_as_float(cn.x), __int_as_float(cn.y), 0.f, 0.f);
+      }
+      float sc1 = 1.f, inv1r = 1.f;
+      if constexpr (!BF16) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        row_scale(mx, sc1, inv1r);
+        if (cr1 >= 0 && lane < 8) s_inv1[cr1] = inv1r;
+      }
+#pragma unroll
+      for (int s = 0; s < R1; ++s) {
+        const int k = kq1 + 16 * s;
+        if (cr1 >= 0 && k < T::K1) {
+          if (k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[s];
+          float4 w = v[s];
+          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+          uint2 hi, lo;
+          split2<BF16>(w.x, w.y, hi.x, lo.x);
+          split2<BF16>(w.z, w.w, hi.y, lo.y);
+          const uint32_t off = umma::kmajor_offset(uint32_t(r1), uint32_t(k), uint32_t(T::K1));
+          *reinterpret_cast<uint2 *>(smem + off) = hi;
+          *reinterpret_cast<uint2 *>(smem + T::A1B + off) = lo;
+        }
+      }
+    }
+    umma::fence_proxy_async();
+    __syncthreads();
+
+    // ---- 3. local differentiation, streamed operator slices
+    if (issuer) {
+      umma::fence_after_sync();
+      const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NB));
+      const uint64_t ah0 = umma::make_desc(sbase, 128, T::K1 * 16), al0 = umma::make_desc(sbase + T::A1B, 128, T::K1 * 16);
+      for (int kk = 0; kk < T::KS1; ++kk) {
+        ok = consume([&](uint32_t b) {
+          const uint64_t ko = uint64_t(kk) * 16u;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const uint64_t bh = umma::make_desc(b + uint32_t(d * NB * 32), 128, 256);
+            const uint64_t bl = umma::make_desc(b + uint32_t((3 + d) * NB * 32), 128, 256);
+            const uint32_t dt = tmem + uint32_t(d * NB);
+            umma::mma_f16(dt, ah0 + ko, bh, idesc, kk > 0 ? 1u : 0u);
+            umma::mma_f16(dt, ah0 + ko, bl, idesc, 1u);
+            umma::mma_f16(dt, al0 + ko, bh, idesc, 1u);
+          }
+        }) && ok;
+      }
+      umma::commit(bar1);
+    }
+
+    // ---- 4. neighbour traces and upwind flux (overlaps GEMM1), in registers
+    float fl[R2][6];
+    uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    if (warp < kFluxWarps) {
+#pragma unroll
+      for (int s0 = 0; s0 < R2; s0 += BATCH) {
+        float qp[BATCH][6];
+        int lidx[BATCH];
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+          const int s = s0 + b;
+          const int blk = warp + kFluxWarps * s;
+          const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk8;
+          lidx[b] = -1;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qp[b][c] = 0.f;
+          if (s < R2 && blk < NBLK && fm < NFF && e < ne) {
+            const int f = fm / NFP, mm = fm - f * NFP;
+            const float4 r2 = s_face[(e * 4 + f) * 3 + 2];
+            const int conn = __float_as_int(r2.y);
+            if (conn != kBoundaryConn) {
+              const int k2 = __float_as_int(r2.x);
+              const int node = s_nb[conn * NFP + mm];
+              const int64_t el = int64_t(k2) - k0;
+              if (el >= 0 && el < ne) {
+                lidx[b] = int(el) * NPP + node;
+              } else {
+                const float *up = a.u + int64_t(k2) * NPP + node;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) qp[b][c] = __ldg(up + c * KN);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+          const int s = s0 + b;
+          if (s >= R2) break;
+          const int blk = warp + kFluxWarps * s;
+          const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk8;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) fl[s][c] = 0.f;
+          if (blk < NBLK && fm < NFF && e < ne) {
+            const int f = fm / NFP;
+            const float4 g0 = s_face[(e * 4 + f) * 3 + 0], w1 = s_face[(e * 4 + f) * 3 + 1];
+            const bool wall = __float_as_int(s_face[(e * 4 + f) * 3 + 2].y) == kBoundaryConn;
+            const int vm = s_fm[fm];
+            float qm[6], q[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) q[c] = lidx[b] >= 0 ? s_u[c * FS + lidx[b]] : qp[b][c];
+            if (wall) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                q[c] = -qm[c];
+                q[c + 3] = qm[c + 3];
+              }
+            }
+            const float nx = g0.x, ny = g0.y, nz = g0.z;
+            const float dEx = q[0] - qm[0], dEy = q[1] - qm[1], dEz = q[2] - qm[2];
+            const float dHx = q[3] - qm[3], dHy = q[4] - qm[4], dHz = q[5] - qm[5];
+            const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
+            const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
+            float vx = w1.z * dHx - a.alpha * cEx, vy = w1.z * dHy - a.alpha * cEy, vz = w1.z * dHz - a.alpha * cEz;
+            fl[s][0] = w1.x * (ny * vz - nz * vy);
+            fl[s][1] = w1.x * (nz * vx - nx * vz);
+            fl[s][2] = w1.x * (nx * vy - ny * vx);
+            vx = w1.w * dEx + a.alpha * cHx, vy = w1.w * dEy + a.alpha * cHy, vz = w1.w * dEz + a.alpha * cHz;
+            fl[s][3] = w1.y * (ny * vz - nz * vy);
+            fl[s][4] = w1.y * (nz * vx - nx * vz);
+            fl[s][5] = w1.y * (nx * vy - ny * vx);
+          }
+          if constexpr (!BF16) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][c])));
+          }
+        }
+      }
+      if constexpr (!BF16) {
+        // one FP16 scale per field component of the tile
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const uint32_t m = __reduce_max_sync(0xffffffffu, fmx[c]);
+          if (lane == 0) atomicMax(s_mx2 + c, m);
+        }
+      }
+    }
+    // A2 overwrites A1: GEMM1 must have completed
+    ok = umma::mbar_wait_bounded(bar1, phase) && ok;
+    __syncthreads();
+
+    // ---- 5. split the face fluxes into the A2 operand
+    if (warp < kFluxWarps) {
+      float sc2[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        sc2[c] = 1.f;
+        if constexpr (!BF16) {
+          float inv;
+          row_scale(__uint_as_float(s_mx2[c]), sc2[c], inv);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < R2; ++s) {
+        const int blk = warp + kFluxWarps * s;
+        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk8;
+        if (blk < NBLK) {
+          const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5)); // the element's six rows share a quarter
+#pragma unroll
+          for (int c = 0; c < 6; c += 2) {
+            uint32_t hi, lo;
+            split2<BF16>(fl[s][c] * sc2[c], fl[s][c + 1] * sc2[c + 1], hi, lo);
+            const uint32_t o0 = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
+            const uint32_t o1 = umma::kmajor_offset(r0 + uint32_t(c + 1), uint32_t(fm), uint32_t(T::K2));
+            *reinterpret_cast<uint16_t *>(smem + o0) = uint16_t(hi);
+            *reinterpret_cast<uint16_t *>(smem + o1) = uint16_t(hi >> 16);
+            *reinterpret_cast<uint16_t *>(smem + T::A2B + o0) = uint16_t(lo);
+            *reinterpret_cast<uint16_t *>(smem + T::A2B + o1) = uint16_t(lo >> 16);
+          }
+        }
+      }
+    }
+    umma::fence_proxy_async();
+    __syncthreads();
+
+    // ---- 6. flux lifting (streamed slices); meanwhile the residual rows are read
+    if (issuer) {
+      umma::fence_after_sync();
+      const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NB));
+      const uint64_t ah0 = umma::make_desc(sbase, 128, T::K2 * 16), al0 = umma::make_desc(sbase + T::A2B, 128, T::K2 * 16);
+      const uint32_t dt = tmem + uint32_t(3 * NB);
+      for (int kk = 0; kk < T::KS2; ++kk) {
+        ok = consume([&](uint32_t b) {
+          const uint64_t ko = uint64_t(kk) * 16u;
+          const uint64_t bh = umma::make_desc(b, 128, 256), bl = umma::make_desc(b + uint32_t(NB * 32), 128, 256);
+          umma::mma_f16(dt, ah0 + ko, bh, idesc, kk > 0 ? 1u : 0u);
+          umma::mma_f16(dt, ah0 + ko, bl, idesc, 1u);
+          umma::mma_f16(dt, al0 + ko, bh, idesc, 1u);
+        }) && ok;
+      }
+      umma::commit(bar2);
+    }
+    const bool live = lane_used && e_loc < ne;
+    const int64_t k = k0 + e_loc;
+    float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f;
+    if (live) {
+      const float *g = a.geo + k * G_STRIDE;
+      g1r = __ldg(g + G_RX + dl1), g1s = __ldg(g + G_SX + dl1), g1t = __ldg(g + G_TX + dl1);
+      g2r = __ldg(g + G_RX + dl2), g2s = __ldg(g + G_SX + dl2), g2t = __ldg(g + G_TX + dl2);
+      w = __ldg(g + (isE ? G_IEPS : G_IMU));
+    }
+    float inv1 = 1.f, inv2 = 1.f;
+    if constexpr (!BF16) {
+      float sc;
+      inv1 = s_inv1[lane_used ? ridx : 0];
+      row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
+    }
+    // residual of one 8-node chunk of this lane's row (loaded one chunk ahead)
+    auto load_res = [&](int ch, float4 &r0, float4 &r1) {
+      r0 = r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (MODE != MODE_LSERK || !live || ch >= ch1) return;
+      const float *rp = a.res + fld * KN + k * NPP + ch * 8;
+      r0 = ldg4(rp);
+      if (ch * 8 + 4 < NPP) r1 = ldg4(rp + 4);
+    };
+    float4 rn0, rn1;
+    load_res(ch0, rn0, rn1);
+    ok = umma::mbar_wait_bounded(bar2, phase) && ok;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err_flag, 1);
+      break;
+    }
+    umma::fence_after_sync();
+
+    // ---- 7. epilogue: chain rule (eq. dg-reference-matrices), curls, lifted
+    // flux, material scale, update; results straight to global memory
+#pragma unroll
+    for (int c = 0; c < CPP; ++c) {
+      const int ch = ch0 + c;
+      if (ch >= ch1) break;
+      const int i0 = ch * 8;
+      const float rsv[8] = {rn0.x, rn0.y, rn0.z, rn0.w, rn1.x, rn1.y, rn1.z, rn1.w};
+      load_res(ch + 1, rn0, rn1);
+      float ur[8], us[8], ut[8], lf[8], vol[8];
+      umma::tmem_ld8(lane_taddr + uint32_t(i0), ur);
+      umma::tmem_ld8(lane_taddr + uint32_t(NB + i0), us);
+      umma::tmem_ld8(lane_taddr + uint32_t(2 * NB + i0), ut);
+      umma::tmem_ld8(lane_taddr + uint32_t(3 * NB + i0), lf);
+      umma::tmem_wait_ld();
+      umma::reg_fence8(ur);
+      umma::reg_fence8(us);
+      umma::reg_fence8(ut);
+      umma::reg_fence8(lf);
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const float dr = ur[n] * inv1, ds = us[n] * inv1, dtv = ut[n] * inv1;
+        const float p1 = g1r * dr + g1s * ds + g1t * dtv;
+        const float p2 = g2r * dr + g2s * ds + g2t * dtv;
+        const float v1 = __shfl_sync(0xffffffffu, p1, src1);
+        const float v2 = __shfl_sync(0xffffffffu, p2, src2);
+        vol[n] = isE ? (v1 - v2) : (v2 - v1);
+      }
+      if (live) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = i0 + 4 * h;
+          if (i < NPP) {
+            float r4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? (vol[4 * h + q] + lf[4 * h + q] * inv2) * w : 0.f;
+            if (MODE == MODE_RHS) {
+              *reinterpret_cast<float4 *>(a.rhs + fld * KN + k * NPP + i) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+            } else {
+              const float4 uo = *reinterpret_cast<const float4 *>(s_u + soff + i);
+              const float uov[4] = {uo.x, uo.y, uo.z, uo.w};
+              float nr[4], nu[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const bool pad = i + q >= NP;
+                nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[4 * h + q], a.dt * r4[q]);
+                nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
+              }
+              *reinterpret_cast<float4 *>(a.res + fld * KN + k * NPP + i) = make_float4(nr[0], nr[1], nr[2], nr[3]);
+              *reinterpret_cast<float4 *>(a.u_out + fld * KN + k * NPP + i) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+            }
+          }
+        }
+      }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (!BF16 && tid < 8) s_mx2[tid] = 0u;
+    phase ^= 1u;
+  }
+  // the two slices produced ahead of the last consumed one must land before exit
+  if (issuer && stream_ok && int(blockIdx.x) < ntiles)
+    for (uint32_t j = jstep; j < jstep + 2u; ++j)
+      umma::mbar_wait_bounded(full + j % uint32_t(kSlots), (j / uint32_t(kSlots)) & 1u);
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, T::TCOLS);
+}
+
+template <int N>
+std::vector<uint8_t> build_stream(const RefOps &o, bool bf16) {
+  using T = TS<N>;
+  std::vector<uint8_t> blk(T::STREAM, 0);
+  auto put = [&](size_t base_hi, size_t base_lo, int row, int k, double v) {
+    uint16_t hb, lb;
+    if (bf16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(float(v));
+      const __nv_bfloat16 l = __float2bfloat16_rn(float(v - double(__bfloat162float(h))));
+      std::memcpy(&hb, &h, 2);
+      std::memcpy(&lb, &l, 2);
+    } else {
+      const __half h = __float2half_rn(float(v));
+      const __half l = __float2half_rn(float(v - double(__half2float(h))));
+      std::memcpy(&hb, &h, 2);
+      std::memcpy(&lb, &l, 2);
+    }
+    const uint32_t off = umma::kmajor_offset(uint32_t(row), uint32_t(k), 16u); // one 16-wide K slice
+    std::memcpy(&blk[base_hi + off], &hb, 2);
+    std::memcpy(&blk[base_lo + off], &lb, 2);
+  };
+  const std::vector<double> *Ds[3] = {&o.Dr, &o.Ds, &o.Dt};
+  for (int kk = 0; kk < T::KS1; ++kk) {
+    const size_t hi = slice_offset<N>(kk), lo = hi + size_t(3) * T::NB * 32;
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < T::NP; ++i)
+        for (int k = 0; k < 16 && 16 * kk + k < T::NP; ++k)
+          put(hi, lo, d * T::NB + i, k, (*Ds[d])[size_t(i) * T::NP + 16 * kk + k]);
+  }
+  for (int kk = 0; kk < T::KS2; ++kk) {
+    const size_t hi = slice_offset<N>(T::KS1 + kk), lo = hi + size_t(T::NB) * 32;
+    for (int i = 0; i < T::NP; ++i)
+      for (int k = 0; k < 16 && 16 * kk + k < T::NFF; ++k)
+        put(hi, lo, i, k, o.LIFT[size_t(i) * T::NFF + 16 * kk + k]);
+  }
+  return blk;
+}
+
+template <int N, int MODE, bool BF16>
+cudaError_t launch_streamed_kernel(const StageArgs &a, const TcState &st, int *flag, cudaStream_t s) {
+  using T = TS<N>;
+  auto kern = k_stage_tc_streamed<N, MODE, BF16>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+  if (e != cudaSuccess) return e;
+  const int ntiles = int((a.K + kTileS - 1) / kTileS);
+  const int grid = ntiles < st.sms ? ntiles : st.sms;
+  kern<<<grid, kThreadsS, T::SMEM, s>>>(a, static_cast<const uint8_t *>(st.d_ops), ntiles, flag);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_streamed_order(int mode, bool bf16, const StageArgs &a, const TcState &st, int *flag,
+                                  cudaStream_t s) {
+  if (mode == MODE_RHS)
+    return bf16 ? launch_streamed_kernel<N, MODE_RHS, true>(a, st, flag, s)
+                : launch_streamed_kernel<N, MODE_RHS, false>(a, st, flag, s);
+  return bf16 ? launch_streamed_kernel<N, MODE_LSERK, true>(a, st, flag, s)
+              : launch_streamed_kernel<N, MODE_LSERK, false>(a, st, flag, s);
+}
+
+} // namespace
+
+namespace tcc {
+
+std::vector<uint8_t> build_streamed_operators(int N, const RefOps &o, bool bf16) {
+  return N == 6 ? build_stream<6>(o, bf16) : build_stream<7>(o, bf16);
+}
+
+cudaError_t launch_tc_streamed(int N, int mode, bool bf16, const StageArgs &a, const TcState &st, int *flag,
+                               cudaStream_t s) {
+  switch (N) {
+  case 6: return launch_streamed_order<6>(mode, bf16, a, st, flag, s);
+  case 7: return launch_streamed_order<7>(mode, bf16, a, st, flag, s);
+  default: return cudaErrorNotSupported;
+  }
+}
+
+} // namespace tcc
+} // namespace dgmx
