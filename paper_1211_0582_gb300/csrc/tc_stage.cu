@@ -42,8 +42,7 @@ using namespace tcc;
 
 constexpr int kThreads = 512;
 constexpr int kTileElems = 20; // 4 TMEM lane quarters x 5 elements
-constexpr int kMaxResidentOrder = 5; // operators resident in shared memory up to here
-constexpr int kMaxTcOrder = 7;
+constexpr int kMaxTcOrder = 7; // N <= 5 here, N = 6, 7 in tc_stage_streamed.cu
 
 template <int N>
 struct TC {

@@ -8,15 +8,18 @@
 // At these orders the hi/lo operators (188 KB at N = 6, 264 KB at N = 7) do
 // not fit in shared memory beside a tile, so the paper's "keep the matrices
 // on chip, stream the field data" (Section 3) is turned around for them: the
-// host stores every 16-wide K slice of [Dr; Ds; Dt] and of LIFT contiguously in
-// the canonical operand layout, and a dedicated warp copies the slices from
-// L2 (where the few hundred KB stay resident) into a three-slot shared-memory
-// ring, one slice ahead of the MMAs that read them (full/empty mbarriers; the
-// MMA completion itself releases a slot). The same warp issues all MMAs.
+// host stores the operators as a sequence of 24 KB-class slices in the
+// canonical operand layout (hi, then lo): for GEMM1 one 16-wide K step of
+// [Dr; Ds; Dt], for GEMM2 three K steps of LIFT. A dedicated warp copies the
+// slices from L2 (where the few hundred KB stay resident) into a three-slot
+// shared-memory ring, two slices ahead of the MMAs that read them
+// (full/empty mbarriers; the MMA completion itself releases a slot). The same
+// warp issues all MMAs. Fewer, larger slices keep the single issuing thread's
+// per-slice overhead (barrier waits, commit, copy issue) small.
 //
-// Per tile: GEMM1 takes K1/16 slices, each feeding three MMAs per split
-// product (one per derivative direction, N = NB columns); GEMM2 takes K2/16
-// slices. TMEM holds [ur | us | ut | lifted flux] = 4 NB columns (all 512 at
+// Per tile: GEMM1 takes K1/16 slices, each feeding the three split products
+// of the three derivative directions (N = NB columns each); GEMM2 takes
+// ceil(K2/48) slices. TMEM holds [ur | us | ut | lifted flux] = 4 NB columns (all 512 at
 // N = 7). A1 and A2 share one shared-memory region: A2 is written once GEMM1
 // has completed. The residual is read and the results are written directly
 // between registers and global memory.
@@ -48,21 +51,26 @@ struct TS {
   using D = Dims<N>;
   static constexpr int NP = D::NP, NFP = D::NFP, NPP = D::NPP, NFF = D::NFF;
   static constexpr int K1 = rup(NP, 16), NB = K1, K2 = rup(NFF, 16);
-  static constexpr int KS1 = K1 / 16, KS2 = K2 / 16, PER = KS1 + KS2; // K slices per tile
-  static constexpr int SL1 = 2 * 3 * NB * 32;                         // GEMM1 slice: hi, lo
-  static constexpr int SL2 = 2 * NB * 32;                             // GEMM2 slice: hi, lo
-  static constexpr int STREAM = KS1 * SL1 + KS2 * SL2;
+  static constexpr int KS1 = K1 / 16, KS2 = K2 / 16;  // K steps of GEMM1, GEMM2
+  static constexpr int G2 = 3;                         // GEMM2 K steps per slice
+  static constexpr int NS2 = (KS2 + G2 - 1) / G2;      // GEMM2 slices
+  static constexpr int PER = KS1 + NS2;                // operator slices per tile
+  static constexpr int SUB = 2 * NB * 32;              // NB rows x 16 K, hi then lo
+  static constexpr int SL = 3 * SUB;                   // one slice (three sub-blocks)
+  static constexpr int STREAM = PER * SL;
   static constexpr int TCOLS = tmem_cols(4 * NB);
   static constexpr int FS = kTileS * NPP + 4; // padded field-block stride of the staged fields
   static constexpr int A1B = 128 * K1 * 2, A2B = 128 * K2 * 2;
   static constexpr int AREG = 2 * (A1B > A2B ? A1B : A2B); // A1 hi/lo, later A2 hi/lo
   static constexpr int OFF_RING = AREG;
-  static constexpr int OFF_U = OFF_RING + kSlots * SL1;          // fp32 [6][FS]
+  static constexpr int OFF_U = OFF_RING + kSlots * SL;           // fp32 [6][FS]
   static constexpr int OFF_FACE = OFF_U + 6 * FS * 4;            // float4 [80][3]
   static constexpr int OFF_TAB = OFF_FACE + kTileS * 4 * 48;
   static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16); // [128] A1 inverse scales, [8] A2 maxima
-  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32; // GEMM1, GEMM2, full[3], empty[3]; TMEM slot
-  static constexpr int SMEM = OFF_BAR + 8 * 8 + 16;
+  static constexpr int NBAR = 2 + 2 * kSlots;          // GEMM1, GEMM2, full[kSlots], empty[kSlots]
+  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32;
+  static constexpr int OFF_TSLOT = OFF_BAR + NBAR * 8;  // TMEM base address
+  static constexpr int SMEM = OFF_TSLOT + 16;
   static_assert(4 * NB <= 512, "accumulators exceed tensor memory");
   static_assert(SMEM <= 232448, "tile does not fit in shared memory");
 };
@@ -70,8 +78,7 @@ struct TS {
 // Byte offset of stream step st (0 .. PER-1) in the operator stream.
 template <int N>
 __host__ __device__ constexpr uint32_t slice_offset(int st) {
-  using T = TS<N>;
-  return st < T::KS1 ? uint32_t(st) * T::SL1 : uint32_t(T::KS1) * T::SL1 + uint32_t(st - T::KS1) * T::SL2;
+  return uint32_t(st) * uint32_t(TS<N>::SL);
 }
 
 template <int N, int MODE, bool BF16>
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   uint64_t *bar2 = bar1 + 1;                                        // GEMM2 done
   uint64_t *full = bar1 + 2;                                        // ring slot filled
   uint64_t *empty = bar1 + 2 + kSlots;                              // ring slot read by its MMAs
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 64);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_TSLOT);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool worker = warp != kMmaWarp;
@@ -123,9 +130,8 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   uint32_t jstep = 0;
   auto produce = [&](uint32_t j) {
     const int st = int(j % uint32_t(T::PER)), slot = int(j % uint32_t(kSlots));
-    const uint32_t bytes = st < T::KS1 ? uint32_t(T::SL1) : uint32_t(T::SL2);
-    umma::mbar_arrive_expect_tx(full + slot, bytes);
-    umma::bulk_g2s(smem + T::OFF_RING + slot * T::SL1, stream + slice_offset<N>(st), bytes, full + slot);
+    umma::mbar_arrive_expect_tx(full + slot, uint32_t(T::SL));
+    umma::bulk_g2s(smem + T::OFF_RING + slot * T::SL, stream + slice_offset<N>(st), uint32_t(T::SL), full + slot);
   };
   // wait for step jstep's slice, issue its MMAs, release the slot when they
   // complete, and refill the previous step's slot with the step kSlots ahead;
@@ -139,7 +145,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     }
     bool ok = umma::mbar_wait_bounded(full + slot, (jstep / uint32_t(kSlots)) & 1u);
     umma::fence_after_sync();
-    if (ok) issue(sbase + uint32_t(T::OFF_RING + slot * T::SL1));
+    if (ok) issue(sbase + uint32_t(T::OFF_RING + slot * T::SL));
     umma::commit(empty + slot);
     if (jstep >= 1u) {
       const uint32_t pj = jstep - 1u;
@@ -190,11 +196,25 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   const int ch0 = part * cpp;
   const int ch1 = !worker ? ch0 : ch0 + cpp < NCH ? ch0 + cpp : NCH;
 
+  // warm L2 with the fields of the CTA's next tile and the residual of this one
+  auto prefetch = [&](int tu, int tr) {
+    if (tu < ntiles) {
+      const int64_t kb = int64_t(tu) * kTileS, nb = a.K - kb < kTileS ? a.K - kb : kTileS;
+      for (int f = 0; f < 6; ++f) umma::prefetch_l2(a.u + f * KN + kb * NPP, uint32_t(nb * NPP * 4));
+    }
+    if (MODE == MODE_LSERK && tr < ntiles) {
+      const int64_t kb = int64_t(tr) * kTileS, nb = a.K - kb < kTileS ? a.K - kb : kTileS;
+      for (int f = 0; f < 6; ++f) umma::prefetch_l2(a.res + f * KN + kb * NPP, uint32_t(nb * NPP * 4));
+    }
+  };
+  if (tid == 32 && int(blockIdx.x) < ntiles) prefetch(blockIdx.x, -1);
+
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t k0 = int64_t(tile) * kTileS;
     const int ne = int(a.K - k0 < kTileS ? a.K - k0 : kTileS);
     bool ok = true;
+    if (tid == 32) prefetch(tile + int(gridDim.x), tile);
 
     // ---- 1. fields and face table of the tile; staging and A1 (the previous
     // tile's last barrier ordered every earlier read of these bytes)
@@ -265,8 +285,8 @@ __global__ void __launch_bounds__(kThreadsS, 1)
           const uint64_t ko = uint64_t(kk) * 16u;
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const uint64_t bh = umma::make_desc(b + uint32_t(d * NB * 32), 128, 256);
-            const uint64_t bl = umma::make_desc(b + uint32_t((3 + d) * NB * 32), 128, 256);
+            const uint32_t sb = b + uint32_t(d * T::SUB);
+            const uint64_t bh = umma::make_desc(sb, 128, 256), bl = umma::make_desc(sb + uint32_t(NB * 32), 128, 256);
             const uint32_t dt = tmem + uint32_t(d * NB);
             umma::mma_f16(dt, ah0 + ko, bh, idesc, kk > 0 ? 1u : 0u);
             umma::mma_f16(dt, ah0 + ko, bl, idesc, 1u);
@@ -409,13 +429,19 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NB));
       const uint64_t ah0 = umma::make_desc(sbase, 128, T::K2 * 16), al0 = umma::make_desc(sbase + T::A2B, 128, T::K2 * 16);
       const uint32_t dt = tmem + uint32_t(3 * NB);
-      for (int kk = 0; kk < T::KS2; ++kk) {
+      for (int g = 0; g < T::NS2; ++g) {
         ok = consume([&](uint32_t b) {
-          const uint64_t ko = uint64_t(kk) * 16u;
-          const uint64_t bh = umma::make_desc(b, 128, 256), bl = umma::make_desc(b + uint32_t(NB * 32), 128, 256);
-          umma::mma_f16(dt, ah0 + ko, bh, idesc, kk > 0 ? 1u : 0u);
-          umma::mma_f16(dt, ah0 + ko, bl, idesc, 1u);
-          umma::mma_f16(dt, al0 + ko, bh, idesc, 1u);
+#pragma unroll
+          for (int j = 0; j < T::G2; ++j) {
+            const int kk = g * T::G2 + j;
+            if (kk >= T::KS2) break;
+            const uint64_t ko = uint64_t(kk) * 16u;
+            const uint32_t sb = b + uint32_t(j * T::SUB);
+            const uint64_t bh = umma::make_desc(sb, 128, 256), bl = umma::make_desc(sb + uint32_t(NB * 32), 128, 256);
+            umma::mma_f16(dt, ah0 + ko, bh, idesc, kk > 0 ? 1u : 0u);
+            umma::mma_f16(dt, ah0 + ko, bl, idesc, 1u);
+            umma::mma_f16(dt, al0 + ko, bh, idesc, 1u);
+          }
         }) && ok;
       }
       umma::commit(bar2);
@@ -512,9 +538,9 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     if (!BF16 && tid < 8) s_mx2[tid] = 0u;
     phase ^= 1u;
   }
-  // the two slices produced ahead of the last consumed one must land before exit
+  // the slices produced ahead of the last consumed one must land before exit
   if (issuer && stream_ok && int(blockIdx.x) < ntiles)
-    for (uint32_t j = jstep; j < jstep + 2u; ++j)
+    for (uint32_t j = jstep; j < jstep + uint32_t(kSlots - 1); ++j)
       umma::mbar_wait_bounded(full + j % uint32_t(kSlots), (j / uint32_t(kSlots)) & 1u);
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, T::TCOLS);
@@ -542,15 +568,15 @@ std::vector<uint8_t> build_stream(const RefOps &o, bool bf16) {
     std::memcpy(&blk[base_lo + off], &lb, 2);
   };
   const std::vector<double> *Ds[3] = {&o.Dr, &o.Ds, &o.Dt};
-  for (int kk = 0; kk < T::KS1; ++kk) {
-    const size_t hi = slice_offset<N>(kk), lo = hi + size_t(3) * T::NB * 32;
-    for (int d = 0; d < 3; ++d)
+  for (int kk = 0; kk < T::KS1; ++kk)
+    for (int d = 0; d < 3; ++d) {
+      const size_t hi = slice_offset<N>(kk) + size_t(d) * T::SUB, lo = hi + size_t(T::NB) * 32;
       for (int i = 0; i < T::NP; ++i)
         for (int k = 0; k < 16 && 16 * kk + k < T::NP; ++k)
-          put(hi, lo, d * T::NB + i, k, (*Ds[d])[size_t(i) * T::NP + 16 * kk + k]);
-  }
+          put(hi, lo, i, k, (*Ds[d])[size_t(i) * T::NP + 16 * kk + k]);
+    }
   for (int kk = 0; kk < T::KS2; ++kk) {
-    const size_t hi = slice_offset<N>(T::KS1 + kk), lo = hi + size_t(T::NB) * 32;
+    const size_t hi = slice_offset<N>(T::KS1 + kk / T::G2) + size_t(kk % T::G2) * T::SUB, lo = hi + size_t(T::NB) * 32;
     for (int i = 0; i < T::NP; ++i)
       for (int k = 0; k < 16 && 16 * kk + k < T::NFF; ++k)
         put(hi, lo, i, k, o.LIFT[size_t(i) * T::NFF + 16 * kk + k]);
