@@ -21,8 +21,10 @@
 // of the three derivative directions (N = NB columns each); GEMM2 takes
 // ceil(K2/48) slices. TMEM holds [ur | us | ut | lifted flux] = 4 NB columns (all 512 at
 // N = 7). A1 and A2 share one shared-memory region: A2 is written once GEMM1
-// has completed. The residual is read and the results are written directly
-// between registers and global memory.
+// has completed, and after GEMM2 the same bytes take the new residual (or the
+// right-hand side) while the new fields overwrite the staged ones; both go out
+// as bulk stores whose drain overlaps the next tile's loads. The residual is
+// read straight from global memory (warmed in L2 one tile ahead).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -87,7 +89,8 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   using T = TS<N>;
   constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, FS = T::FS, NB = T::NB;
   extern __shared__ __align__(1024) uint8_t smem[];
-  float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);
+  float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);  // fields; the new fields after the epilogue
+  float *s_out = reinterpret_cast<float *>(smem);           // [6][FS] new residual / rhs (A region)
   float4 *s_face = reinterpret_cast<float4 *>(smem + T::OFF_FACE); // {n, Fs}, {wE, wH, Z+, Y+}, {k2, conn}
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
@@ -216,39 +219,41 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     bool ok = true;
     if (tid == 32) prefetch(tile + int(gridDim.x), tile);
 
-    // ---- 1. fields and face table of the tile; staging and A1 (the previous
-    // tile's last barrier ordered every earlier read of these bytes)
-    {
-      float4 v[R1];
-      float mx = 0.f;
+    // ---- 1. fields and face table of the tile into registers; once the
+    // previous tile's bulk stores have read shared memory, the staging and A1
+    float4 v[R1];
+    float mx = 0.f;
 #pragma unroll
-      for (int s = 0; s < R1; ++s) {
-        const int k = kq1 + 16 * s;
-        v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (cr1 >= 0 && k < NPP && e1 < ne) {
-          v[s] = ldg4(a.u + f1 * KN + (k0 + e1) * NPP + k);
-          if (k + 3 >= NP) {
-            if (k + 0 >= NP) v[s].x = 0.f;
-            if (k + 1 >= NP) v[s].y = 0.f;
-            if (k + 2 >= NP) v[s].z = 0.f;
-            if (k + 3 >= NP) v[s].w = 0.f;
-          }
+    for (int s = 0; s < R1; ++s) {
+      const int k = kq1 + 16 * s;
+      v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (cr1 >= 0 && k < NPP && e1 < ne) {
+        v[s] = ldg4(a.u + f1 * KN + (k0 + e1) * NPP + k);
+        if (k + 3 >= NP) {
+          if (k + 0 >= NP) v[s].x = 0.f;
+          if (k + 1 >= NP) v[s].y = 0.f;
+          if (k + 2 >= NP) v[s].z = 0.f;
+          if (k + 3 >= NP) v[s].w = 0.f;
         }
-        if constexpr (!BF16) mx = absmax4(mx, v[s]);
       }
-      if (tid < kTileS * 4) {
-        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 1.f, 1.f);
-        int2 cn = make_int2(0, kBoundaryConn);
-        if ((tid >> 2) < ne) {
-          const int64_t q = (k0 + (tid >> 2)) * 4 + (tid & 3);
-          cn = __ldg(a.fconn + q);
-          g0 = __ldg(a.fgeo + q);
-          g1 = __ldg(a.fmat + q);
-        }
-        s_face[tid * 3 + 0] = g0;
-        s_face[tid * 3 + 1] = g1;
-        s_face[tid * 3 + 2] = make_float4(__int_as_float(cn.x), __int_as_float(cn.y), 0.f, 0.f);
+      if constexpr (!BF16) mx = absmax4(mx, v[s]);
+    }
+    if (tid < kTileS * 4) {
+      float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 1.f, 1.f);
+      int2 cn = make_int2(0, kBoundaryConn);
+      if ((tid >> 2) < ne) {
+        const int64_t q = (k0 + (tid >> 2)) * 4 + (tid & 3);
+        cn = __ldg(a.fconn + q);
+        g0 = __ldg(a.fgeo + q);
+        g1 = __ldg(a.fmat + q);
       }
+      s_face[tid * 3 + 0] = g0;
+      s_face[tid * 3 + 1] = g1;
+      s_face[tid * 3 + 2] = make_float4(__int_as_float(cn.x), __int_as_float(cn.y), 0.f, 0.f);
+    }
+    if (issuer) umma::bulk_wait_read_all();
+    __syncthreads();
+    {
       float sc1 = 1.f, inv1r = 1.f;
       if constexpr (!BF16) {
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     umma::fence_after_sync();
 
     // ---- 7. epilogue: chain rule (eq. dg-reference-matrices), curls, lifted
-    // flux, material scale, update; results straight to global memory
+    // flux, material scale, update; results to shared memory
 #pragma unroll
     for (int c = 0; c < CPP; ++c) {
       const int ch = ch0 + c;
@@ -515,9 +520,10 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 #pragma unroll
             for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? (vol[4 * h + q] + lf[4 * h + q] * inv2) * w : 0.f;
             if (MODE == MODE_RHS) {
-              *reinterpret_cast<float4 *>(a.rhs + fld * KN + k * NPP + i) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+              *reinterpret_cast<float4 *>(s_out + soff + i) = make_float4(r4[0], r4[1], r4[2], r4[3]);
             } else {
-              const float4 uo = *reinterpret_cast<const float4 *>(s_u + soff + i);
+              float4 *up = reinterpret_cast<float4 *>(s_u + soff + i);
+              const float4 uo = *up;
               const float uov[4] = {uo.x, uo.y, uo.z, uo.w};
               float nr[4], nu[4];
 #pragma unroll
@@ -526,18 +532,32 @@ __global__ void __launch_bounds__(kThreadsS, 1)
                 nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[4 * h + q], a.dt * r4[q]);
                 nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
               }
-              *reinterpret_cast<float4 *>(a.res + fld * KN + k * NPP + i) = make_float4(nr[0], nr[1], nr[2], nr[3]);
-              *reinterpret_cast<float4 *>(a.u_out + fld * KN + k * NPP + i) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+              *reinterpret_cast<float4 *>(s_out + soff + i) = make_float4(nr[0], nr[1], nr[2], nr[3]);
+              *up = make_float4(nu[0], nu[1], nu[2], nu[3]);
             }
           }
         }
       }
     }
+    umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
+    if (issuer) {
+      const uint32_t rowbytes = uint32_t(ne * NPP * 4);
+      for (int f = 0; f < 6; ++f) {
+        if (MODE == MODE_RHS) {
+          umma::bulk_s2g(a.rhs + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
+        } else {
+          umma::bulk_s2g(a.res + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
+          umma::bulk_s2g(a.u_out + f * KN + k0 * NPP, s_u + f * FS, rowbytes);
+        }
+      }
+      umma::bulk_commit();
+    }
     if (!BF16 && tid < 8) s_mx2[tid] = 0u;
     phase ^= 1u;
   }
+  if (issuer) umma::bulk_wait_all();
   // the slices produced ahead of the last consumed one must land before exit
   if (issuer && stream_ok && int(blockIdx.x) < ntiles)
     for (uint32_t j = jstep; j < jstep + uint32_t(kSlots - 1); ++j)
