@@ -182,10 +182,22 @@ int dg_ensemble_tuning(const dg_ctx *ctx, int *best_eb, int *eb, float *ms_per_s
 int dg_ensemble_graph_used(const dg_ctx *ctx);
 
 /* Wait for all work enqueued on the context's stream and report device-side
- * failures: returns DG_ERR_TIMEOUT (and clears the flag) if a tensor-core
- * kernel gave up waiting for its matrix units after its iteration limit
- * (about one second), DG_ERR_CUDA if the stream reports an error. */
+ * failures: returns DG_ERR_TIMEOUT (and clears the flag) if a kernel gave up
+ * on a device-side wait (a tensor-core kernel on its MMA or copy barriers, the
+ * ensemble launch on its grid barrier) after the wait limit, DG_ERR_CUDA if the
+ * stream reports an error. After a timeout the work of that launch is
+ * incomplete (its outputs are unspecified) but the context stays usable. */
 int dg_sync(dg_ctx *ctx);
+
+/* Device-side watchdog: every bounded wait of the stage kernels (tensor-core
+ * barriers, the ensemble grid barrier) gives up after `cycles` SM clock cycles;
+ * 0 restores the default of 2^31 cycles (about one second). A limit shorter
+ * than the work waited for makes the launch give up and dg_sync return
+ * DG_ERR_TIMEOUT: the failure-detection path, exercised without a GPU fault.
+ * Waits that only drain copies or matrix operations already in flight before
+ * a kernel exits keep the default limit. Drops a captured ensemble graph.
+ * Returns DG_ERR_ARG for a negative limit. */
+int dg_set_wait_limit(dg_ctx *ctx, long long cycles);
 
 /* Transpose of the right-hand-side operator in the Euclidean inner product,
  * w = A(eps)^T v (DEVICE field vectors, no aliasing), in FP32 on the CUDA

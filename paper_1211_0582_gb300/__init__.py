@@ -57,6 +57,7 @@ def lib():
             L.dg_step.argtypes = [vp, vp, vp, dbl, i32, flt]
             L.dg_energy.argtypes = [vp, vp, C.POINTER(dbl)]
             L.dg_sync.argtypes = [vp]
+            L.dg_set_wait_limit.argtypes = [vp, C.c_longlong]
             L.dg_step_noalloc.argtypes = [vp, vp, vp, dbl, i32, flt]
             L.dg_rhs_transpose.argtypes = [vp, vp, vp, flt]
             L.dg_ensemble_upload.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -234,6 +235,10 @@ class Solver:
 
     def sync(self):
         self._check(lib().dg_sync(self._h))
+
+    def set_wait_limit(self, cycles: int):
+        """Device-side wait limit in SM cycles (0 = default, about one second)."""
+        self._check(lib().dg_set_wait_limit(self._h, int(cycles)))
 
     def energy(self, u) -> float:
         E = C.c_double()

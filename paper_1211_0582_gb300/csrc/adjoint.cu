@@ -508,6 +508,7 @@ StageArgs stage_base(const dg_ctx *c, float alpha, double dt) {
   a.fgeo = c->d_fgeo;
   a.fconn = c->d_fconn;
   a.fmat = c->d_fmat;
+  a.wait_limit = c->wait_limit;
   a.DT = c->d_DT;
   a.LT = c->d_LT;
   a.fmask = c->d_tab;

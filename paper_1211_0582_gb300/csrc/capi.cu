@@ -85,6 +85,7 @@ StageArgs base_args(const dg_ctx *c) {
   a.fgeo = c->d_fgeo;
   a.fconn = c->d_fconn;
   a.fmat = c->d_fmat;
+  a.wait_limit = c->wait_limit;
   a.DT = c->d_DT;
   a.LT = c->d_LT;
   a.fmask = c->d_tab;
@@ -385,7 +386,22 @@ int dg_sync(dg_ctx *ctx) {
   e = cudaMemcpy(&flag, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && flag) e = cudaMemcpy(ctx->d_flag + 1, &zero, sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_err(ctx, e, "dg_sync");
-  if (flag) return set_err(ctx, DG_ERR_TIMEOUT, "a tensor-core kernel timed out waiting for its MMA completion barrier");
+  if (flag) {
+    // blocks of a persistent launch that gave up leave its grid barrier half-counted
+    e = ensemble_reset_barrier(ctx);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "dg_sync");
+    return set_err(ctx, DG_ERR_TIMEOUT,
+                   "a device wait timed out (tensor-core MMA / copy barrier or ensemble grid barrier)");
+  }
+  return DG_OK;
+}
+
+int dg_set_wait_limit(dg_ctx *ctx, long long cycles) {
+  if (!ctx) return DG_ERR_ARG;
+  if (cycles < 0) return set_err(ctx, DG_ERR_ARG, "dg_set_wait_limit: negative limit");
+  ctx->wait_limit = cycles;
+  ensemble_drop_graph(ctx); // a captured ensemble launch carries the old limit
   return DG_OK;
 }
 

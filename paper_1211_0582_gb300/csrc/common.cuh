@@ -31,6 +31,7 @@ struct StageArgs {
   const float4 *fgeo;  // [K][4] {nx, ny, nz, Fscale}
   const int2 *fconn;   // [K][4] {neighbour element, connection kind}
   const float4 *fmat;  // [K][4] {Fscale/(Z-+Z+), -Fscale/(Y-+Y+), Z+, Y+} flux weights per face
+  long long wait_limit; // device waits give up after this many SM cycles (0 = default, ~1 s)
   const float *DT;     // [3][Np][Npad]  transposed Dr, Ds, Dt
   const float *LT;     // [4Nfp][Npad]   transposed LIFT
   const uint8_t *fmask;  // [4Nfp]  volume node of each face node
@@ -60,6 +61,11 @@ cudaError_t launch_set_eps(int64_t K, const float *eps, float *geo, int *bad, cu
 cudaError_t launch_face_weights(int64_t K, const float *geo, const float4 *fgeo, const int2 *fconn, float4 *fmat,
                                 cudaStream_t s);
 void ensemble_free(dg_ctx *ctx);
+// Re-arms the ensemble grid barrier after a timed-out launch (blocks that gave
+// up leave its arrival count behind).
+cudaError_t ensemble_reset_barrier(dg_ctx *ctx);
+// Drops the captured graph of the ensemble step (its arguments changed).
+void ensemble_drop_graph(dg_ctx *ctx);
 cudaError_t launch_energy(int N, int64_t K, int Npad, const float *u, const float *geo, const double *M,
                           double *out, cudaStream_t s);
 
@@ -94,6 +100,7 @@ struct dg_ctx {
   float *d_scratch = nullptr;  // field vector for the LSERK stage ping-pong
   double *d_red = nullptr;     // reduction outputs
   int *d_flag = nullptr;
+  long long wait_limit = 0;    // device-wait limit in SM cycles for the stage kernels (0 = default)
   void *tc = nullptr;          // tensor-core operator buffers (precision != DG_FP32)
   void *ens = nullptr;         // ensemble state (dg_ensemble_upload)
   std::vector<double> host_vert;   // VX, VY, VZ (kept for node coordinates)

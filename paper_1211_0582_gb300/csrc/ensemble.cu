@@ -128,6 +128,7 @@ StageArgs ens_args(const dg_ctx *c, float alpha) {
   a.fgeo = c->d_fgeo;
   a.fconn = c->d_fconn;
   a.fmat = c->d_fmat;
+  a.wait_limit = c->wait_limit;
   a.DT = c->d_DT;
   a.LT = c->d_LT;
   a.fmask = c->d_tab;
@@ -166,6 +167,17 @@ void free_graph(EnsembleState &st) {
 }
 
 } // namespace
+
+cudaError_t ensemble_reset_barrier(dg_ctx *c) {
+  EnsembleState *st = state(c);
+  if (!st || !st->gb) return cudaSuccess;
+  return cudaMemsetAsync(st->gb, 0, sizeof(GridBarrier), c->stream);
+}
+
+void ensemble_drop_graph(dg_ctx *c) {
+  EnsembleState *st = state(c);
+  if (st) free_graph(*st);
+}
 
 void ensemble_free(dg_ctx *c) {
   EnsembleState *st = state(c);

@@ -19,8 +19,8 @@ struct GridBarrier {
 };
 
 // Sense-free generation barrier over all blocks of a cooperative launch.
-// Gives up after about 2^31 cycles (~1 s) and returns false.
-__device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
+// Gives up after `limit` cycles and returns false.
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -36,7 +36,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
     } else {
       const long long t0 = clock64();
       while (*vgen == my_gen) {
-        if (clock64() - t0 > (1ll << 31)) {
+        if (clock64() - t0 > limit) {
           ok = 0;
           break;
         }
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(SimtCfg<N, EB>::NT)
         __syncthreads(); // shared memory of the previous tile is no longer read
         simt_stage_tile<N, MODE_LSERK, EB, true>(a, t * EB, smem4);
       }
-      if (!grid_barrier(gb)) {
+      if (!grid_barrier(gb, a.wait_limit > 0 ? a.wait_limit : (1ll << 31))) {
         if (threadIdx.x == 0) atomicExch(err_flag, 1);
         return;
       }

@@ -88,6 +88,7 @@ extern "C" int dg_step_noalloc(dg_ctx *ctx, float *u, float *res, double dt, int
   a.fgeo = ctx->d_fgeo;
   a.fconn = ctx->d_fconn;
   a.fmat = ctx->d_fmat;
+  a.wait_limit = ctx->wait_limit;
   a.DT = ctx->d_DT;
   a.LT = ctx->d_LT;
   a.fmask = ctx->d_tab;

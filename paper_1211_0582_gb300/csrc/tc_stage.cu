@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *barR = bar1 + 2;                                        // residual tile landed
   uint64_t *barU = bar1 + 3;                                        // fields and face data of a tile landed
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 32);
+  volatile int *s_staged = reinterpret_cast<volatile int *>(smem + T::OFF_BAR + 36); // next tile's copies issued
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // single-thread roles sit in the last four warps, which have the least flux
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool storer = tid == kThreads - 128;
   const int64_t KN = a.K * NPP;
   const uint32_t sbase = umma::smem_u32(smem);
+  const long long wlim = umma::wait_cycles(a.wait_limit); // main waits; drains use the default
 
   // fields of tile t into the A1 bytes, its face and element data into a
   // slot (one thread; completes on barU)
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- 1. the staged fields into registers; once the previous tile's bulk
     // stores have read shared memory, the residual copy starts and the fields
     // go to the tile staging and (split) to the A1 operand
-    const bool okU = umma::mbar_wait_bounded(barU, phase);
+    const bool okU = umma::mbar_wait_bounded(barU, phase, wlim);
     float4 v[R1];
     float mx = 0.f;
 #pragma unroll
@@ -367,8 +369,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // once GEMM1 has read A1, the next tile's fields and face data are staged
     if (stager) {
-      ok = umma::mbar_wait_bounded(bar1, phase);
-      if (ok && tile + int(gridDim.x) < ntiles) stage_tile(tile + gridDim.x, slot ^ 1);
+      ok = umma::mbar_wait_bounded(bar1, phase, wlim);
+      const bool more = ok && tile + int(gridDim.x) < ntiles;
+      if (more) stage_tile(tile + gridDim.x, slot ^ 1);
+      *s_staged = more ? 1 : 0;
     }
     if constexpr (!BF16) {
       // one FP16 scale per field component of the tile: |x| as float bits
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       inv1 = s_inv1[lane_used ? ridx : 0];
       row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
     }
-    ok = umma::mbar_wait_bounded(bar1, phase) && ok;
+    ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
     umma::fence_after_sync();
     float vol[CPP][8];
 #pragma unroll
@@ -466,8 +470,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
       }
     }
-    ok = umma::mbar_wait_bounded(bar2, phase) && ok;
-    if (MODE == MODE_LSERK) ok = umma::mbar_wait_bounded(barR, phase) && ok;
+    ok = umma::mbar_wait_bounded(bar2, phase, wlim) && ok;
+    if (MODE == MODE_LSERK) ok = umma::mbar_wait_bounded(barR, phase, wlim) && ok;
     // this slot's face and element data are rewritten by the staging after next
     umma::fence_proxy_async();
     if (__syncthreads_or(!ok)) {
@@ -477,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // before tensor and shared memory are released
         umma::mbar_wait_bounded(bar2, phase);
         if (MODE == MODE_LSERK) umma::mbar_wait_bounded(barR, phase);
-        if (tile + int(gridDim.x) < ntiles) umma::mbar_wait_bounded(barU, phase ^ 1u);
+        if (*s_staged) umma::mbar_wait_bounded(barU, phase ^ 1u);
       }
       break;
     }

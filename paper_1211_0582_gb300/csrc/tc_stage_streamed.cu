@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   const bool issuer = warp == kMmaWarp && lane == 0;
   const int64_t KN = a.K * NPP;
   const uint32_t sbase = umma::smem_u32(smem);
+  const long long wlim = umma::wait_cycles(a.wait_limit); // main waits; drains use the default
 
   // ---- one-time setup
   for (int i = tid; i < T::AREG / 16; i += kThreadsS) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -130,34 +131,38 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 
   // operator stream (issuer only): step j of the periodic slice sequence
   // goes to slot j % kSlots
-  uint32_t jstep = 0;
+  uint32_t jstep = 0; // next step to consume
+  uint32_t jprod = 0; // next step to produce (steps are produced in order)
   auto produce = [&](uint32_t j) {
     const int st = int(j % uint32_t(T::PER)), slot = int(j % uint32_t(kSlots));
     umma::mbar_arrive_expect_tx(full + slot, uint32_t(T::SL));
     umma::bulk_g2s(smem + T::OFF_RING + slot * T::SL, stream + slice_offset<N>(st), uint32_t(T::SL), full + slot);
+    jprod = j + 1u;
   };
   // wait for step jstep's slice, issue its MMAs, release the slot when they
   // complete, and refill the previous step's slot with the step kSlots ahead;
-  // after a timed-out wait nothing more is waited for or issued
+  // after a timed-out wait nothing more is waited for or issued (the slices
+  // still in flight are waited for before the kernel exits)
   bool stream_ok = true;
   auto consume = [&](auto &&issue) -> bool {
+    if (!stream_ok) return false;
     const int slot = int(jstep % uint32_t(kSlots));
-    if (!stream_ok) {
-      ++jstep;
+    if (!umma::mbar_wait_bounded(full + slot, (jstep / uint32_t(kSlots)) & 1u, wlim)) {
+      stream_ok = false;
       return false;
     }
-    bool ok = umma::mbar_wait_bounded(full + slot, (jstep / uint32_t(kSlots)) & 1u);
     umma::fence_after_sync();
-    if (ok) issue(sbase + uint32_t(T::OFF_RING + slot * T::SL));
+    issue(sbase + uint32_t(T::OFF_RING + slot * T::SL));
     umma::commit(empty + slot);
     if (jstep >= 1u) {
       const uint32_t pj = jstep - 1u;
-      ok = umma::mbar_wait_bounded(empty + pj % uint32_t(kSlots), (pj / uint32_t(kSlots)) & 1u) && ok;
-      if (ok) produce(pj + uint32_t(kSlots));
+      if (umma::mbar_wait_bounded(empty + pj % uint32_t(kSlots), (pj / uint32_t(kSlots)) & 1u, wlim))
+        produce(pj + uint32_t(kSlots));
+      else
+        stream_ok = false;
     }
     ++jstep;
-    stream_ok = ok;
-    return ok;
+    return stream_ok;
   };
   if (issuer && int(blockIdx.x) < ntiles)
     for (int j = 0; j < kSlots; ++j) produce(uint32_t(j));
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       }
     }
     // A2 overwrites A1: GEMM1 must have completed
-    ok = umma::mbar_wait_bounded(bar1, phase) && ok;
+    ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
     __syncthreads();
 
     // ---- 5. split the face fluxes into the A2 operand
@@ -476,9 +481,12 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     };
     float4 rn0, rn1;
     load_res(ch0, rn0, rn1);
-    ok = umma::mbar_wait_bounded(bar2, phase) && ok;
+    ok = umma::mbar_wait_bounded(bar2, phase, wlim) && ok;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicExch(err_flag, 1);
+      // the matrix operations issued for this tile complete before tensor
+      // memory is released (bar2 is committed after them in every case)
+      if (issuer) umma::mbar_wait_bounded(bar2, phase);
       break;
     }
     umma::fence_after_sync();
@@ -558,9 +566,9 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     phase ^= 1u;
   }
   if (issuer) umma::bulk_wait_all();
-  // the slices produced ahead of the last consumed one must land before exit
-  if (issuer && stream_ok && int(blockIdx.x) < ntiles)
-    for (uint32_t j = jstep; j < jstep + uint32_t(kSlots - 1); ++j)
+  // the slices produced but not consumed must land before exit
+  if (issuer)
+    for (uint32_t j = jstep; j < jprod; ++j)
       umma::mbar_wait_bounded(full + j % uint32_t(kSlots), (j / uint32_t(kSlots)) & 1u);
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, T::TCOLS);

@@ -144,13 +144,36 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Bounded wait: gives up after about 2^31 SM cycles (~1 s) and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr long long kDefaultWaitCycles = 1ll << 31; // ~1 s at 2 GHz
+
+// Bounded wait: gives up after `limit` SM cycles and returns false. A phase
+// that has not completed at the first (non-blocking) test is waited for only
+// while the limit has not passed, so a tiny limit fails deterministically.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit = kDefaultWaitCycles) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (clock64() - t0 > limit) return false;
+    if (mbar_try_wait(bar, parity)) return true;
   }
-  return true;
+}
+
+// The wait limit a kernel argument asks for (0 = the default).
+__host__ __device__ constexpr long long wait_cycles(long long requested) {
+  return requested > 0 ? requested : kDefaultWaitCycles;
 }
 
 } // namespace umma

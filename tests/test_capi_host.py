@@ -86,3 +86,13 @@ def test_mesh_validation_on_host():
     # no mesh yet: the field entry points refuse
     L = dg.lib()
     assert L.dg_rhs(s._h, None, None, 1.0) == -1
+
+
+def test_wait_limit_validation_on_host():
+    s = dg.Solver(3, stream=None)
+    s.set_wait_limit(0)
+    s.set_wait_limit(1 << 20)
+    with pytest.raises(dg.DGError) as e:
+        s.set_wait_limit(-1)
+    assert e.value.code == -1
+    assert dg.lib().dg_set_wait_limit(None, 5) == -1
