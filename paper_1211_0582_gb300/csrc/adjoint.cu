@@ -31,7 +31,8 @@ namespace dgmx {
 
 struct AdjArgs {
   const float *lr_in;  // lambda_r (read)
-  float *lr_out;       // k_adj_lift: lr + b lu (may alias lr_in, may be null); k_adj_vol: a * lr
+  float *lr_out;       // k_adj_lift: lr_scale lr + b lu (may alias lr_in, may be null); k_adj_vol: a * lr (may be null)
+  float lr_scale;      // k_adj_lift: the factor a of the stage reversed before, still to be applied to lr
   const float *lu_in;  // lambda_u (read; null = 0)
   float *lu_out;       // k_adj_vol: lu + dt A^T lr
   float *g;            // face data [6][K][NFF]
@@ -59,8 +60,7 @@ struct AdjCfg {
   static constexpr int EB2 = 240 / D::NQ;                     // elements per volume block
   static constexpr int NT2 = (EB2 * D::NQ + 31) / 32 * 32;
   static constexpr size_t SMEM1 = size_t(6) * EB1 * D::NPP * 4;
-  static constexpr size_t SMEM2 =
-      (size_t(6) * EB2 * D::NPP * 2 + size_t(18) * EB2 * D::NPP + EB2) * 4 + ((200 * D::NFP + 15) / 16) * 16;
+  static constexpr size_t SMEM2 = (size_t(6) * EB2 * D::NPP * 3 + EB2) * 4 + ((200 * D::NFP + 15) / 16) * 16;
 };
 
 __device__ __forceinline__ void cross3(const float *a, const float *b, float *c) {
@@ -116,7 +116,8 @@ __device__ __forceinline__ void flux_weight_partials(const float *n, const float
   }
 }
 
-// ---- 1. lr <- lr + b lu (own element) and g = Fscale * LIFT^T (W lr)
+// ---- 1. lr <- s lr + b lu (own element; s = the previous stage's a, applied
+// here instead of as a separate pass) and g = Fscale * LIFT^T (W lr)
 template <int N>
 __global__ void __launch_bounds__(AdjCfg<N>::NT1) k_adj_lift(AdjArgs a) {
   using D = Dims<N>;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT1) k_adj_lift(AdjArgs a) {
     if (k < a.K) {
       const int64_t off = c * KN + k * NPP + 4 * q;
       v = *reinterpret_cast<const float4 *>(a.lr_in + off);
+      v.x *= a.lr_scale, v.y *= a.lr_scale, v.z *= a.lr_scale, v.w *= a.lr_scale;
       if (a.lu_in) {
         const float4 lu = *reinterpret_cast<const float4 *>(a.lu_in + off);
         v.x = fmaf(a.b, lu.x, v.x), v.y = fmaf(a.b, lu.y, v.y), v.z = fmaf(a.b, lu.z, v.z), v.w = fmaf(a.b, lu.w, v.w);
@@ -190,8 +192,8 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
   extern __shared__ float4 smem4[];
   float *s_v = reinterpret_cast<float *>(smem4); // W lr   [6][EB][NPP]
   float *s_w = s_v + 6 * EB * NPP;               // surface contributions [6][EB][NPP]
-  float *s_q = s_w + 6 * EB * NPP;               // contravariant combinations [18][EB][NPP]
-  float *s_gr = s_q + 18 * EB * NPP;             // gradient partial per element [EB]
+  float *s_us = s_w + 6 * EB * NPP;              // stage state u_s of the block's elements [6][EB][NPP]
+  float *s_gr = s_us + 6 * EB * NPP;             // gradient partial per element [EB]
   uint8_t *s_fm = reinterpret_cast<uint8_t *>(s_gr + EB);
   uint8_t *s_nb = s_fm + NFF, *s_nf = s_nb + kConnKinds * NFP;
   const int tid = threadIdx.x;
@@ -219,6 +221,9 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
     }
     reinterpret_cast<float4 *>(s_v)[(c * EB + e) * NQ + q] = v;
     reinterpret_cast<float4 *>(s_w)[(c * EB + e) * NQ + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (GRAD)
+      reinterpret_cast<float4 *>(s_us)[(c * EB + e) * NQ + q] =
+          k < a.K ? *reinterpret_cast<const float4 *>(a.u_s + c * KN + k * NPP + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
 
@@ -232,30 +237,6 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
       const float4 r = *reinterpret_cast<const float4 *>(a.rhs_s + c * KN + k * NPP + 4 * q);
       const float4 v = reinterpret_cast<const float4 *>(s_v)[(c * EB + e) * NQ + q];
       atomicAdd(&s_gr[e], -(v.x * r.x + v.y * r.y + v.z * r.z + v.w * r.w));
-    }
-  }
-
-  // -- contravariant combinations q_{T,d} = sum_l (dr_d/dx_l) (+-W lr) of the transposed curl:
-  //    H_c <- d_{c+2}^T (W lr)_{E_{c+1}} - d_{c+1}^T (W lr)_{E_{c+2}}
-  //    E_c <- -d_{c+2}^T (W lr)_{H_{c+1}} + d_{c+1}^T (W lr)_{H_{c+2}}
-  for (int idx = tid; idx < EB * NPP; idx += NT) {
-    const int e = idx / NPP, i = idx - e * NPP;
-    const int64_t k = k0 + e;
-    float G[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) G[t] = k < a.K ? __ldg(a.geo + k * G_STRIDE + t) : 0.f;
-    float v[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) v[c] = s_v[(c * EB + e) * NPP + i];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float g1 = G[3 * d + c1], g2 = G[3 * d + c2];
-        s_q[((3 + c) * 3 + d) * EB * NPP + e * NPP + i] = g2 * v[c1] - g1 * v[c2];
-        s_q[(c * 3 + d) * EB * NPP + e * NPP + i] = -g2 * v[3 + c1] + g1 * v[3 + c2];
-      }
     }
   }
 
@@ -313,7 +294,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
       const float dZ = -Zk / (2.f * ek), dY = Yk / (2.f * ek);
       float qm[6], qp[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) qm[c] = __ldg(a.u_s + c * KN + k * NPP + vm);
+      for (int c = 0; c < 6; ++c) qm[c] = s_us[(c * EB + e) * NPP + vm];
       if (wall) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -322,8 +303,14 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
         }
       } else {
         const int vn = s_nb[cn.y * NFP + m];
+        const int64_t e2 = k2 - k0; // neighbours inside the block come from shared memory
+        if (e2 >= 0 && e2 < EB) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) qp[c] = __ldg(a.u_s + c * KN + k2 * NPP + vn);
+          for (int c = 0; c < 6; ++c) qp[c] = s_us[(c * EB + int(e2)) * NPP + vn];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qp[c] = __ldg(a.u_s + c * KN + k2 * NPP + vn);
+        }
       }
       float sZm, sZp, sYm, sYp;
       flux_weight_partials(n, qm, qp, Zk, Z2, Yk, Y2, a.alpha, gk, sZm, sZp, sYm, sYp);
@@ -341,27 +328,44 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
   }
   __syncthreads();
 
-  // -- transposed volume term: w_T[j] = sum_d sum_i D_d[i][j] q_{T,d}[i]
+  // -- transposed volume term: w_T[j] = sum_d sum_i D_d[i][j] q_{T,d}[i] with
+  //    the contravariant combinations q_{T,d} = sum_l (dr_d/dx_l) (+-W lr) of
+  //    the transposed curl formed per node from the element's metric terms:
+  //    H_c <- d_{c+2}^T (W lr)_{E_{c+1}} - d_{c+1}^T (W lr)_{E_{c+2}}
+  //    E_c <- -d_{c+2}^T (W lr)_{H_{c+1}} + d_{c+1}^T (W lr)_{H_{c+2}}
   const int e = tid / NQ, q = tid - (tid / NQ) * NQ;
   const int64_t k = k0 + e;
   if (tid < EB * NQ && k < a.K) {
+    float G[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) G[t] = __ldg(a.geo + k * G_STRIDE + t);
     float acc[6][4];
 #pragma unroll
     for (int c = 0; c < 6; ++c)
 #pragma unroll
       for (int n = 0; n < 4; ++n) acc[c][n] = 0.f;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
 #pragma unroll 2
-      for (int i = 0; i < NP; ++i) {
+    for (int i = 0; i < NP; ++i) {
+      float v[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[c] = s_v[(c * EB + e) * NPP + i];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
         const float4 Dv = ldg4(a.Dn + (d * NP + i) * NPP + 4 * q);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const float qv = s_q[(c * 3 + d) * EB * NPP + e * NPP + i];
-          acc[c][0] = fmaf(Dv.x, qv, acc[c][0]);
-          acc[c][1] = fmaf(Dv.y, qv, acc[c][1]);
-          acc[c][2] = fmaf(Dv.z, qv, acc[c][2]);
-          acc[c][3] = fmaf(Dv.w, qv, acc[c][3]);
+        for (int c = 0; c < 3; ++c) {
+          const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+          const float g1 = G[3 * d + c1], g2 = G[3 * d + c2];
+          const float qH = g2 * v[c1] - g1 * v[c2];         // into H_c
+          const float qE = -g2 * v[3 + c1] + g1 * v[3 + c2]; // into E_c
+          acc[3 + c][0] = fmaf(Dv.x, qH, acc[3 + c][0]);
+          acc[3 + c][1] = fmaf(Dv.y, qH, acc[3 + c][1]);
+          acc[3 + c][2] = fmaf(Dv.z, qH, acc[3 + c][2]);
+          acc[3 + c][3] = fmaf(Dv.w, qH, acc[3 + c][3]);
+          acc[c][0] = fmaf(Dv.x, qE, acc[c][0]);
+          acc[c][1] = fmaf(Dv.y, qE, acc[c][1]);
+          acc[c][2] = fmaf(Dv.z, qE, acc[c][2]);
+          acc[c][3] = fmaf(Dv.w, qE, acc[c][3]);
         }
       }
     }
@@ -469,23 +473,39 @@ int fail(dg_ctx *ctx, int code, const std::string &msg) {
   return code;
 }
 
-// Owns the temporary device buffers of one adjoint call.
-struct DevBufs {
-  std::vector<void *> ptrs;
-  ~DevBufs() {
-    for (void *p : ptrs) cudaFree(p);
-  }
+// Device work buffers of the adjoint and receiver-trace calls, kept in the
+// context between calls (an optimisation loop calls them many times) and grown
+// on demand; released with the mesh.
+struct AdjWorkspace {
+  static constexpr int kSlots = 16;
+  void *p[kSlots] = {};
+  size_t cap[kSlots] = {};
   template <class T>
-  T *get(size_t count) {
-    void *p = nullptr;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
+  T *get(int slot, size_t count) {
+    const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+    if (cap[slot] < bytes) {
+      if (p[slot]) cudaFree(p[slot]);
+      p[slot] = nullptr;
+      cap[slot] = 0;
+      if (cudaMalloc(&p[slot], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p[slot] = nullptr;
+        return nullptr;
+      }
+      cap[slot] = bytes;
     }
-    ptrs.push_back(p);
-    return static_cast<T *>(p);
+    return static_cast<T *>(p[slot]);
+  }
+  ~AdjWorkspace() {
+    for (void *q : p)
+      if (q) cudaFree(q);
   }
 };
+
+AdjWorkspace &workspace(dg_ctx *c) {
+  if (!c->adj) c->adj = new AdjWorkspace();
+  return *static_cast<AdjWorkspace *>(c->adj);
+}
 
 AdjArgs adj_base(const dg_ctx *c, float alpha) {
   AdjArgs a{};
@@ -499,6 +519,7 @@ AdjArgs adj_base(const dg_ctx *c, float alpha) {
   a.nbrface = c->d_tab + 4 * c->ops.Nfp + kConnKinds * c->ops.Nfp;
   a.K = c->K;
   a.alpha = alpha;
+  a.lr_scale = 1.f;
   return a;
 }
 
@@ -541,6 +562,12 @@ int check_common(dg_ctx *ctx, const float *u0, double dt, int nsteps, float alph
 }
 
 } // namespace
+
+void adjoint_free(dg_ctx *c) {
+  delete static_cast<AdjWorkspace *>(c->adj);
+  c->adj = nullptr;
+}
+
 } // namespace dgmx
 
 using namespace dgmx;
@@ -555,8 +582,7 @@ int dg_rhs_transpose(dg_ctx *ctx, const float *v, float *w, float alpha) {
   const size_t bytes = size_t(6) * ctx->K * ctx->ops.Npad * sizeof(float);
   const uintptr_t pv = reinterpret_cast<uintptr_t>(v), pw = reinterpret_cast<uintptr_t>(w);
   if (pv < pw + bytes && pw < pv + bytes) return fail(ctx, DG_ERR_ARG, "dg_rhs_transpose: v and w overlap");
-  DevBufs buf;
-  float *g = buf.get<float>(size_t(6) * ctx->K * 4 * ctx->ops.Nfp);
+  float *g = workspace(ctx).get<float>(5, size_t(6) * ctx->K * 4 * ctx->ops.Nfp);
   if (!g) return fail(ctx, DG_ERR_OOM, "dg_rhs_transpose: device allocation failed");
   AdjArgs a = adj_base(ctx, alpha);
   a.lr_in = v;
@@ -577,8 +603,8 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
   if (!out) return fail(ctx, DG_ERR_ARG, "dg_receiver_traces: null output");
   if (eps && (rc = dg_set_eps(ctx, eps))) return rc;
   const size_t fl = size_t(6) * ctx->K * ctx->ops.Npad;
-  DevBufs buf;
-  float *u = buf.get<float>(fl), *nxt = buf.get<float>(fl), *res = buf.get<float>(fl);
+  AdjWorkspace &ws = workspace(ctx);
+  float *u = ws.get<float>(0, fl), *nxt = ws.get<float>(1, fl), *res = ws.get<float>(2, fl);
   if (!u || !nxt || !res) return fail(ctx, DG_ERR_OOM, "dg_receiver_traces: device allocation failed");
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaMemcpyAsync(u, u0, fl * 4, cudaMemcpyDeviceToDevice, s);
@@ -621,14 +647,14 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   const size_t gfl = size_t(6) * ctx->K * 4 * ctx->ops.Nfp;
   cudaStream_t s = ctx->stream;
 
-  DevBufs buf;
-  float *u = buf.get<float>(fl), *nxt = buf.get<float>(fl), *res = buf.get<float>(fl);
-  float *lu = buf.get<float>(fl), *lr = buf.get<float>(fl), *g = buf.get<float>(gfl);
-  float *resid = buf.get<float>(size_t(nsteps) * 3 * R);
-  double *Jd = buf.get<double>(1), *grad = buf.get<double>(ctx->K);
-  float *ck = buf.get<float>(fl * nseg);
+  AdjWorkspace &ws = workspace(ctx);
+  float *u = ws.get<float>(0, fl), *nxt = ws.get<float>(1, fl), *res = ws.get<float>(2, fl);
+  float *lu = ws.get<float>(3, fl), *lr = ws.get<float>(4, fl), *g = ws.get<float>(5, gfl);
+  float *resid = ws.get<float>(6, size_t(nsteps) * 3 * R);
+  double *Jd = ws.get<double>(7, 1), *grad = ws.get<double>(8, ctx->K);
+  float *ck = ws.get<float>(9, fl * nseg);
   // stage states u_s and stage right-hand sides A u_s of one segment
-  float *US = buf.get<float>(fl * 5 * C), *RS = buf.get<float>(fl * 5 * C);
+  float *US = ws.get<float>(10, fl * 5 * C), *RS = ws.get<float>(11, fl * 5 * C);
   if (!u || !nxt || !res || !lu || !lr || !g || !resid || !Jd || !grad || !ck || !US || !RS)
     return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed (checkpoints and one segment of stage "
                                  "states are kept in device memory)");
@@ -665,6 +691,7 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   aa.g = g;
   aa.grad = grad;
   aa.dt = float(dt);
+  float pending = 1.f; // a of the stage reversed last, applied to lr by the next lift
   for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
     const int n0 = seg * C, n1 = (n0 + C < nsteps) ? n0 + C : nsteps;
     // recompute the segment, storing every stage state and its right-hand side
@@ -688,13 +715,15 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
         aa.lr_out = lr;
         aa.lu_in = lu;
         aa.b = float(kLserkB[st]);
-        e = launch_adj(ctx->N, 0, aa, s); // lr += b lu; g = Fscale LIFT^T W lr
+        aa.lr_scale = pending;
+        e = launch_adj(ctx->N, 0, aa, s); // lr = pending lr + b lu; g = Fscale LIFT^T W lr
         if (e != cudaSuccess) break;
+        aa.lr_out = nullptr;
         aa.lu_out = lu;
-        aa.a = float(kLserkA[st]);
         aa.u_s = j == 0 ? ck + fl * seg : US + fl * j;
         aa.rhs_s = RS + fl * j;
-        e = launch_adj(ctx->N, 1, aa, s); // lu += dt A^T lr; grad; lr *= a
+        e = launch_adj(ctx->N, 1, aa, s); // lu += dt A^T lr; grad
+        pending = float(kLserkA[st]);
       }
     }
   }

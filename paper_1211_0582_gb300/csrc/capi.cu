@@ -61,6 +61,7 @@ void free_mesh(dg_ctx *c) {
   dfree(c->d_flag);
   tc_free(c);
   ensemble_free(c);
+  adjoint_free(c);
   c->K = 0;
 }
 

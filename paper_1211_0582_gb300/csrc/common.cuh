@@ -61,6 +61,8 @@ cudaError_t launch_set_eps(int64_t K, const float *eps, float *geo, int *bad, cu
 cudaError_t launch_face_weights(int64_t K, const float *geo, const float4 *fgeo, const int2 *fconn, float4 *fmat,
                                 cudaStream_t s);
 void ensemble_free(dg_ctx *ctx);
+// Releases the adjoint work buffers.
+void adjoint_free(dg_ctx *ctx);
 // Re-arms the ensemble grid barrier after a timed-out launch (blocks that gave
 // up leave its arrival count behind).
 cudaError_t ensemble_reset_barrier(dg_ctx *ctx);
@@ -103,6 +105,7 @@ struct dg_ctx {
   long long wait_limit = 0;    // device-wait limit in SM cycles for the stage kernels (0 = default)
   void *tc = nullptr;          // tensor-core operator buffers (precision != DG_FP32)
   void *ens = nullptr;         // ensemble state (dg_ensemble_upload)
+  void *adj = nullptr;         // adjoint / receiver-trace work buffers (grown on demand)
   std::vector<double> host_vert;   // VX, VY, VZ (kept for node coordinates)
   std::vector<int32_t> host_EToV;
 };
