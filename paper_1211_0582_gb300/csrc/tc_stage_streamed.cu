@@ -17,9 +17,9 @@
 // warp issues all MMAs. Fewer, larger slices keep the single issuing thread's
 // per-slice overhead (barrier waits, commit, copy issue) small.
 //
-// Per tile: GEMM1 takes K1/16 slices, each feeding the three split products
-// of the three derivative directions (N = NB columns each); GEMM2 takes
-// ceil(K2/48) slices. TMEM holds [ur | us | ut | lifted flux] = 4 NB columns (all 512 at
+// Per tile: GEMM1 takes K1/16 slices ([Dr; Ds; Dt] hi, then lo), each feeding
+// the three split products as two MMAs: Dr and Ds together (N = 2 NB) and Dt
+// (N = NB); GEMM2 takes ceil(K2/48) slices. TMEM holds [ur | us | ut | lifted flux] = 4 NB columns (all 512 at
 // N = 7). A1 and A2 share one shared-memory region: A2 is written once GEMM1
 // has completed, and after GEMM2 the same bytes take the new residual (or the
 // right-hand side) while the new fields overwrite the staged ones; both go out
@@ -57,8 +57,8 @@ struct TS {
   static constexpr int G2 = 3;                         // GEMM2 K steps per slice
   static constexpr int NS2 = (KS2 + G2 - 1) / G2;      // GEMM2 slices
   static constexpr int PER = KS1 + NS2;                // operator slices per tile
-  static constexpr int SUB = 2 * NB * 32;              // NB rows x 16 K, hi then lo
-  static constexpr int SL = 3 * SUB;                   // one slice (three sub-blocks)
+  static constexpr int SUB = 2 * NB * 32;              // GEMM2: NB rows x 16 K, hi then lo
+  static constexpr int SL = 3 * SUB;                   // one slice: GEMM1 [Dr;Ds;Dt] hi, lo; GEMM2 three SUB
   static constexpr int STREAM = PER * SL;
   static constexpr int TCOLS = tmem_cols(4 * NB);
   static constexpr int FS = kTileS * NPP + 4; // padded field-block stride of the staged fields
@@ -288,20 +288,23 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     // ---- 3. local differentiation, streamed operator slices
     if (issuer) {
       umma::fence_after_sync();
-      const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NB));
+      // Dr, Ds: rows 0 .. 2NB-1 of a half slice (N = 2NB); Dt: rows 2NB .. 3NB-1
+      const uint32_t idesc2 = umma::make_idesc(BF16, 128, uint32_t(2 * NB));
+      const uint32_t idesc1 = umma::make_idesc(BF16, 128, uint32_t(NB));
       const uint64_t ah0 = umma::make_desc(sbase, 128, T::K1 * 16), al0 = umma::make_desc(sbase + T::A1B, 128, T::K1 * 16);
       for (int kk = 0; kk < T::KS1; ++kk) {
         ok = consume([&](uint32_t b) {
           const uint64_t ko = uint64_t(kk) * 16u;
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const uint32_t sb = b + uint32_t(d * T::SUB);
-            const uint64_t bh = umma::make_desc(sb, 128, 256), bl = umma::make_desc(sb + uint32_t(NB * 32), 128, 256);
-            const uint32_t dt = tmem + uint32_t(d * NB);
-            umma::mma_f16(dt, ah0 + ko, bh, idesc, kk > 0 ? 1u : 0u);
-            umma::mma_f16(dt, ah0 + ko, bl, idesc, 1u);
-            umma::mma_f16(dt, al0 + ko, bh, idesc, 1u);
-          }
+          const uint32_t lo = b + uint32_t(3 * NB * 32), dt3 = uint32_t(2 * NB * 32);
+          const uint64_t bh = umma::make_desc(b, 128, 256), bl = umma::make_desc(lo, 128, 256);
+          const uint64_t th = umma::make_desc(b + dt3, 128, 256), tl = umma::make_desc(lo + dt3, 128, 256);
+          const uint32_t acc = kk > 0 ? 1u : 0u;
+          umma::mma_f16(tmem, ah0 + ko, bh, idesc2, acc);
+          umma::mma_f16(tmem, ah0 + ko, bl, idesc2, 1u);
+          umma::mma_f16(tmem, al0 + ko, bh, idesc2, 1u);
+          umma::mma_f16(tmem + uint32_t(2 * NB), ah0 + ko, th, idesc1, acc);
+          umma::mma_f16(tmem + uint32_t(2 * NB), ah0 + ko, tl, idesc1, 1u);
+          umma::mma_f16(tmem + uint32_t(2 * NB), al0 + ko, th, idesc1, 1u);
         }) && ok;
       }
       umma::commit(bar1);
@@ -596,13 +599,13 @@ std::vector<uint8_t> build_stream(const RefOps &o, bool bf16) {
     std::memcpy(&blk[base_lo + off], &lb, 2);
   };
   const std::vector<double> *Ds[3] = {&o.Dr, &o.Ds, &o.Dt};
-  for (int kk = 0; kk < T::KS1; ++kk)
-    for (int d = 0; d < 3; ++d) {
-      const size_t hi = slice_offset<N>(kk) + size_t(d) * T::SUB, lo = hi + size_t(T::NB) * 32;
+  for (int kk = 0; kk < T::KS1; ++kk) {
+    const size_t hi = slice_offset<N>(kk), lo = hi + size_t(3) * T::NB * 32;
+    for (int d = 0; d < 3; ++d)
       for (int i = 0; i < T::NP; ++i)
         for (int k = 0; k < 16 && 16 * kk + k < T::NP; ++k)
-          put(hi, lo, i, k, (*Ds[d])[size_t(i) * T::NP + 16 * kk + k]);
-    }
+          put(hi, lo, d * T::NB + i, k, (*Ds[d])[size_t(i) * T::NP + 16 * kk + k]);
+  }
   for (int kk = 0; kk < T::KS2; ++kk) {
     const size_t hi = slice_offset<N>(T::KS1 + kk / T::G2) + size_t(kk % T::G2) * T::SUB, lo = hi + size_t(T::NB) * 32;
     for (int i = 0; i < T::NP; ++i)
