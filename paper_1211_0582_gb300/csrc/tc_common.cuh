@@ -23,20 +23,11 @@ struct TcState {
   int sms = 0;
 };
 
-// Round-to-nearest-even of a finite FP32 bit pattern to 23 - DROP explicit
-// mantissa bits (low DROP bits cleared), by integer arithmetic on the
-// sign-magnitude encoding; a carry into the exponent is the correct rounding.
-template <int DROP>
-__device__ __forceinline__ uint32_t rne_bits(uint32_t u) {
-  return (u + ((1u << (DROP - 1)) - 1u) + ((u >> DROP) & 1u)) & ~((1u << DROP) - 1u);
-}
-
 // hi/lo split of two FP32 values into packed 16-bit pairs (x0 in the low half).
 // BF16: hi by a rounding conversion, widened back by a shift (BF16 is the top
 // half of FP32); lo = x - hi is exact in FP32 and converted with rounding.
-// FP16: hi is rounded to 11 significant bits (exact in FP16 for |x| >= 2^-14;
-// below that the conversion rounds it to the subnormal grid, an error of at
-// most 2^-25), lo = x - hi is exact in FP32 and converted with rounding.
+// FP16: hi by a rounding conversion and widened back exactly; lo = x - hi is
+// exact in FP32 and converted with rounding.
 template <bool BF16>
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
   if constexpr (BF16) {
@@ -46,9 +37,9 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_
     const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - h0, x1 - h1);
     lo = *reinterpret_cast<const uint32_t *>(&ll);
   } else {
-    const float h0 = __uint_as_float(rne_bits<13>(__float_as_uint(x0)));
-    const float h1 = __uint_as_float(rne_bits<13>(__float_as_uint(x1)));
-    const __half2 hh = __floats2half2_rn(h0, h1), ll = __floats2half2_rn(x0 - h0, x1 - h1);
+    const __half2 hh = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
     hi = *reinterpret_cast<const uint32_t *>(&hh);
     lo = *reinterpret_cast<const uint32_t *>(&ll);
   }
