@@ -45,4 +45,25 @@ __device__ __forceinline__ void maxwell_flux(float4 nf, const float *qm, const f
   out[5] = wH * (nx * vy - ny * vx);
 }
 
+// The same flux with the face's precomputed weights
+// w = {Fscale/(Z- + Z+), -Fscale/(Y- + Y+), Z+, Y+}.
+__device__ __forceinline__ void maxwell_flux_w(float4 nf, const float *qm, const float *qp, float4 w, float alpha,
+                                               float *out) {
+  const float nx = nf.x, ny = nf.y, nz = nf.z;
+  const float dEx = qp[0] - qm[0], dEy = qp[1] - qm[1], dEz = qp[2] - qm[2];
+  const float dHx = qp[3] - qm[3], dHy = qp[4] - qm[4], dHz = qp[5] - qm[5];
+  const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
+  const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
+  float vx = w.z * dHx - alpha * cEx, vy = w.z * dHy - alpha * cEy, vz = w.z * dHz - alpha * cEz;
+  out[0] = w.x * (ny * vz - nz * vy);
+  out[1] = w.x * (nz * vx - nx * vz);
+  out[2] = w.x * (nx * vy - ny * vx);
+  vx = w.w * dEx + alpha * cHx;
+  vy = w.w * dEy + alpha * cHy;
+  vz = w.w * dEz + alpha * cHz;
+  out[3] = w.y * (ny * vz - nz * vy);
+  out[4] = w.y * (nz * vx - nx * vz);
+  out[5] = w.y * (nx * vy - ny * vx);
+}
+
 } // namespace dgmx

@@ -9,7 +9,8 @@
 //      chain rule (eq. dg-reference-matrices) and the curls;
 //   3. flux gather (eq. num-flux): interior trace from shared memory,
 //      exterior trace from the neighbour's row (L2), PEC mirror on walls,
-//      upwind flux with impedance weights, times Fscale, into shared memory;
+//      upwind flux with the face's precomputed impedance weights (Fscale
+//      included), into shared memory;
 //   4. flux lifting: LIFT (Np x 4Nfp) times the face fluxes, added to the
 //      curls and scaled by 1/eps, 1/mu;
 // then either stores the right-hand side or applies the low-storage RK
@@ -134,10 +135,9 @@ __device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, 
       float qm[6], qp[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) qm[c] = s_u[(c * EB + ee) * NPP + vm];
-      int2 cn = __ldg(a.fconn + kk * 4 + f);
-      float4 nf = __ldg(a.fgeo + kk * 4 + f);
-      float Zm = __ldg(a.geo + kk * G_STRIDE + G_Z), Ym = __ldg(a.geo + kk * G_STRIDE + G_Y);
-      float Zp = Zm, Yp = Ym;
+      const int2 cn = __ldg(a.fconn + kk * 4 + f);
+      const float4 nf = __ldg(a.fgeo + kk * 4 + f);
+      const float4 wf = __ldg(a.fmat + kk * 4 + f); // face weights (neighbour or mirror impedances)
       if (cn.y == kBoundaryConn) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -149,10 +149,8 @@ __device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, 
         const float *up = a.u + int64_t(cn.x) * NPP + vn;
 #pragma unroll
         for (int c = 0; c < 6; ++c) qp[c] = load_field<COHERENT>(up + c * KN);
-        Zp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Z);
-        Yp = __ldg(a.geo + int64_t(cn.x) * G_STRIDE + G_Y);
       }
-      maxwell_flux(nf, qm, qp, Zm, Zp, Ym, Yp, a.alpha, fl);
+      maxwell_flux_w(nf, qm, qp, wf, a.alpha, fl);
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) s_fl[(c * EB + ee) * NFF + fm] = fl[c];
