@@ -16,14 +16,23 @@
 // then either stores the right-hand side or applies the low-storage RK
 // update res = a res + dt rhs, u_out = u + b res (operator assembly).
 // The transposed operators D^T[j][i], LIFT^T[m][i] are read as float4 along i
-// through the read-only cache; they are small and stay cache resident.
+// through the read-only cache; they are small and stay cache resident. The
+// launch is persistent (blocks loop over element tiles) with the elements per
+// block picked per order from measurements: 128 / (Np_pad / 4), 80 / (...) at
+// N = 4.
 #pragma once
 #include "common.cuh"
 #include "flux.cuh"
 
 namespace dgmx {
 
-template <int N, int EB_ = 240 / Dims<N>::NQ>
+// Elements per block of the single-mesh launch (measured best on GB300).
+template <int N>
+constexpr int simt_default_eb() {
+  return (N == 4 ? 80 : 128) / Dims<N>::NQ > 0 ? (N == 4 ? 80 : 128) / Dims<N>::NQ : 1;
+}
+
+template <int N, int EB_ = simt_default_eb<N>()>
 struct SimtCfg {
   using D = Dims<N>;
   static constexpr int EB = EB_;                         // elements per block
@@ -32,9 +41,10 @@ struct SimtCfg {
       (size_t(6) * EB * D::NPP + size_t(6) * EB * D::NFF) * 4 + ((100 * D::NFP + 15) / 16) * 16;
 };
 
-// Field loads: through the read-only path for single-stage launches, or from
-// L2 (bypassing the non-coherent L1) when other blocks of the same launch wrote
-// the data in an earlier stage (persistent multi-stage kernels).
+// Field loads: from L2, bypassing L1 (fields are streamed once and the
+// neighbour traces hit L2 anyway; L1 stays with the operator matrices), or
+// through the read-only path (measured slower). Persistent multi-stage kernels
+// need the L2 path for coherence: other blocks wrote the data in an earlier stage.
 template <bool COHERENT>
 __device__ __forceinline__ float4 load_field4(const float *p) {
   if constexpr (COHERENT) return __ldcg(reinterpret_cast<const float4 *>(p));
@@ -208,7 +218,12 @@ __device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, 
 template <int N, int MODE>
 __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
   extern __shared__ float4 smem4[];
-  simt_stage_tile<N, MODE, SimtCfg<N>::EB, false>(a, int64_t(blockIdx.x) * SimtCfg<N>::EB, smem4);
+  constexpr int EB = SimtCfg<N>::EB;
+  const int64_t ntiles = (a.K + EB - 1) / EB;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    __syncthreads(); // shared memory of the previous tile is no longer read
+    simt_stage_tile<N, MODE, EB, true>(a, t * EB, smem4);
+  }
 }
 
 template <int N>
@@ -227,7 +242,22 @@ cudaError_t launch_simt_order(int mode, const StageArgs &a, cudaStream_t s) {
     if (e3 != cudaSuccess) return e3;
     configured = true;
   }
-  unsigned blocks = unsigned((a.K + Cfg::EB - 1) / Cfg::EB);
+  // persistent grid: as many blocks as fit on the GPU at once (at most one per tile)
+  static int per_sm[3] = {0, 0, 0};
+  const void *kern = mode == MODE_RHS ? (const void *)k_stage_simt<N, MODE_RHS>
+                     : mode == MODE_LSERK ? (const void *)k_stage_simt<N, MODE_LSERK>
+                                          : (const void *)k_stage_simt<N, MODE_LSERK_STORE>;
+  if (per_sm[mode] == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[mode], kern, Cfg::NT, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm[mode] < 1) return cudaErrorInvalidConfiguration;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (a.K + Cfg::EB - 1) / Cfg::EB, cap = int64_t(per_sm[mode]) * sms;
+  const unsigned blocks = unsigned(ntiles < cap ? ntiles : cap);
   if (mode == MODE_RHS)
     k_stage_simt<N, MODE_RHS><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
   else if (mode == MODE_LSERK)
