@@ -57,7 +57,7 @@ struct AdjCfg {
   static constexpr int MQ = D::NFF / 4;                       // face-node quads
   static constexpr int EB1 = 240 / MQ > 0 ? 240 / MQ : 1;     // elements per lift block
   static constexpr int NT1 = (EB1 * MQ + 31) / 32 * 32;
-  static constexpr int EB2 = 240 / D::NQ;                     // elements per volume block
+  static constexpr int EB2 = 80 / D::NQ > 0 ? 80 / D::NQ : 1; // elements per volume block (measured best)
   static constexpr int NT2 = (EB2 * D::NQ + 31) / 32 * 32;
   static constexpr size_t SMEM1 = size_t(6) * EB1 * D::NPP * 4;
   static constexpr size_t SMEM2 = (size_t(6) * EB2 * D::NPP * 3 + EB2) * 4 + ((200 * D::NFP + 15) / 16) * 16;
