@@ -150,3 +150,35 @@ def test_cavity_mode_full_size_short_run():
     err = np.abs(s.from_device(u) - exact).max()
     assert err < 1e-4, err
     assert E1 <= E0 * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+@pytest.mark.parametrize("N", [3, 5])
+def test_cavity_h_convergence(precision, N):
+    # the closed-form cavity eigenmode on the 8^3 and 12^3 jittered meshes, run
+    # to the same time T: M-weighted L2 error against the exact solution
+    # (||e||^2 = 2 E(e) with eps = mu = 1) and its rate in h (the oracle's own
+    # rate is pinned on the CPU)
+    T = 0.2
+    errs = []
+    for n in (8, 12):
+        VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+        s = dg.Solver(N, precision=precision).upload(VX, VY, VZ, EToV)
+        x, y, z = s.node_coords()
+        steps = int(np.ceil(T / (0.5 / n / N ** 2)))
+        u = s.to_device(W.cavity_mode(x, y, z, 0.0))
+        r = s.zeros()
+        s.step(u, r, T / steps, steps)
+        exact = W.cavity_mode(x, y, z, T)
+        err = np.sqrt(2.0 * s.energy(s.to_device(s.from_device(u) - exact)))
+        ref = np.sqrt(2.0 * s.energy(s.to_device(exact)))
+        errs.append(err / ref)
+    rate = np.log(errs[0] / errs[1]) / np.log(12 / 8)
+    print(f"{precision} N={N}: rel errors {errs[0]:.3e} (8^3), {errs[1]:.3e} (12^3), rate {rate:.2f}")
+    if N == 3:
+        # upwind flux: h^(N+1)
+        assert N + 0.5 < rate < N + 1.5
+    else:
+        # at N=5 the method's error on these meshes is below the FP32 resolution
+        # of the state: both runs sit at the FP32 floor
+        assert max(errs) < 2e-6
