@@ -368,14 +368,15 @@ def run_precision(args):
     VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
     K = EToV.shape[0]
     eps = W.element_eps(K, seed=2) if eps_rule else None
-    # error reference: the same setup on a 3^3 mesh, 10 steps, against the oracle
-    sVX, sVY, sVZ, sE = W.kuhn_cube(3, jitter=0.1, seed=1)
+    # error reference: the same setup on a 6^3 mesh, 20 steps, against the oracle
+    ne_ref, steps_ref = 6, 20
+    sVX, sVY, sVZ, sE = W.kuhn_cube(ne_ref, jitter=0.1, seed=1)
     seps = W.element_eps(sE.shape[0], seed=2) if eps_rule else None
     m = O.Mesh(N, sVX, sVY, sVZ, sE, eps=None if seps is None else seps.astype(np.float64))
     x, y, z = m.coords()
     su0 = W.cavity_mode(x, y, z, 0.0)
-    sdt = 0.5 / 3 / N ** 2
-    ref, _ = m.lserk(su0, sdt, 10)
+    sdt = 0.5 / ne_ref / N ** 2
+    ref, _ = m.lserk(su0, sdt, steps_ref)
     out = {}
     for prec in ("fp32", "bf16x3", "fp16x3"):
         try:
@@ -391,7 +392,7 @@ def run_precision(args):
         ms = _timed(lambda: s.step(u, res, dt, args.steps), stream)
         ss = dg.Solver(N, precision=prec, stream=stream).upload(sVX, sVY, sVZ, sE, eps=seps)
         su, sr = ss.to_device(su0), ss.zeros()
-        ss.step(su, sr, sdt, 10)
+        ss.step(su, sr, sdt, steps_ref)
         err = float(np.linalg.norm(ss.from_device(su) - ref) / np.linalg.norm(ref))
         dof = 6 * s.Np * K
         out[prec] = {"gdof_s": STAGES * dof * args.steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / args.steps,
@@ -403,7 +404,7 @@ def run_precision(args):
             "dtype": best[1], "data": "synthetic",
             "config": {"workload": f"precision form, {n}^3x6 jittered tets, N={N}, "
                                    f"{'eps U[1,4] per element' if eps_rule else 'eps=mu=1'}, LSERK4",
-                       "K": K, "error_reference": "FP64 oracle, 3^3x6 version, 10 steps"},
+                       "K": K, "error_reference": f"FP64 oracle, {ne_ref}^3x6 version, {steps_ref} steps"},
             "precisions": out, "speedup_vs_fp32": {k: v["gdof_s"] / fp32 for k, v in out.items() if "gdof_s" in v}}
     print(json.dumps(line), flush=True)
 
