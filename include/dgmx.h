@@ -59,8 +59,13 @@ typedef enum {
 typedef enum {
   DG_FP32 = 0,   /* FP32 arithmetic on the CUDA cores */
   DG_BF16X3 = 1, /* D and LIFT contractions on tensor cores, BF16 hi+lo split, FP32 accumulate */
-  DG_FP16X3 = 2  /* same with FP16 hi+lo split (row-scaled), FP32 accumulate */
+  DG_FP16X3 = 2  /* same with FP16 hi+lo split, FP32 accumulate; power-of-two scaled per
+                    (element, field) row of the field operand and per field component of
+                    a tile's flux operand (FP16 range) */
 } dg_precision;
+/* The tensor-core precisions cover N = 1..7: up to N = 5 the split operators
+ * stay in shared memory, at N = 6, 7 they are streamed from L2 slice by slice.
+ * They need an sm_103 device (GB300). */
 
 /* Create a context for polynomial order N (1..7) and the given arithmetic.
  * cuda_stream is a cudaStream_t (may be NULL). *out receives the context.
