@@ -438,10 +438,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       g2r = g[G_RX + dl2], g2s = g[G_SX + dl2], g2t = g[G_TX + dl2];
       w = g[isE ? G_IEPS : G_IMU];
     }
-    float inv1 = 1.f, inv2 = 1.f;
+    float inv2 = 1.f;
     if constexpr (!BF16) {
+      // the row's FP16 scale is undone through the metric factors of the chain rule
       float sc;
-      inv1 = s_inv1[lane_used ? ridx : 0];
+      const float inv1 = s_inv1[lane_used ? ridx : 0];
+      g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
       row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
     }
     ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
@@ -462,9 +464,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       umma::reg_fence8(ut);
 #pragma unroll
       for (int n = 0; n < 8; ++n) {
-        const float dr = ur[n] * inv1, ds = us[n] * inv1, dt = ut[n] * inv1;
-        const float p1 = g1r * dr + g1s * ds + g1t * dt;
-        const float p2 = g2r * dr + g2s * ds + g2t * dt;
+        const float p1 = g1r * ur[n] + g1s * us[n] + g1t * ut[n];
+        const float p2 = g2r * ur[n] + g2s * us[n] + g2t * ut[n];
         const float v1 = __shfl_sync(0xffffffffu, p1, src1);
         const float v2 = __shfl_sync(0xffffffffu, p2, src2);
         vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
