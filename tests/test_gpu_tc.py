@@ -111,3 +111,20 @@ def test_tc_streamed_full_size_sampled(precision):
     again = s.from_device(s.rhs(ud))
     assert np.array_equal(again, got)
     s.sync()
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("N", [3, 7])
+def test_tc_single_partial_tile(precision, N):
+    # 1^3 x 6 = 6 elements: one tile of 20 with 14 empty element slots, one CTA
+    s, m = pair(N, 1, precision)
+    u = np.random.default_rng(13).standard_normal(m.shape)
+    err = rel_l2(s.from_device(s.rhs(s.to_device(u))), m.rhs(u))
+    assert err < TOL[precision]
+    x, y, z = m.coords()
+    u0 = W.cavity_mode(x, y, z, 0.0)
+    ref, _ = m.lserk(u0, 0.5 / N ** 2, 2)
+    ud, rd = s.to_device(u0), s.zeros()
+    s.step(ud, rd, 0.5 / N ** 2, 2)
+    s.sync()
+    assert rel_l2(s.from_device(ud), ref) < TOL[precision]
