@@ -268,12 +268,14 @@ def run_ours(args):
     u_h = torch.empty((6, K, Npad), dtype=torch.float32).pin_memory()
     r_h = torch.zeros((6, K, Npad), dtype=torch.float32).pin_memory()
     u_h.copy_(u.cpu())
-    out_h = [torch.empty_like(u_h).pin_memory() for _ in range(2)]
-    streams = [stream, torch.cuda.Stream(device)]
-    solvers = [s, dg.Solver(N, precision=args.precision, stream=streams[1]).upload(VX, VY, VZ, EToV)]
-    ud = [torch.empty_like(u) for _ in range(2)]
-    rd = [torch.empty_like(res) for _ in range(2)]
-    for j in range(2):  # warm-up of both contexts
+    ns = max(1, args.e2e_streams)
+    out_h = [torch.empty_like(u_h).pin_memory() for _ in range(ns)]
+    streams = [stream] + [torch.cuda.Stream(device) for _ in range(ns - 1)]
+    solvers = [s] + [dg.Solver(N, precision=args.precision, stream=streams[j]).upload(VX, VY, VZ, EToV)
+                     for j in range(1, ns)]
+    ud = [torch.empty_like(u) for _ in range(ns)]
+    rd = [torch.empty_like(res) for _ in range(ns)]
+    for j in range(ns):  # warm-up of every context
         with torch.cuda.stream(streams[j]):
             ud[j].copy_(u_h, non_blocking=True)
             rd[j].copy_(r_h, non_blocking=True)
@@ -283,15 +285,17 @@ def run_ours(args):
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(streams[0])
-    streams[1].wait_event(e0)
+    for j in range(1, ns):
+        streams[j].wait_event(e0)
     for i in range(e2e_steps):
-        j = i % 2
+        j = i % ns
         with torch.cuda.stream(streams[j]):
             ud[j].copy_(u_h, non_blocking=True)
             rd[j].copy_(r_h, non_blocking=True)
             solvers[j].step(ud[j], rd[j], dt, 1)
             out_h[j].copy_(ud[j], non_blocking=True)
-    streams[0].wait_stream(streams[1])
+    for j in range(1, ns):
+        streams[0].wait_stream(streams[j])
     e1.record(streams[0])
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -325,7 +329,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes,
                 "d2h_bytes_per_step": field_bytes, "steps": e2e_steps,
                 "how": "each step: u, res from pinned host memory, 1 LSERK4 step, u back to pinned host memory; "
-                       "independent steps alternate over two contexts/streams (copies overlap compute)"},
+                       f"independent steps alternate over {ns} contexts/streams (copies overlap compute)"},
         "gpu_launches": launches, "roofline": roof, "clocks": clk,
         "kernel_ms_per_launch": launch_ms, "energy_after": energy,
     }
@@ -532,6 +536,7 @@ def main():
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--n", type=int, default=24, help="hexahedra per cube edge")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-streams", type=int, default=3, help="contexts/streams the end-to-end steps alternate over")
     ap.add_argument("--cpu-sample", type=int, default=50000, help="elements in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["cavity", "precision", "ensemble", "adjoint"], default="cavity",
