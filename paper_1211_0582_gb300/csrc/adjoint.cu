@@ -653,8 +653,9 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   float *resid = ws.get<float>(6, size_t(nsteps) * 3 * R);
   double *Jd = ws.get<double>(7, 1), *grad = ws.get<double>(8, ctx->K);
   float *ck = ws.get<float>(9, fl * nseg);
-  // stage states u_s and stage right-hand sides A u_s of one segment
-  float *US = ws.get<float>(10, fl * 5 * C), *RS = ws.get<float>(11, fl * 5 * C);
+  // stage states u_s and the E components of the stage right-hand sides A u_s of one segment
+  const size_t hfl = fl / 2; // three of the six fields
+  float *US = ws.get<float>(10, fl * 5 * C), *RS = ws.get<float>(11, hfl * 5 * C);
   if (!u || !nxt || !res || !lu || !lr || !g || !resid || !Jd || !grad || !ck || !US || !RS)
     return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed (checkpoints and one segment of stage "
                                  "states are kept in device memory)");
@@ -701,7 +702,7 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
         const size_t j = size_t(n - n0) * 5 + st;
         sa.u = j == 0 ? ck + fl * seg : US + fl * j;
         sa.u_out = (j + 1 < size_t(5) * C) ? US + fl * (j + 1) : nxt;
-        sa.rhs = RS + fl * j;
+        sa.rhs = RS + hfl * j;
         sa.rk_a = float(kLserkA[st]);
         sa.rk_b = float(kLserkB[st]);
         e = launch_stage_simt(ctx->N, MODE_LSERK_STORE, sa, s);
@@ -721,7 +722,7 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
         aa.lr_out = nullptr;
         aa.lu_out = lu;
         aa.u_s = j == 0 ? ck + fl * seg : US + fl * j;
-        aa.rhs_s = RS + fl * j;
+        aa.rhs_s = RS + hfl * j;
         e = launch_adj(ctx->N, 1, aa, s); // lu += dt A^T lr; grad
         pending = float(kLserkA[st]);
       }

@@ -19,7 +19,8 @@ enum GeoSlot {
 };
 
 // Stage kinds of the fused kernels.
-enum StageMode { MODE_RHS = 0, MODE_LSERK = 1, MODE_LSERK_STORE = 2 }; // STORE: LSERK update that also writes rhs
+// MODE_LSERK_STORE: LSERK update that also writes the E components of the rhs
+enum StageMode { MODE_RHS = 0, MODE_LSERK = 1, MODE_LSERK_STORE = 2 };
 
 // Arguments of one fused right-hand-side / LSERK-stage launch.
 struct StageArgs {

@@ -210,7 +210,9 @@ __device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, 
       }
       *reinterpret_cast<float4 *>(a.res + off) = make_float4(rv[0], rv[1], rv[2], rv[3]);
       *reinterpret_cast<float4 *>(a.u_out + off) = make_float4(uv[0], uv[1], uv[2], uv[3]);
-      if (MODE == MODE_LSERK_STORE) *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+      // the adjoint's eps gradient reads only the E components of the stage right-hand side
+      if (MODE == MODE_LSERK_STORE && c < 3)
+        *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
     }
   }
 }
