@@ -391,24 +391,23 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
 template <int N>
 cudaError_t launch_adj_order(int which, const AdjArgs &a, cudaStream_t s) {
   using C = AdjCfg<N>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_adj_lift<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM1));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_adj_vol<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_adj_vol<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // the shared-memory opt-in is a per-device function attribute: set it on every launch
+  cudaError_t e;
   if (which == 0) {
+    e = cudaFuncSetAttribute(k_adj_lift<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM1));
+    if (e != cudaSuccess) return e;
     k_adj_lift<N><<<unsigned((a.K + C::EB1 - 1) / C::EB1), C::NT1, C::SMEM1, s>>>(a);
   } else {
     const unsigned blocks = unsigned((a.K + C::EB2 - 1) / C::EB2);
-    if (a.u_s)
+    if (a.u_s) {
+      e = cudaFuncSetAttribute(k_adj_vol<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
+      if (e != cudaSuccess) return e;
       k_adj_vol<N, true><<<blocks, C::NT2, C::SMEM2, s>>>(a);
-    else
+    } else {
+      e = cudaFuncSetAttribute(k_adj_vol<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
+      if (e != cudaSuccess) return e;
       k_adj_vol<N, false><<<blocks, C::NT2, C::SMEM2, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

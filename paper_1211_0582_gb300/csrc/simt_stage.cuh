@@ -21,6 +21,8 @@
 // block picked per order from measurements: 128 / (Np_pad / 4), 80 / (...) at
 // N = 4.
 #pragma once
+#include <atomic>
+
 #include "common.cuh"
 #include "flux.cuh"
 
@@ -231,34 +233,27 @@ __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
 template <int N>
 cudaError_t launch_simt_order(int mode, const StageArgs &a, cudaStream_t s) {
   using Cfg = SimtCfg<N>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e1 = cudaFuncSetAttribute(k_stage_simt<N, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(Cfg::SMEM));
-    cudaError_t e2 = cudaFuncSetAttribute(k_stage_simt<N, MODE_LSERK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(Cfg::SMEM));
-    if (e1 != cudaSuccess) return e1;
-    if (e2 != cudaSuccess) return e2;
-    cudaError_t e3 = cudaFuncSetAttribute(k_stage_simt<N, MODE_LSERK_STORE>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::SMEM));
-    if (e3 != cudaSuccess) return e3;
-    configured = true;
-  }
-  // persistent grid: as many blocks as fit on the GPU at once (at most one per tile)
-  static int per_sm[3] = {0, 0, 0};
   const void *kern = mode == MODE_RHS ? (const void *)k_stage_simt<N, MODE_RHS>
                      : mode == MODE_LSERK ? (const void *)k_stage_simt<N, MODE_LSERK>
                                           : (const void *)k_stage_simt<N, MODE_LSERK_STORE>;
-  if (per_sm[mode] == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[mode], kern, Cfg::NT, Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    if (per_sm[mode] < 1) return cudaErrorInvalidConfiguration;
-  }
+  // the shared-memory opt-in is a per-device function attribute: set it on every launch
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::SMEM));
   int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = (a.K + Cfg::EB - 1) / Cfg::EB, cap = int64_t(per_sm[mode]) * sms;
+  // persistent grid: as many blocks as fit on the GPU at once (at most one per
+  // tile); blocks per SM of each kernel cached per device
+  constexpr int kDevCache = 64;
+  static std::atomic<int> per_sm_cache[3][kDevCache];
+  int per_sm = dev < kDevCache ? per_sm_cache[mode][dev].load(std::memory_order_relaxed) : 0;
+  if (per_sm == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (dev < kDevCache) per_sm_cache[mode][dev].store(per_sm, std::memory_order_relaxed);
+  }
+  const int64_t ntiles = (a.K + Cfg::EB - 1) / Cfg::EB, cap = int64_t(per_sm) * sms;
   const unsigned blocks = unsigned(ntiles < cap ? ntiles : cap);
   if (mode == MODE_RHS)
     k_stage_simt<N, MODE_RHS><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
