@@ -12,6 +12,7 @@
 // of 20 elements (5 per 32-lane TMEM quarter, 30 of 32 lanes used):
 //   GEMM1  V[(e,f), (d,i)] = sum_j u[(e,f), j] D_d[i, j]        (d = r, s, t)
 //   GEMM2  S[(e,f), i]     = sum_m flux[(e,f), m] LIFT[i, m]
+// (the face-node columns m of GEMM2 are padded to an even count per face).
 // The operators (B operands) stay resident in shared memory for the whole
 // persistent kernel ("store the matrices, stream the vector data", Section 3).
 // The epilogue reads V and S from TMEM with one thread per row, applies the
@@ -51,7 +52,8 @@ struct TC {
   static constexpr int K1 = rup(NP, 16);  // GEMM1 reduction length (input nodes)
   static constexpr int NB = rup(NP, 16);  // output columns per derivative direction
   static constexpr int N1 = 3 * NB;       // GEMM1 output columns
-  static constexpr int K2 = rup(NFF, 16); // GEMM2 reduction length (face nodes)
+  static constexpr int NFPE = (NFP + 1) / 2 * 2; // A2 columns per face (even: column pairs stay in one face)
+  static constexpr int K2 = rup(4 * NFPE, 16);   // GEMM2 reduction length (face-node columns)
   static constexpr int N2 = NB;           // GEMM2 output columns
   static constexpr int TCOLS = tmem_cols(N1 + N2);
   static constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staged tiles
@@ -187,13 +189,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int cr1 = compact_row(r1);
   const int e1 = cr1 >= 0 ? cr1 / 6 : 0, f1 = cr1 >= 0 ? cr1 % 6 : 0;
   const int kq1 = 4 * ((lane >> 3) & 1) + 8 * (lane >> 4); // + 16 s
-  // flux: blocks of 4 elements x 8 face-node columns of A2 (padding columns
-  // included, written as zeros), lane -> (element, column); block b goes to
-  // warp b % 16, so the last warp gets the fewest
-  constexpr int KGF = T::K2 / 8;
+  // flux: blocks of 4 elements x 16 columns of A2 (padding columns included,
+  // written as zeros), lane -> (element, pair of adjacent columns); column
+  // f * NFPE + m holds face node m of face f, so a pair never straddles two
+  // faces; block b goes to warp b % 16, so the last warps get the fewest
+  constexpr int NFPE = T::NFPE;
+  constexpr int KGF = T::K2 / 16;
   constexpr int NBLK = (kTileElems / 4) * KGF;
   constexpr int R2 = (NBLK + 15) / 16;
-  const int eo = lane >> 3, kk = lane & 7;
+  const int eo = lane >> 3, kp = lane & 7;
 
   // epilogue: one thread per (element, field) row of the accumulators
   const int quarter = warp & 3, part = warp >> 2;
@@ -292,79 +296,83 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     bool ok = true;
 
-    // ---- 4. neighbour traces and upwind flux (overlaps GEMM1), in registers;
-    // neighbours inside the tile are read from the staged fields
-    float fl[R2][6];
-    uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-    {
-      float qp[R2][6];
-      int lidx[R2];
+    // ---- 4. upwind flux (overlaps GEMM1), in registers
+    // neighbour traces outside the tile are requested before the field split,
+    // which hides their latency; neighbours inside the tile are read from the
+    // staged fields once they are in place
+    float qp[R2][2][6];
+    int lidx[R2][2];
 #pragma unroll
-      for (int s = 0; s < R2; ++s) {
-        const int blk = warp + 16 * s;
-        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk;
-        lidx[s] = -1;
+    for (int s = 0; s < R2; ++s) {
+      const int blk = warp + 16 * s;
+      const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+      const int f = fm / NFPE, mm = fm - f * NFPE;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) qp[s][c] = 0.f;
-        if (blk < NBLK && fm < NFF && e < ne) {
-          const int f = fm / NFP, mm = fm - f * NFP;
-          const int2 cn = s_fconn[e * 4 + f];
-          if (cn.y != kBoundaryConn) {
-            const int node = s_nb[cn.y * NFP + mm];
-            const int64_t el = int64_t(cn.x) - k0;
-            if (el >= 0 && el < ne) {
-              lidx[s] = int(el) * NPP + node;
-            } else {
-              const float *up = a.u + int64_t(cn.x) * NPP + node;
+      for (int h = 0; h < 2; ++h) {
+        lidx[s][h] = -1;
 #pragma unroll
-              for (int c = 0; c < 6; ++c) qp[s][c] = __ldg(up + c * KN);
+        for (int c = 0; c < 6; ++c) qp[s][h][c] = 0.f;
+      }
+      if (blk < NBLK && f < 4 && e < ne) {
+        const int2 cn = s_fconn[e * 4 + f];
+        if (cn.y != kBoundaryConn) {
+          const int el = cn.x - int(k0);
+          const bool local = el >= 0 && el < ne;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (mm + h < NFP) {
+              const int node = s_nb[cn.y * NFP + mm + h];
+              if (local) {
+                lidx[s][h] = el * NPP + node;
+              } else {
+                const float *up = a.u + int64_t(cn.x) * NPP + node;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) qp[s][h][c] = __ldg(up + c * KN);
+              }
             }
           }
         }
       }
+    }
+    float fl[R2][2][6];
+    uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-      for (int s = 0; s < R2; ++s) {
-        const int blk = warp + 16 * s;
-        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk;
+    for (int s = 0; s < R2; ++s) {
+      const int blk = warp + 16 * s;
+      const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+      const int f = fm / NFPE, mm = fm - f * NFPE;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) fl[s][c] = 0.f;
-        if (blk < NBLK && fm < NFF && e < ne) {
-          const int f = fm / NFP;
-          const float4 g0 = s_fgeo[e * 4 + f], w1 = s_fmat[e * 4 + f];
-          const bool wall = s_fconn[e * 4 + f].y == kBoundaryConn;
-          const int vm = s_fm[fm];
-          float qm[6];
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
-          if (lidx[s] >= 0) {
+        for (int c = 0; c < 6; ++c) fl[s][h][c] = 0.f;
+      if (blk < NBLK && f < 4 && e < ne) {
+        const float4 g0 = s_fgeo[e * 4 + f], w1 = s_fmat[e * 4 + f];
+        const bool wall = s_fconn[e * 4 + f].y == kBoundaryConn;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) qp[s][c] = s_u[c * FS + lidx[s]];
-          }
-          if (wall) {
+        for (int h = 0; h < 2; ++h) {
+          if (mm + h < NFP) {
+            const int vm = s_fm[f * NFP + mm + h];
+            float qm[6], q[6];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              qp[s][c] = -qm[c];
-              qp[s][c + 3] = qm[c + 3];
+            for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) q[c] = lidx[s][h] >= 0 ? s_u[c * FS + lidx[s][h]] : qp[s][h][c];
+            if (wall) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                q[c] = -qm[c];
+                q[c + 3] = qm[c + 3];
+              }
             }
+            maxwell_flux_w(g0, qm, q, w1, a.alpha, fl[s][h]);
           }
-          const float nx = g0.x, ny = g0.y, nz = g0.z;
-          const float dEx = qp[s][0] - qm[0], dEy = qp[s][1] - qm[1], dEz = qp[s][2] - qm[2];
-          const float dHx = qp[s][3] - qm[3], dHy = qp[s][4] - qm[4], dHz = qp[s][5] - qm[5];
-          const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
-          const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
-          float vx = w1.z * dHx - a.alpha * cEx, vy = w1.z * dHy - a.alpha * cEy, vz = w1.z * dHz - a.alpha * cEz;
-          fl[s][0] = w1.x * (ny * vz - nz * vy);
-          fl[s][1] = w1.x * (nz * vx - nx * vz);
-          fl[s][2] = w1.x * (nx * vy - ny * vx);
-          vx = w1.w * dEx + a.alpha * cHx, vy = w1.w * dEy + a.alpha * cHy, vz = w1.w * dEz + a.alpha * cHz;
-          fl[s][3] = w1.y * (ny * vz - nz * vy);
-          fl[s][4] = w1.y * (nz * vx - nx * vz);
-          fl[s][5] = w1.y * (nx * vy - ny * vx);
         }
-        if constexpr (!BF16) {
+      }
+      if constexpr (!BF16) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][c])));
-        }
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][h][c])));
       }
     }
     // once GEMM1 has read A1, the next tile's fields and face data are staged
@@ -401,20 +409,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int s = 0; s < R2; ++s) {
         const int blk = warp + 16 * s;
-        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk;
+        const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
         if (blk < NBLK) {
-          // the six rows of element e lie in one TMEM lane quarter
+          // the six rows of element e lie in one TMEM lane quarter; a column
+          // pair is one 32-bit word of a core-matrix row
           const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
 #pragma unroll
-          for (int c = 0; c < 6; c += 2) {
+          for (int c = 0; c < 6; ++c) {
             uint32_t hi, lo;
-            split2<BF16>(fl[s][c] * sc2[c], fl[s][c + 1] * sc2[c + 1], hi, lo);
-            const uint32_t o0 = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
-            const uint32_t o1 = umma::kmajor_offset(r0 + uint32_t(c + 1), uint32_t(fm), uint32_t(T::K2));
-            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2H + o0) = uint16_t(hi);
-            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2H + o1) = uint16_t(hi >> 16);
-            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2L + o0) = uint16_t(lo);
-            *reinterpret_cast<uint16_t *>(smem + T::OFF_A2L + o1) = uint16_t(lo >> 16);
+            split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
+            const uint32_t o = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
+            *reinterpret_cast<uint32_t *>(smem + T::OFF_A2H + o) = hi;
+            *reinterpret_cast<uint32_t *>(smem + T::OFF_A2L + o) = lo;
           }
         }
       }
@@ -580,7 +586,8 @@ std::vector<uint8_t> build_operand_block(const RefOps &o, bool bf16) {
     for (int i = 0; i < T::NP; ++i)
       for (int j = 0; j < T::NP; ++j) put(b1h, b1l, d * T::NB + i, j, T::K1, (*Ds[d])[i * T::NP + j]);
   for (int i = 0; i < T::NP; ++i)
-    for (int m = 0; m < T::NFF; ++m) put(b2h, b2l, i, m, T::K2, o.LIFT[i * T::NFF + m]);
+    for (int m = 0; m < T::NFF; ++m)
+      put(b2h, b2l, i, (m / T::NFP) * T::NFPE + m % T::NFP, T::K2, o.LIFT[i * T::NFF + m]);
   return blk;
 }
 
