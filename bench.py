@@ -475,8 +475,9 @@ def run_ensemble(args):
 
 def run_adjoint(args):
     """Adjoint workload: 20^3 x 6 jittered tets, N=4, FP32, 256 receivers,
-    checkpoints every 20 steps; adjoint-to-forward cost ratio and a finite
-    difference check along 4 directions."""
+    segment length chosen by the library from the free device memory (the
+    whole run in one stored segment when it fits); adjoint-to-forward cost
+    ratio and a finite difference check along 4 directions."""
     import numpy as np
     import torch
 
@@ -484,7 +485,7 @@ def run_adjoint(args):
     import workloads as W
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    N, n, steps, ck = 4, 20, args.steps, 20
+    N, n, steps, ck = 4, 20, args.steps, 0
     VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
     K = EToV.shape[0]
     eps = W.element_eps(K, seed=2)
@@ -504,6 +505,7 @@ def run_adjoint(args):
     s.adjoint(u0, recv, Eref, dt, steps, ck, eps=epsd)  # warm-up: the work buffers stay in the context
     adj_ms = _timed(lambda: out.setdefault("r", s.adjoint(u0, recv, Eref, dt, steps, ck, eps=epsd)), stream)
     J, g_eps, g_u0 = out["r"]
+    seg = s.adjoint_segment_steps()
     h = 1e-3
     dirs = 2.0 * W.uniform(5, 4 * K).reshape(4, K) - 1.0
     rels = []
@@ -518,8 +520,10 @@ def run_adjoint(args):
     line = {"metric": METRIC, "value": adj_ms / fwd_ms, "unit": "adjoint/forward time", "n_gpus": 1,
             "steps": steps, "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "adjoint, 20^3x6 jittered tets, N=4, 256 receivers, checkpoints every 20",
-                       "K": K, "dof": dof},
+            "config": {"workload": f"adjoint, 20^3x6 jittered tets, N=4, 256 receivers, {steps} steps in "
+                                   f"segments of {seg} (automatic; the last segment stored by the forward sweep)",
+                       "K": K, "dof": dof, "segment_steps": seg, "recomputed_steps": steps - seg,
+                       "segment_bytes": int(seg * 5 * 1.5 * 6 * K * ((s.Np + 3) // 4 * 4) * 4)},
             "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "J": J,
             "timing": "second call of each (warm-up first; adjoint work buffers kept in the context)",
             "forward_gdof_s": STAGES * dof * steps / (fwd_ms * 1e-3) / 1e9,

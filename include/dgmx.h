@@ -223,18 +223,29 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * of the run of dg_receiver_traces, and its exact discrete gradient by the
  * hand-written adjoint: the transposed LSERK4 recursion swept backwards stage
  * by stage (lambda_r += b_s lambda_u; lambda_u += dt A^T lambda_r;
- * dJ/deps += dt <lambda_r, dA/deps u_s>; lambda_r *= a_s), with the forward
- * state restored from checkpoints saved every ckpt_every steps (one segment of
- * stage states and stage right-hand sides is recomputed and held at a time).
- * Inputs (DEVICE): u0 [6][K][Np_pad], eps (K, or NULL = current), recv (R),
- * Eref [nsteps][3][R] FP32. Outputs: *J (HOST double), dJ_deps (DEVICE, K
- * doubles, reduced in FP64; may be NULL), dJ_du0 (DEVICE field vector; may be
- * NULL). FP32 CUDA-core kernels regardless of the context's precision.
- * Device memory: about (nsteps/ckpt_every + 10 ckpt_every + 8) field vectors.
- * Synchronises. Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE. */
+ * dJ/deps += dt <lambda_r, dA/deps u_s>; lambda_r *= a_s). The run is cut
+ * into segments of ckpt_every steps, aligned to its end (the first segment
+ * takes the remainder); every stage state and the E components of every stage
+ * right-hand side of one segment are held at a time. The forward sweep saves a
+ * checkpoint at each segment start and stores the last segment directly, so
+ * only the earlier segments are recomputed (nsteps - ckpt_every forward steps
+ * in all). ckpt_every = 0 picks the longest segment that fits in half of the
+ * device memory that is free or already held by these buffers (one segment,
+ * no recomputation, when the whole run fits); dg_adjoint_segment_steps reports
+ * the choice. Inputs (DEVICE): u0 [6][K][Np_pad], eps (K, or NULL = current),
+ * recv (R), Eref [nsteps][3][R] FP32. Outputs: *J (HOST double), dJ_deps
+ * (DEVICE, K doubles, reduced in FP64; may be NULL), dJ_du0 (DEVICE field
+ * vector; may be NULL). FP32 CUDA-core kernels regardless of the context's
+ * precision. Device memory: about (nsteps/ckpt_every + 7.5 ckpt_every + 8)
+ * field vectors. Synchronises. Errors: DG_ERR_ARG (also ckpt_every < 0),
+ * DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE. */
 int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, int ckpt_every,
                     float alpha, const int64_t *recv, int64_t R, const float *Eref, double *J, double *dJ_deps,
                     float *dJ_du0);
+
+/* Steps per segment used by the last dg_adjoint_step call on ctx (0 before
+ * the first call, or for ctx == NULL). */
+int dg_adjoint_segment_steps(const dg_ctx *ctx);
 
 /* Discrete energy 1/2 sum_k J_k (eps_k E^T M E + mu_k H^T M H), reduced in
  * FP64 on the device; *E_out is a HOST double. Synchronises the stream.

@@ -68,6 +68,7 @@ def lib():
             L.dg_ensemble_graph_used.argtypes = [vp]
             L.dg_receiver_traces.argtypes = [vp, vp, vp, dbl, i32, flt, vp, i64, vp]
             L.dg_adjoint_step.argtypes = [vp, vp, vp, dbl, i32, i32, flt, vp, i64, vp, C.POINTER(dbl), vp, vp]
+            L.dg_adjoint_segment_steps.argtypes = [vp]
             _lib = L
     return _lib
 
@@ -181,7 +182,8 @@ class Solver:
         return out
 
     def adjoint(self, u0, recv, Eref, dt: float, nsteps: int, ckpt_every: int = 20, eps=None, alpha: float = 1.0):
-        """Misfit J (float) and its gradients (dJ/deps FP64 [K], dJ/du0 [6][K][Np_pad])."""
+        """Misfit J (float) and its gradients (dJ/deps FP64 [K], dJ/du0 [6][K][Np_pad]).
+        ckpt_every = 0 lets the library choose the segment length from the free device memory."""
         import torch
         J = C.c_double()
         g_eps = torch.empty(self.K, dtype=torch.float64, device=u0.device)
@@ -190,6 +192,10 @@ class Solver:
                                           int(nsteps), int(ckpt_every), float(alpha), _t_ptr(recv), recv.numel(),
                                           _t_ptr(Eref), C.byref(J), _t_ptr(g_eps), _t_ptr(g_u0)))
         return J.value, g_eps, g_u0
+
+    def adjoint_segment_steps(self) -> int:
+        """Steps per segment used by the last adjoint call (ckpt_every = 0 chooses it)."""
+        return int(lib().dg_adjoint_segment_steps(self._h))
 
     # ---------------------------------------------------------------- ensembles
     def upload_ensemble(self, meshes, eps=None, dt=None):

@@ -573,6 +573,8 @@ using namespace dgmx;
 
 extern "C" {
 
+int dg_adjoint_segment_steps(const dg_ctx *ctx) { return ctx ? ctx->adj_segment : 0; }
+
 int dg_rhs_transpose(dg_ctx *ctx, const float *v, float *w, float alpha) {
   if (!ctx) return DG_ERR_ARG;
   if (ctx->K <= 0) return fail(ctx, DG_ERR_ARG, "dg_rhs_transpose: no mesh uploaded");
@@ -636,24 +638,41 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   int rc = check_common(ctx, u0, dt, nsteps, alpha, recv, R, "dg_adjoint_step");
   if (rc) return rc;
   if (!Eref) return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: null Eref");
-  if (ckpt_every < 1) return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: ckpt_every must be >= 1");
+  if (ckpt_every < 0) return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: ckpt_every must be >= 0");
   if (dJ_du0 && (reinterpret_cast<uintptr_t>(dJ_du0) & 15u))
     return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: dJ_du0 must be 16-byte aligned");
   if (eps && (rc = dg_set_eps(ctx, eps))) return rc;
-  const int C = ckpt_every < nsteps ? ckpt_every : nsteps;
-  const int nseg = (nsteps + C - 1) / C;
   const size_t fl = size_t(6) * ctx->K * ctx->ops.Npad;
   const size_t gfl = size_t(6) * ctx->K * 4 * ctx->ops.Nfp;
+  const size_t hfl = fl / 2; // three of the six fields
   cudaStream_t s = ctx->stream;
-
   AdjWorkspace &ws = workspace(ctx);
+
+  // steps per segment: given, or (0) as many as half of the device memory
+  // that is free or already held for segment storage can take
+  int C = ckpt_every;
+  if (C == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(ctx, DG_ERR_CUDA, "dg_adjoint_step: cudaMemGetInfo");
+    const size_t per_step = size_t(5) * (fl + hfl) * sizeof(float);
+    const size_t fit = (fr + ws.cap[10] + ws.cap[11]) / 2 / per_step;
+    C = fit < size_t(nsteps) ? int(fit) : nsteps;
+    if (C < 1) C = 1;
+  }
+  if (C > nsteps) C = nsteps;
+  // segments are aligned to the end of the run: all but the first have C
+  // steps; the last one is stored during the forward sweep, the others are
+  // recomputed from their checkpoints
+  const int nseg = (nsteps + C - 1) / C;
+  const int first_len = nsteps - (nseg - 1) * C;
+  auto seg_start = [&](int sg) { return sg == 0 ? 0 : first_len + (sg - 1) * C; };
+  ctx->adj_segment = C;
   float *u = ws.get<float>(0, fl), *nxt = ws.get<float>(1, fl), *res = ws.get<float>(2, fl);
   float *lu = ws.get<float>(3, fl), *lr = ws.get<float>(4, fl), *g = ws.get<float>(5, gfl);
   float *resid = ws.get<float>(6, size_t(nsteps) * 3 * R);
   double *Jd = ws.get<double>(7, 1), *grad = ws.get<double>(8, ctx->K);
   float *ck = ws.get<float>(9, fl * nseg);
   // stage states u_s and the E components of the stage right-hand sides A u_s of one segment
-  const size_t hfl = fl / 2; // three of the six fields
   float *US = ws.get<float>(10, fl * 5 * C), *RS = ws.get<float>(11, hfl * 5 * C);
   if (!u || !nxt || !res || !lu || !lr || !g || !resid || !Jd || !grad || !ck || !US || !RS)
     return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed (checkpoints and one segment of stage "
@@ -667,20 +686,49 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   StageArgs sa = stage_base(ctx, alpha, dt);
   const unsigned rb = unsigned((3 * R + 255) / 256);
 
-  // ---- forward sweep with checkpoints every C steps and the receiver residuals
-  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-    if (n % C == 0) e = cudaMemcpyAsync(ck + fl * (n / C), u, fl * 4, cudaMemcpyDeviceToDevice, s);
+  // one step of the stored form: every stage state and the E components of
+  // its right-hand side go to the segment buffers (state j of the segment
+  // that starts at checkpoint sg); returns the state after the step
+  auto stored_step = [&](int n, int n0, int sg) -> const float * {
     sa.res = res;
     for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
-      sa.u = u;
-      sa.u_out = nxt;
+      const size_t j = size_t(n - n0) * 5 + st;
+      sa.u = j == 0 ? ck + fl * sg : US + fl * j;
+      sa.u_out = (j + 1 < size_t(5) * C) ? US + fl * (j + 1) : nxt;
+      sa.rhs = RS + hfl * j;
       sa.rk_a = float(kLserkA[st]);
       sa.rk_b = float(kLserkB[st]);
-      e = launch_stage_simt(ctx->N, MODE_LSERK, sa, s);
-      std::swap(u, nxt);
+      e = launch_stage_simt(ctx->N, MODE_LSERK_STORE, sa, s);
+    }
+    const size_t jn = size_t(n - n0 + 1) * 5;
+    return jn < size_t(5) * C ? US + fl * jn : nxt;
+  };
+
+  // ---- forward sweep: checkpoints at the segment starts, the last segment
+  // stored, and the receiver residuals
+  const int n0_last = seg_start(nseg - 1);
+  for (int n = 0, sg = 0; n < nsteps && e == cudaSuccess; ++n) {
+    if (n == seg_start(sg)) {
+      e = cudaMemcpyAsync(ck + fl * sg, u, fl * 4, cudaMemcpyDeviceToDevice, s);
+      ++sg;
+    }
+    const float *after = u;
+    if (n >= n0_last) {
+      after = stored_step(n, n0_last, nseg - 1);
+    } else {
+      sa.res = res;
+      for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+        sa.u = u;
+        sa.u_out = nxt;
+        sa.rk_a = float(kLserkA[st]);
+        sa.rk_b = float(kLserkB[st]);
+        e = launch_stage_simt(ctx->N, MODE_LSERK, sa, s);
+        std::swap(u, nxt);
+      }
+      after = u;
     }
     if (e == cudaSuccess) {
-      k_recv_residual<<<rb, 256, 0, s>>>(u, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, Eref + int64_t(n) * 3 * R,
+      k_recv_residual<<<rb, 256, 0, s>>>(after, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, Eref + int64_t(n) * 3 * R,
                                          resid + int64_t(n) * 3 * R, Jd);
       e = cudaGetLastError();
     }
@@ -693,19 +741,10 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   aa.dt = float(dt);
   float pending = 1.f; // a of the stage reversed last, applied to lr by the next lift
   for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
-    const int n0 = seg * C, n1 = (n0 + C < nsteps) ? n0 + C : nsteps;
-    // recompute the segment, storing every stage state and its right-hand side
-    sa.res = res;
-    for (int n = n0; n < n1 && e == cudaSuccess; ++n)
-      for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
-        const size_t j = size_t(n - n0) * 5 + st;
-        sa.u = j == 0 ? ck + fl * seg : US + fl * j;
-        sa.u_out = (j + 1 < size_t(5) * C) ? US + fl * (j + 1) : nxt;
-        sa.rhs = RS + hfl * j;
-        sa.rk_a = float(kLserkA[st]);
-        sa.rk_b = float(kLserkB[st]);
-        e = launch_stage_simt(ctx->N, MODE_LSERK_STORE, sa, s);
-      }
+    const int n0 = seg_start(seg), n1 = seg + 1 < nseg ? seg_start(seg + 1) : nsteps;
+    // recompute the segment from its checkpoint (the last one is already stored)
+    if (seg < nseg - 1)
+      for (int n = n0; n < n1 && e == cudaSuccess; ++n) stored_step(n, n0, seg);
     for (int n = n1 - 1; n >= n0 && e == cudaSuccess; --n) {
       k_recv_source<<<rb, 256, 0, s>>>(lu, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, resid + int64_t(n) * 3 * R);
       e = cudaGetLastError();

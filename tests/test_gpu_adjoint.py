@@ -3,6 +3,9 @@
 - transpose identity <A u, v> = <u, A^T v> and parity of A^T with the oracle;
 - receiver traces and the misfit gradient against the FP64 oracle's discrete
   adjoint on the 6^3 x 6 version of the adjoint workload (N=4);
+- the same gradient for every segmentation of the run (recomputed segments,
+  segments aligned to the end with the last one stored, one stored segment,
+  the automatic choice);
 - central finite differences (step 1e-3, 16 seeded directions) of the misfit
   on the 20^3 x 6 adjoint workload (48,000 tets, N=4, 400 steps, checkpoints
   every 20 steps, 256 receivers).
@@ -76,6 +79,25 @@ def test_adjoint_gradient_matches_oracle_discrete_adjoint():
     assert abs(J - Jo) < 1e-5 * Jo
     assert rel(g_eps.cpu().numpy(), go_eps) < 1e-4
     assert rel(s.from_device(g_u0), go_u0) < 1e-4
+
+
+def test_adjoint_segmentations_agree():
+    # 4^3 x 6 tets at N=4, 12 steps: one-step segments (everything recomputed),
+    # segments of 5 aligned to the end (2 + 5 + 5, the last one stored by the
+    # forward sweep), one stored segment, and the automatic choice
+    N, n, steps = 4, 4, 12
+    s, m, eps, eps_t, u0, u0d, recv, rd, Eref, dt = _misfit_problem(N, n, steps)
+    epsd = torch.as_tensor(eps, device="cuda")
+    J1, ge1, gu1 = s.adjoint(u0d, rd, Eref, dt, steps, 1, eps=epsd)
+    assert s.adjoint_segment_steps() == 1
+    for ck, seg in ((5, 5), (12, 12), (40, 12), (0, 12)):
+        J, ge, gu = s.adjoint(u0d, rd, Eref, dt, steps, ck, eps=epsd)
+        assert s.adjoint_segment_steps() == seg
+        assert abs(J - J1) <= 1e-12 * J1
+        assert rel(ge.cpu().numpy(), ge1.cpu().numpy()) < 1e-6
+        assert rel(s.from_device(gu), s.from_device(gu1)) < 1e-6
+    with pytest.raises(dg.DGError):
+        s.adjoint(u0d, rd, Eref, dt, steps, -1, eps=epsd)
 
 
 def test_adjoint_finite_differences_full_size():
