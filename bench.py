@@ -64,8 +64,7 @@ def bytes_per_element(N: int, Npad: int) -> float:
 # DRAM bytes per launch of the dominant stage kernel from one ncu capture of the
 # default workload (profiles/k_stage_tc_fp16x3_n5_24cube.md); None where the
 # kernel changed since its counters were taken or none were taken.
-NCU_TRAFFIC = {("fp32", 5, 24): 241.824256e6 + 174.203648e6,
-               ("fp16x3", 5, 24): 241.912064e6 + 170.269696e6}
+NCU_TRAFFIC = {("fp32", 5, 24): 241.824256e6 + 174.203648e6}
 
 
 def measured_peaks():
