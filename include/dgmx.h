@@ -126,8 +126,9 @@ int dg_rhs(dg_ctx *ctx, const float *u, float *rhs, float alpha);
 
 /* Advance nsteps LSERK4 steps of size dt: for each of the five stages s,
  * res <- a_s res + dt A u, u <- u + b_s res (one fused kernel per stage).
- * u and res are DEVICE field vectors, updated in place; res should be zero
- * before the first step of a run (a_1 = 0 makes its old value irrelevant).
+ * u and res are DEVICE field vectors, updated in place; the entry value of
+ * res is not read (a_1 = 0: the first stage overwrites it), on exit res holds
+ * the last stage's residual.
  * Uses a library-owned scratch field vector for the stage ping-pong.
  * Errors: DG_ERR_ARG, DG_ERR_CUDA. */
 int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);

@@ -200,8 +200,11 @@ __device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, 
     if (MODE == MODE_RHS) {
       *reinterpret_cast<float4 *>(a.rhs + off) = make_float4(r4[0], r4[1], r4[2], r4[3]);
     } else {
-      float4 rs = COHERENT ? __ldcg(reinterpret_cast<const float4 *>(a.res + off))
-                           : *reinterpret_cast<const float4 *>(a.res + off);
+      // the first LSERK4 stage has a = 0: the residual it overwrites is not read
+      float4 rs = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.rk_a != 0.f)
+        rs = COHERENT ? __ldcg(reinterpret_cast<const float4 *>(a.res + off))
+                      : *reinterpret_cast<const float4 *>(a.res + off);
       float4 uo = reinterpret_cast<const float4 *>(s_u)[(c * EB + e) * NQ + q];
       float rv[4] = {rs.x, rs.y, rs.z, rs.w}, uv[4] = {uo.x, uo.y, uo.z, uo.w};
 #pragma unroll

@@ -140,6 +140,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t KN = a.K * NPP;
   const uint32_t sbase = umma::smem_u32(smem);
   const long long wlim = umma::wait_cycles(a.wait_limit); // main waits; drains use the default
+  // the first LSERK4 stage has a = 0: the residual it overwrites is not read
+  const bool read_res = MODE == MODE_LSERK && a.rk_a != 0.f;
 
   // fields of tile t into the A1 bytes, its face and element data into a
   // slot (one thread; completes on barU)
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       break;
     }
-    if (MODE == MODE_LSERK && rloader) {
+    if (read_res && rloader) {
       umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
       for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
     }
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     ok = umma::mbar_wait_bounded(bar2, phase, wlim) && ok;
-    if (MODE == MODE_LSERK) ok = umma::mbar_wait_bounded(barR, phase, wlim) && ok;
+    if (read_res) ok = umma::mbar_wait_bounded(barR, phase, wlim) && ok;
     // this slot's face and element data are rewritten by the staging after next
     umma::fence_proxy_async();
     if (__syncthreads_or(!ok)) {
@@ -487,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // give the products and the copies in flight one more bounded wait
         // before tensor and shared memory are released
         umma::mbar_wait_bounded(bar2, phase);
-        if (MODE == MODE_LSERK) umma::mbar_wait_bounded(barR, phase);
+        if (read_res) umma::mbar_wait_bounded(barR, phase);
         if (*s_staged) umma::mbar_wait_bounded(barU, phase ^ 1u);
       }
       break;
@@ -517,7 +519,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (MODE == MODE_RHS) {
               *op = make_float4(r4[0], r4[1], r4[2], r4[3]);
             } else {
-              const float4 rs = *reinterpret_cast<const float4 *>(s_res + soff + i);
+              const float4 rs = read_res ? *reinterpret_cast<const float4 *>(s_res + soff + i)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
               const float4 uo = *reinterpret_cast<const float4 *>(s_u + soff + i);
               const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
               float nr[4], nu[4];

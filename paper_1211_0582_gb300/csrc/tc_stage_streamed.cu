@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       const int64_t kb = int64_t(tu) * kTileS, nb = a.K - kb < kTileS ? a.K - kb : kTileS;
       for (int f = 0; f < 6; ++f) umma::prefetch_l2(a.u + f * KN + kb * NPP, uint32_t(nb * NPP * 4));
     }
-    if (MODE == MODE_LSERK && tr < ntiles) {
+    if (MODE == MODE_LSERK && a.rk_a != 0.f && tr < ntiles) {
       const int64_t kb = int64_t(tr) * kTileS, nb = a.K - kb < kTileS ? a.K - kb : kTileS;
       for (int f = 0; f < 6; ++f) umma::prefetch_l2(a.res + f * KN + kb * NPP, uint32_t(nb * NPP * 4));
     }
@@ -479,7 +479,8 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     // residual of one 8-node chunk of this lane's row (loaded one chunk ahead)
     auto load_res = [&](int ch, float4 &r0, float4 &r1) {
       r0 = r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (MODE != MODE_LSERK || !live || ch >= ch1) return;
+      // (the first LSERK4 stage has a = 0: the residual it overwrites is not read)
+      if (MODE != MODE_LSERK || a.rk_a == 0.f || !live || ch >= ch1) return;
       const float *rp = a.res + fld * KN + k * NPP + ch * 8;
       r0 = ldg4(rp);
       if (ch * 8 + 4 < NPP) r1 = ldg4(rp + 4);

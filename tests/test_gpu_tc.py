@@ -44,6 +44,28 @@ def test_tc_rhs_parity(precision, N, n):
     s.sync()
 
 
+@pytest.mark.parametrize("N,precision", [(3, "fp32"), (6, "fp32"), (4, "fp16x3"), (5, "bf16x3"), (7, "fp16x3"),
+                                         (6, "bf16x3")])
+def test_step_ignores_entry_residual(N, precision):
+    # a_1 = 0: the first stage of every step overwrites the residual without
+    # reading it, so a NaN residual on entry gives the same step as a zero one
+    import torch
+    VX, VY, VZ, EToV = W.kuhn_cube(3, jitter=0.1, seed=1)
+    s = dg.Solver(N, precision=precision).upload(VX, VY, VZ, EToV, eps=W.element_eps(EToV.shape[0], seed=2))
+    x, y, z = s.node_coords()
+    u0 = W.gaussian_pulse(x, y, z, seed=7)
+    outs = []
+    for fill in (0.0, float("nan")):
+        u, r = s.to_device(u0), s.zeros()
+        r.fill_(fill)
+        s.step(u, r, 1e-3, 2)
+        outs.append((s.from_device(u), r.cpu().numpy()))
+    assert np.isfinite(outs[1][0]).all()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
 def test_tc_smooth_field_and_scaling(precision):
     # a smooth field (strong cancellation in D u) at tiny and large magnitudes:
