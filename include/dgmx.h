@@ -166,11 +166,17 @@ int dg_ensemble_upload(dg_ctx *ctx, int M, const int64_t *Nv, const double *VX, 
 int dg_ensemble_layout(const dg_ctx *ctx, int *M, int64_t *offsets);
 
 /* Advance every mesh of the ensemble by nsteps LSERK4 steps of its own dt in
- * ONE persistent cooperative kernel launch (FP32 CUDA cores; a grid-wide
- * barrier with a bounded wait separates the stages; a wait that runs out sets
- * the flag reported by dg_sync), replayed from a CUDA graph captured on the
- * first call with these arguments. u and res are DEVICE field vectors (in/out).
- * The first call autotunes the elements per block unless dg_ensemble_tune ran. */
+ * ONE persistent cooperative kernel launch (a grid-wide barrier with a bounded
+ * wait separates the stages; a wait that runs out sets the flag reported by
+ * dg_sync), replayed from a CUDA graph captured on the first call with these
+ * arguments. FP32 contexts and N = 6, 7: the FP32 CUDA-core stage, elements
+ * per block autotuned on the first call unless dg_ensemble_tune ran.
+ * BF16X3/FP16X3 contexts at N <= 5: the tensor-core stage of dg_step (FP32
+ * fields, split-precision contractions), one block per SM, tiles of 20
+ * elements fixed by the 128-row matrix operation (nothing to tune; FP16X3
+ * scales each tile's fluxes, so a tile spanning two meshes couples their
+ * roundings, within the split's error). u and res are DEVICE field vectors
+ * (in/out; the entry value of res is not read). */
 int dg_ensemble_step(dg_ctx *ctx, float *u, float *res, int nsteps, float alpha);
 
 /* Autotuner: time every elements-per-block candidate of the persistent
@@ -181,7 +187,8 @@ int dg_ensemble_step(dg_ctx *ctx, float *u, float *res, int nsteps, float alpha)
 int dg_ensemble_tune(dg_ctx *ctx, int force);
 
 /* Tuning log: the chosen elements per block, and for each of the 4 candidates
- * its elements per block and measured ms per step (0 = not timed). HOST outputs. */
+ * its elements per block and measured ms per step (0 = not timed; the
+ * tensor-core form has one candidate, 20). HOST outputs. */
 int dg_ensemble_tuning(const dg_ctx *ctx, int *best_eb, int *eb, float *ms_per_step);
 
 /* 1 if the last dg_ensemble_step was replayed from a captured CUDA graph. */

@@ -20,6 +20,7 @@
 #include "../../include/dgmx.h"
 #include "common.cuh"
 #include "ensemble.cuh"
+#include "tc_api.h"
 
 namespace dgmx {
 
@@ -42,6 +43,7 @@ extern template cudaError_t launch_ensemble_order<7>(int, const StageArgs &, con
 namespace {
 
 constexpr int kCandidates = 4;
+constexpr int kTcTileElems = 20; // elements per tile of the tensor-core form
 
 int candidate_eb(int N, int i) {
   switch (N) {
@@ -99,9 +101,9 @@ std::string cache_path() {
   return std::string(home ? home : "/tmp") + "/.cache/dgmx_ensemble_tune.txt";
 }
 
-std::string cache_key(const EnsembleState &st, int N, int64_t K) {
+std::string cache_key(const EnsembleState &st, int N, int precision, int64_t K) {
   std::ostringstream os;
-  os << st.gpu << "|N=" << N << "|K=" << K;
+  os << st.gpu << "|N=" << N << "|P=" << precision << "|K=" << K;
   return os.str();
 }
 
@@ -148,13 +150,19 @@ StageCoeffs coeffs() {
   return rk;
 }
 
-// Enqueue one call: persistent launch for nsteps, then the copy back when the
-// stage count is odd (the result then sits in the scratch buffer).
+// Enqueue one call: persistent launch for nsteps (the tensor-core form in
+// split-precision contexts at N <= 5, whose tile is fixed by the 128-row
+// matrix operation; the FP32 form with candidate `cand` otherwise), then the
+// copy back when the stage count is odd (the result then sits in the scratch
+// buffer).
 cudaError_t enqueue(dg_ctx *c, EnsembleState &st, int cand, float *u, float *res, int nsteps, float alpha,
                     cudaStream_t s) {
   StageArgs a = ens_args(c, alpha);
   a.res = res;
-  cudaError_t e = launch_ensemble(c->N, cand, a, coeffs(), u, c->d_scratch, nsteps, st.gb, c->d_flag + 1, s, st.sms);
+  cudaError_t e = tc_ensemble_supported(c)
+                      ? launch_tc_ensemble(c, a, coeffs(), u, c->d_scratch, nsteps, st.gb, s)
+                      : launch_ensemble(c->N, cand, a, coeffs(), u, c->d_scratch, nsteps, st.gb, c->d_flag + 1, s,
+                                        st.sms);
   if (e == cudaSuccess && (5 * nsteps) % 2 == 1)
     e = cudaMemcpyAsync(u, c->d_scratch, size_t(6) * c->K * c->ops.Npad * sizeof(float), cudaMemcpyDeviceToDevice, s);
   return e;
@@ -260,7 +268,7 @@ int dg_ensemble_layout(const dg_ctx *ctx, int *M, int64_t *offsets) {
 int dg_ensemble_tune(dg_ctx *ctx, int force) {
   if (!ctx || !ctx->ens) return DG_ERR_ARG;
   EnsembleState &st = *state(ctx);
-  const std::string key = cache_key(st, ctx->N, ctx->K);
+  const std::string key = cache_key(st, ctx->N, ctx->precision, ctx->K);
   if (!force) {
     const int c = cache_lookup(key);
     if (c >= 0 && c < kCandidates) {
@@ -283,8 +291,10 @@ int dg_ensemble_tune(dg_ctx *ctx, int force) {
   if (e == cudaSuccess) e = cudaMemsetAsync(r, 0, fl * 4, s);
   float best_ms = 1e30f;
   int best = -1;
+  const bool tc = tc_ensemble_supported(ctx); // one configuration: nothing to choose
   for (int cand = 0; cand < kCandidates && e == cudaSuccess; ++cand) {
     st.ms[cand] = 0.f;
+    if (tc && cand > 0) continue;
     if (cand > 0 && candidate_eb(ctx->N, cand) == candidate_eb(ctx->N, cand - 1)) continue;
     float t_min = 1e30f;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
@@ -316,9 +326,11 @@ int dg_ensemble_tune(dg_ctx *ctx, int force) {
 int dg_ensemble_tuning(const dg_ctx *ctx, int *best_eb, int *eb, float *ms_per_step) {
   if (!ctx || !ctx->ens) return DG_ERR_ARG;
   const EnsembleState *st = static_cast<const EnsembleState *>(ctx->ens);
-  if (best_eb) *best_eb = st->best >= 0 ? candidate_eb(ctx->N, st->best) : 0;
+  const bool tc = tc_ensemble_supported(ctx);
+  auto eb_of = [&](int i) { return tc ? (i == 0 ? kTcTileElems : 0) : candidate_eb(ctx->N, i); };
+  if (best_eb) *best_eb = st->best >= 0 ? eb_of(st->best) : 0;
   for (int i = 0; i < kCandidates; ++i) {
-    if (eb) eb[i] = candidate_eb(ctx->N, i);
+    if (eb) eb[i] = eb_of(i);
     if (ms_per_step) ms_per_step[i] = st->ms[i];
   }
   return DG_OK;

@@ -31,6 +31,7 @@
 
 #include "../../include/dgmx.h"
 #include "flux.cuh"
+#include "grid_sync.cuh"
 #include "tc_api.h"
 #include "tc_common.cuh"
 #include "umma.cuh"
@@ -108,9 +109,22 @@ __device__ __forceinline__ void issue_split_gemm(uint32_t d_tmem, uint32_t a_hi,
   }
 }
 
-template <int N, int MODE, bool BF16>
+// Multi-step persistent form (ensembles): stage coefficients, the two state
+// buffers the stages alternate between, the step count and the grid barrier.
+struct EnsLaunch {
+  StageCoeffs rk;
+  float *ua, *ub;
+  int nsteps;
+  GridBarrier *gb;
+};
+
+// ENS = false: one stage (MODE_RHS or MODE_LSERK) over all tiles. ENS = true:
+// 5 * nsteps LSERK stages in one cooperative launch, a grid barrier after each
+// stage (a stage reads the neighbours' states the previous one wrote), field
+// gathers through L2 (another SM's L1 may hold a copy from two stages ago).
+template <int N, int MODE, bool BF16, bool ENS>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_stage_tc(StageArgs a, const uint4 *__restrict__ ops, int ntiles, int *err_flag) {
+    k_stage_tc(StageArgs a, const uint4 *__restrict__ ops, int ntiles, int *err_flag, EnsLaunch ens) {
   using T = TC<N>;
   constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, FS = T::FS;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -141,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t sbase = umma::smem_u32(smem);
   const long long wlim = umma::wait_cycles(a.wait_limit); // main waits; drains use the default
   // the first LSERK4 stage has a = 0: the residual it overwrites is not read
-  const bool read_res = MODE == MODE_LSERK && a.rk_a != 0.f;
+  bool read_res = MODE == MODE_LSERK && a.rk_a != 0.f;
 
   // fields of tile t into the A1 bytes, its face and element data into a
   // slot (one thread; completes on barU)
@@ -179,7 +193,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
-  if (stager && int(blockIdx.x) < ntiles) stage_tile(blockIdx.x, 0);
 
   // field split: warp w owns operand rows 8w..8w+7 of A1; lane -> (row, half of
   // a K group of 8), so one row's maximum is a reduction over 4 lanes and every
@@ -221,340 +234,377 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int ch1 = (part + 1) * CPP < NCH ? (part + 1) * CPP : NCH;
 
   uint32_t phase = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t k0 = int64_t(tile) * kTileElems;
-    const int ne = int(a.K - k0 < kTileElems ? a.K - k0 : kTileElems);
-    const uint32_t rowbytes = uint32_t(ne * NPP * 4);
-    const int slot = int(phase);
-    const uint8_t *fslot = smem + T::OFF_FACE + slot * T::FSLOT;
-    const float4 *s_fgeo = reinterpret_cast<const float4 *>(fslot + T::FGEO);
-    const float4 *s_fmat = reinterpret_cast<const float4 *>(fslot + T::FMAT);
-    const float *s_geo = reinterpret_cast<const float *>(fslot + T::FELEM);
-    const int2 *s_fconn = reinterpret_cast<const int2 *>(fslot + T::FCONN);
+  // the residual barrier completes only for tiles of stages that read the
+  // residual, so its parity is counted separately from the tile parity
+  uint32_t rphase = 0;
+  bool failed = false;
+  const int nstages = ENS ? 5 * ens.nsteps : 1;
+  for (int sg = 0; sg < nstages && !failed; ++sg) {
+    if constexpr (ENS) {
+      const bool flip = (sg & 1) != 0;
+      a.u = flip ? ens.ub : ens.ua;
+      a.u_out = flip ? ens.ua : ens.ub;
+      a.rk_a = ens.rk.a[sg % 5];
+      a.rk_b = ens.rk.b[sg % 5];
+      read_res = a.rk_a != 0.f;
+    }
+    // the stage's first tile (the following ones are staged one tile ahead)
+    if (stager && int(blockIdx.x) < ntiles) {
+      if (ENS) umma::fence_proxy_async_global();
+      stage_tile(blockIdx.x, int(phase));
+    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int64_t k0 = int64_t(tile) * kTileElems;
+      const int ne = int(a.K - k0 < kTileElems ? a.K - k0 : kTileElems);
+      const uint32_t rowbytes = uint32_t(ne * NPP * 4);
+      const int slot = int(phase);
+      const uint8_t *fslot = smem + T::OFF_FACE + slot * T::FSLOT;
+      const float4 *s_fgeo = reinterpret_cast<const float4 *>(fslot + T::FGEO);
+      const float4 *s_fmat = reinterpret_cast<const float4 *>(fslot + T::FMAT);
+      const float *s_geo = reinterpret_cast<const float *>(fslot + T::FELEM);
+      const int2 *s_fconn = reinterpret_cast<const int2 *>(fslot + T::FCONN);
 
-    // ---- 1. the staged fields into registers; once the previous tile's bulk
-    // stores have read shared memory, the residual copy starts and the fields
-    // go to the tile staging and (split) to the A1 operand
-    const bool okU = umma::mbar_wait_bounded(barU, phase, wlim);
-    float4 v[R1];
-    float mx = 0.f;
+      // ---- 1. the staged fields into registers; once the previous tile's bulk
+      // stores have read shared memory, the residual copy starts and the fields
+      // go to the tile staging and (split) to the A1 operand
+      const bool okU = umma::mbar_wait_bounded(barU, phase, wlim);
+      float4 v[R1];
+      float mx = 0.f;
 #pragma unroll
-    for (int s = 0; s < R1; ++s) {
-      const int k = kq1 + 16 * s;
-      v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (cr1 >= 0 && k < NPP && e1 < ne) {
-        v[s] = *reinterpret_cast<const float4 *>(s_stage + f1 * FS + e1 * NPP + k);
-        if (k + 3 >= NP) {
-          if (k + 0 >= NP) v[s].x = 0.f;
-          if (k + 1 >= NP) v[s].y = 0.f;
-          if (k + 2 >= NP) v[s].z = 0.f;
-          if (k + 3 >= NP) v[s].w = 0.f;
-        }
-      }
-      if constexpr (!BF16) mx = absmax4(mx, v[s]);
-    }
-    float sc1 = 1.f, inv1r = 1.f;
-    if constexpr (!BF16) {
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-      row_scale(mx, sc1, inv1r);
-    }
-    if (__syncthreads_or(!okU)) {
-      if (tid == 0) {
-        atomicExch(err_flag, 1);
-        umma::mbar_wait_bounded(barU, phase);
-      }
-      break;
-    }
-    if (read_res && rloader) {
-      umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
-      for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
-    }
-    if (!BF16 && cr1 >= 0 && lane < 8) s_inv1[cr1] = inv1r;
-#pragma unroll
-    for (int s = 0; s < R1; ++s) {
-      const int k = kq1 + 16 * s;
-      if (cr1 >= 0 && k < T::K1) {
-        if (k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[s];
-        float4 w = v[s];
-        if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
-        uint2 hi, lo;
-        split2<BF16>(w.x, w.y, hi.x, lo.x);
-        split2<BF16>(w.z, w.w, hi.y, lo.y);
-        const uint32_t off = umma::kmajor_offset(uint32_t(r1), uint32_t(k), uint32_t(T::K1));
-        *reinterpret_cast<uint2 *>(smem + T::OFF_A1H + off) = hi;
-        *reinterpret_cast<uint2 *>(smem + T::OFF_A1L + off) = lo;
-      }
-    }
-    umma::fence_proxy_async();
-    __syncthreads();
-
-    // ---- 3. local differentiation on the tensor cores (asynchronous)
-    if (issuer) {
-      umma::fence_after_sync();
-      issue_split_gemm<BF16, T::K1, T::N1>(tmem, sbase + T::OFF_A1H, sbase + T::OFF_A1L, sbase + T::OFF_B1H,
-                                           sbase + T::OFF_B1L);
-      umma::commit(bar1);
-    }
-    bool ok = true;
-
-    // ---- 4. upwind flux (overlaps GEMM1), in registers
-    // neighbour traces outside the tile are requested before the field split,
-    // which hides their latency; neighbours inside the tile are read from the
-    // staged fields once they are in place
-    float qp[R2][2][6];
-    int lidx[R2][2];
-#pragma unroll
-    for (int s = 0; s < R2; ++s) {
-      const int blk = warp + 16 * s;
-      const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
-      const int f = fm / NFPE, mm = fm - f * NFPE;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        lidx[s][h] = -1;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) qp[s][h][c] = 0.f;
-      }
-      if (blk < NBLK && f < 4 && e < ne) {
-        const int2 cn = s_fconn[e * 4 + f];
-        if (cn.y != kBoundaryConn) {
-          const int el = cn.x - int(k0);
-          const bool local = el >= 0 && el < ne;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (mm + h < NFP) {
-              const int node = s_nb[cn.y * NFP + mm + h];
-              if (local) {
-                lidx[s][h] = el * NPP + node;
-              } else {
-                const float *up = a.u + int64_t(cn.x) * NPP + node;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) qp[s][h][c] = __ldg(up + c * KN);
-              }
-            }
+      for (int s = 0; s < R1; ++s) {
+        const int k = kq1 + 16 * s;
+        v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cr1 >= 0 && k < NPP && e1 < ne) {
+          v[s] = *reinterpret_cast<const float4 *>(s_stage + f1 * FS + e1 * NPP + k);
+          if (k + 3 >= NP) {
+            if (k + 0 >= NP) v[s].x = 0.f;
+            if (k + 1 >= NP) v[s].y = 0.f;
+            if (k + 2 >= NP) v[s].z = 0.f;
+            if (k + 3 >= NP) v[s].w = 0.f;
           }
         }
+        if constexpr (!BF16) mx = absmax4(mx, v[s]);
       }
-    }
-    float fl[R2][2][6];
-    uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int s = 0; s < R2; ++s) {
-      const int blk = warp + 16 * s;
-      const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
-      const int f = fm / NFPE, mm = fm - f * NFPE;
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) fl[s][h][c] = 0.f;
-      if (blk < NBLK && f < 4 && e < ne) {
-        const float4 g0 = s_fgeo[e * 4 + f], w1 = s_fmat[e * 4 + f];
-        const bool wall = s_fconn[e * 4 + f].y == kBoundaryConn;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (mm + h < NFP) {
-            const int vm = s_fm[f * NFP + mm + h];
-            float qm[6], q[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) q[c] = lidx[s][h] >= 0 ? s_u[c * FS + lidx[s][h]] : qp[s][h][c];
-            if (wall) {
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                q[c] = -qm[c];
-                q[c + 3] = qm[c + 3];
-              }
-            }
-            maxwell_flux_w(g0, qm, q, w1, a.alpha, fl[s][h]);
-          }
-        }
-      }
+      float sc1 = 1.f, inv1r = 1.f;
       if constexpr (!BF16) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][h][c])));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        row_scale(mx, sc1, inv1r);
       }
-    }
-    // once GEMM1 has read A1, the next tile's fields and face data are staged
-    if (stager) {
-      ok = umma::mbar_wait_bounded(bar1, phase, wlim);
-      const bool more = ok && tile + int(gridDim.x) < ntiles;
-      if (more) stage_tile(tile + gridDim.x, slot ^ 1);
-      *s_staged = more ? 1 : 0;
-    }
-    if constexpr (!BF16) {
-      // one FP16 scale per field component of the tile: |x| as float bits
-      // orders like |x|
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const uint32_t m = __reduce_max_sync(0xffffffffu, fmx[c]);
-        if (lane == 0) atomicMax(s_mx2 + c, m);
+      if (__syncthreads_or(!okU)) {
+        if (tid == 0) {
+          atomicExch(err_flag, 1);
+          umma::mbar_wait_bounded(barU, phase);
+        }
+        failed = true;
+        break;
       }
-    }
-    // the previous tile's bulk stores must have read the A2 bytes
-    if (storer) umma::bulk_wait_read_all();
-    __syncthreads();
-
-    // ---- 5. split the face fluxes into the A2 operand
-    {
-      float sc2[6];
+      if (read_res && rloader) {
+        umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
+        for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
+      }
+      if (!BF16 && cr1 >= 0 && lane < 8) s_inv1[cr1] = inv1r;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        sc2[c] = 1.f;
-        if constexpr (!BF16) {
-          float inv;
-          row_scale(__uint_as_float(s_mx2[c]), sc2[c], inv);
+      for (int s = 0; s < R1; ++s) {
+        const int k = kq1 + 16 * s;
+        if (cr1 >= 0 && k < T::K1) {
+          if (k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[s];
+          float4 w = v[s];
+          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+          uint2 hi, lo;
+          split2<BF16>(w.x, w.y, hi.x, lo.x);
+          split2<BF16>(w.z, w.w, hi.y, lo.y);
+          const uint32_t off = umma::kmajor_offset(uint32_t(r1), uint32_t(k), uint32_t(T::K1));
+          *reinterpret_cast<uint2 *>(smem + T::OFF_A1H + off) = hi;
+          *reinterpret_cast<uint2 *>(smem + T::OFF_A1L + off) = lo;
         }
       }
+      umma::fence_proxy_async();
+      __syncthreads();
+
+      // ---- 3. local differentiation on the tensor cores (asynchronous)
+      if (issuer) {
+        umma::fence_after_sync();
+        issue_split_gemm<BF16, T::K1, T::N1>(tmem, sbase + T::OFF_A1H, sbase + T::OFF_A1L, sbase + T::OFF_B1H,
+                                             sbase + T::OFF_B1L);
+        umma::commit(bar1);
+      }
+      bool ok = true;
+
+      // ---- 4. upwind flux (overlaps GEMM1), in registers
+      // neighbour traces outside the tile are requested before the field split,
+      // which hides their latency; neighbours inside the tile are read from the
+      // staged fields once they are in place
+      float qp[R2][2][6];
+      int lidx[R2][2];
 #pragma unroll
       for (int s = 0; s < R2; ++s) {
         const int blk = warp + 16 * s;
         const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
-        if (blk < NBLK) {
-          // the six rows of element e lie in one TMEM lane quarter; a column
-          // pair is one 32-bit word of a core-matrix row
-          const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            uint32_t hi, lo;
-            split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
-            const uint32_t o = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
-            *reinterpret_cast<uint32_t *>(smem + T::OFF_A2H + o) = hi;
-            *reinterpret_cast<uint32_t *>(smem + T::OFF_A2L + o) = lo;
-          }
-        }
-      }
-    }
-    umma::fence_proxy_async();
-    __syncthreads();
-
-    // ---- 6. flux lifting on the tensor cores; meanwhile the volume terms
-    // from GEMM1: chain rule (eq. dg-reference-matrices) and curls
-    if (issuer) {
-      umma::fence_after_sync();
-      issue_split_gemm<BF16, T::K2, T::N2>(tmem + uint32_t(T::N1), sbase + T::OFF_A2H, sbase + T::OFF_A2L,
-                                           sbase + T::OFF_B2H, sbase + T::OFF_B2L);
-      umma::commit(bar2);
-    }
-    const bool live = lane_used && e_loc < ne;
-    float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f;
-    if (live) {
-      const float *g = s_geo + e_loc * G_STRIDE;
-      g1r = g[G_RX + dl1], g1s = g[G_SX + dl1], g1t = g[G_TX + dl1];
-      g2r = g[G_RX + dl2], g2s = g[G_SX + dl2], g2t = g[G_TX + dl2];
-      w = g[isE ? G_IEPS : G_IMU];
-    }
-    float inv2 = 1.f;
-    if constexpr (!BF16) {
-      // the row's FP16 scale is undone through the metric factors of the chain rule
-      float sc;
-      const float inv1 = s_inv1[lane_used ? ridx : 0];
-      g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
-      row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
-    }
-    ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
-    umma::fence_after_sync();
-    float vol[CPP][8];
-#pragma unroll
-    for (int c = 0; c < CPP; ++c) {
-      const int ch = ch0 + c;
-      if (ch >= ch1) break;
-      const int i0 = ch * 8;
-      float ur[8], us[8], ut[8];
-      umma::tmem_ld8(lane_taddr + uint32_t(i0), ur);
-      umma::tmem_ld8(lane_taddr + uint32_t(T::NB + i0), us);
-      umma::tmem_ld8(lane_taddr + uint32_t(2 * T::NB + i0), ut);
-      umma::tmem_wait_ld();
-      umma::reg_fence8(ur);
-      umma::reg_fence8(us);
-      umma::reg_fence8(ut);
-#pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        const float p1 = g1r * ur[n] + g1s * us[n] + g1t * ut[n];
-        const float p2 = g2r * ur[n] + g2s * us[n] + g2t * ut[n];
-        const float v1 = __shfl_sync(0xffffffffu, p1, src1);
-        const float v2 = __shfl_sync(0xffffffffu, p2, src2);
-        vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
-      }
-    }
-    ok = umma::mbar_wait_bounded(bar2, phase, wlim) && ok;
-    if (read_res) ok = umma::mbar_wait_bounded(barR, phase, wlim) && ok;
-    // this slot's face and element data are rewritten by the staging after next
-    umma::fence_proxy_async();
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicExch(err_flag, 1);
-        // give the products and the copies in flight one more bounded wait
-        // before tensor and shared memory are released
-        umma::mbar_wait_bounded(bar2, phase);
-        if (read_res) umma::mbar_wait_bounded(barR, phase);
-        if (*s_staged) umma::mbar_wait_bounded(barU, phase ^ 1u);
-      }
-      break;
-    }
-    umma::fence_after_sync();
-
-    // ---- 7. epilogue: lifted flux, material scale, update; results go to the
-    // A2 bytes
-#pragma unroll
-    for (int c = 0; c < CPP; ++c) {
-      const int ch = ch0 + c;
-      if (ch >= ch1) break;
-      const int i0 = ch * 8;
-      float lf[8];
-      umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
-      umma::tmem_wait_ld();
-      umma::reg_fence8(lf);
-      if (live) {
+        const int f = fm / NFPE, mm = fm - f * NFPE;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int i = i0 + 4 * h;
-          if (i < NPP) {
-            float r4[4];
+          lidx[s][h] = -1;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? (vol[c][4 * h + q] + lf[4 * h + q] * inv2) * w : 0.f;
-            float4 *op = reinterpret_cast<float4 *>(s_out + soff + i);
-            if (MODE == MODE_RHS) {
-              *op = make_float4(r4[0], r4[1], r4[2], r4[3]);
-            } else {
-              const float4 rs = read_res ? *reinterpret_cast<const float4 *>(s_res + soff + i)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-              const float4 uo = *reinterpret_cast<const float4 *>(s_u + soff + i);
-              const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
-              float nr[4], nu[4];
+          for (int c = 0; c < 6; ++c) qp[s][h][c] = 0.f;
+        }
+        if (blk < NBLK && f < 4 && e < ne) {
+          const int2 cn = s_fconn[e * 4 + f];
+          if (cn.y != kBoundaryConn) {
+            const int el = cn.x - int(k0);
+            const bool local = el >= 0 && el < ne;
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const bool pad = i + q >= NP;
-                nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[q], a.dt * r4[q]);
-                nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
+            for (int h = 0; h < 2; ++h) {
+              if (mm + h < NFP) {
+                const int node = s_nb[cn.y * NFP + mm + h];
+                if (local) {
+                  lidx[s][h] = el * NPP + node;
+                } else {
+                  const float *up = a.u + int64_t(cn.x) * NPP + node;
+#pragma unroll
+                  for (int c = 0; c < 6; ++c) qp[s][h][c] = ENS ? __ldcg(up + c * KN) : __ldg(up + c * KN);
+                }
               }
-              op[0] = make_float4(nr[0], nr[1], nr[2], nr[3]);
-              op[6 * FS / 4] = make_float4(nu[0], nu[1], nu[2], nu[3]);
             }
           }
         }
       }
-    }
-    umma::fence_proxy_async();
-    umma::fence_before_sync();
-    __syncthreads();
-    // ---- 8. write the tile back with asynchronous bulk stores; clear the
-    // flux maxima for the next tile
-    if (storer) {
-      for (int f = 0; f < 6; ++f) {
-        if (MODE == MODE_RHS) {
-          umma::bulk_s2g(a.rhs + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
-        } else {
-          umma::bulk_s2g(a.res + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
-          umma::bulk_s2g(a.u_out + f * KN + k0 * NPP, s_out + (6 + f) * FS, rowbytes);
+      float fl[R2][2][6];
+      uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int s = 0; s < R2; ++s) {
+        const int blk = warp + 16 * s;
+        const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+        const int f = fm / NFPE, mm = fm - f * NFPE;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) fl[s][h][c] = 0.f;
+        if (blk < NBLK && f < 4 && e < ne) {
+          const float4 g0 = s_fgeo[e * 4 + f], w1 = s_fmat[e * 4 + f];
+          const bool wall = s_fconn[e * 4 + f].y == kBoundaryConn;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (mm + h < NFP) {
+              const int vm = s_fm[f * NFP + mm + h];
+              float qm[6], q[6];
+#pragma unroll
+              for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
+#pragma unroll
+              for (int c = 0; c < 6; ++c) q[c] = lidx[s][h] >= 0 ? s_u[c * FS + lidx[s][h]] : qp[s][h][c];
+              if (wall) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  q[c] = -qm[c];
+                  q[c + 3] = qm[c + 3];
+                }
+              }
+              maxwell_flux_w(g0, qm, q, w1, a.alpha, fl[s][h]);
+            }
+          }
+        }
+        if constexpr (!BF16) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][h][c])));
         }
       }
-      umma::bulk_commit();
+      // once GEMM1 has read A1, the next tile's fields and face data are staged
+      if (stager) {
+        ok = umma::mbar_wait_bounded(bar1, phase, wlim);
+        const bool more = ok && tile + int(gridDim.x) < ntiles;
+        if (more) stage_tile(tile + gridDim.x, slot ^ 1);
+        *s_staged = more ? 1 : 0;
+      }
+      if constexpr (!BF16) {
+        // one FP16 scale per field component of the tile: |x| as float bits
+        // orders like |x|
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const uint32_t m = __reduce_max_sync(0xffffffffu, fmx[c]);
+          if (lane == 0) atomicMax(s_mx2 + c, m);
+        }
+      }
+      // the previous tile's bulk stores must have read the A2 bytes
+      if (storer) umma::bulk_wait_read_all();
+      __syncthreads();
+
+      // ---- 5. split the face fluxes into the A2 operand
+      {
+        float sc2[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          sc2[c] = 1.f;
+          if constexpr (!BF16) {
+            float inv;
+            row_scale(__uint_as_float(s_mx2[c]), sc2[c], inv);
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < R2; ++s) {
+          const int blk = warp + 16 * s;
+          const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+          if (blk < NBLK) {
+            // the six rows of element e lie in one TMEM lane quarter; a column
+            // pair is one 32-bit word of a core-matrix row
+            const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              uint32_t hi, lo;
+              split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
+              const uint32_t o = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
+              *reinterpret_cast<uint32_t *>(smem + T::OFF_A2H + o) = hi;
+              *reinterpret_cast<uint32_t *>(smem + T::OFF_A2L + o) = lo;
+            }
+          }
+        }
+      }
+      umma::fence_proxy_async();
+      __syncthreads();
+
+      // ---- 6. flux lifting on the tensor cores; meanwhile the volume terms
+      // from GEMM1: chain rule (eq. dg-reference-matrices) and curls
+      if (issuer) {
+        umma::fence_after_sync();
+        issue_split_gemm<BF16, T::K2, T::N2>(tmem + uint32_t(T::N1), sbase + T::OFF_A2H, sbase + T::OFF_A2L,
+                                             sbase + T::OFF_B2H, sbase + T::OFF_B2L);
+        umma::commit(bar2);
+      }
+      const bool live = lane_used && e_loc < ne;
+      float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f, dtk = a.dt;
+      if (live) {
+        const float *g = s_geo + e_loc * G_STRIDE;
+        if (a.dt_geo) dtk = g[G_DT];
+        g1r = g[G_RX + dl1], g1s = g[G_SX + dl1], g1t = g[G_TX + dl1];
+        g2r = g[G_RX + dl2], g2s = g[G_SX + dl2], g2t = g[G_TX + dl2];
+        w = g[isE ? G_IEPS : G_IMU];
+      }
+      float inv2 = 1.f;
+      if constexpr (!BF16) {
+        // the row's FP16 scale is undone through the metric factors of the chain rule
+        float sc;
+        const float inv1 = s_inv1[lane_used ? ridx : 0];
+        g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
+        row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
+      }
+      ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
+      umma::fence_after_sync();
+      float vol[CPP][8];
+#pragma unroll
+      for (int c = 0; c < CPP; ++c) {
+        const int ch = ch0 + c;
+        if (ch >= ch1) break;
+        const int i0 = ch * 8;
+        float ur[8], us[8], ut[8];
+        umma::tmem_ld8(lane_taddr + uint32_t(i0), ur);
+        umma::tmem_ld8(lane_taddr + uint32_t(T::NB + i0), us);
+        umma::tmem_ld8(lane_taddr + uint32_t(2 * T::NB + i0), ut);
+        umma::tmem_wait_ld();
+        umma::reg_fence8(ur);
+        umma::reg_fence8(us);
+        umma::reg_fence8(ut);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+          const float p1 = g1r * ur[n] + g1s * us[n] + g1t * ut[n];
+          const float p2 = g2r * ur[n] + g2s * us[n] + g2t * ut[n];
+          const float v1 = __shfl_sync(0xffffffffu, p1, src1);
+          const float v2 = __shfl_sync(0xffffffffu, p2, src2);
+          vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
+        }
+      }
+      ok = umma::mbar_wait_bounded(bar2, phase, wlim) && ok;
+      if (read_res) ok = umma::mbar_wait_bounded(barR, rphase, wlim) && ok;
+      // this slot's face and element data are rewritten by the staging after next
+      umma::fence_proxy_async();
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicExch(err_flag, 1);
+          // give the products and the copies in flight one more bounded wait
+          // before tensor and shared memory are released
+          umma::mbar_wait_bounded(bar2, phase);
+          if (read_res) umma::mbar_wait_bounded(barR, rphase);
+          if (*s_staged) umma::mbar_wait_bounded(barU, phase ^ 1u);
+        }
+        failed = true;
+        break;
+      }
+      umma::fence_after_sync();
+
+      // ---- 7. epilogue: lifted flux, material scale, update; results go to the
+      // A2 bytes
+#pragma unroll
+      for (int c = 0; c < CPP; ++c) {
+        const int ch = ch0 + c;
+        if (ch >= ch1) break;
+        const int i0 = ch * 8;
+        float lf[8];
+        umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
+        umma::tmem_wait_ld();
+        umma::reg_fence8(lf);
+        if (live) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int i = i0 + 4 * h;
+            if (i < NPP) {
+              float r4[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? (vol[c][4 * h + q] + lf[4 * h + q] * inv2) * w : 0.f;
+              float4 *op = reinterpret_cast<float4 *>(s_out + soff + i);
+              if (MODE == MODE_RHS) {
+                *op = make_float4(r4[0], r4[1], r4[2], r4[3]);
+              } else {
+                const float4 rs = read_res ? *reinterpret_cast<const float4 *>(s_res + soff + i)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 uo = *reinterpret_cast<const float4 *>(s_u + soff + i);
+                const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
+                float nr[4], nu[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const bool pad = i + q >= NP;
+                  nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[q], dtk * r4[q]);
+                  nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
+                }
+                op[0] = make_float4(nr[0], nr[1], nr[2], nr[3]);
+                op[6 * FS / 4] = make_float4(nu[0], nu[1], nu[2], nu[3]);
+              }
+            }
+          }
+        }
+      }
+      umma::fence_proxy_async();
+      umma::fence_before_sync();
+      __syncthreads();
+      // ---- 8. write the tile back with asynchronous bulk stores; clear the
+      // flux maxima for the next tile
+      if (storer) {
+        for (int f = 0; f < 6; ++f) {
+          if (MODE == MODE_RHS) {
+            umma::bulk_s2g(a.rhs + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
+          } else {
+            umma::bulk_s2g(a.res + f * KN + k0 * NPP, s_out + f * FS, rowbytes);
+            umma::bulk_s2g(a.u_out + f * KN + k0 * NPP, s_out + (6 + f) * FS, rowbytes);
+          }
+        }
+        umma::bulk_commit();
+      }
+      if (!BF16 && tid < 8) s_mx2[tid] = 0u;
+      phase ^= 1u;
+      if (read_res) rphase ^= 1u;
     }
-    if (!BF16 && tid < 8) s_mx2[tid] = 0u;
-    phase ^= 1u;
+    if constexpr (ENS) {
+      if (!failed) {
+        // the stage's results are in global memory before any block reads them
+        if (storer) {
+          umma::bulk_wait_all();
+          umma::fence_proxy_async_global();
+        }
+        if (!grid_barrier(ens.gb, wlim)) {
+          if (tid == 0) atomicExch(err_flag, 1);
+          failed = true;
+        }
+      }
+    }
   }
   if (storer) umma::bulk_wait_all();
   __syncthreads();
@@ -598,13 +648,42 @@ template <int N, int MODE, bool BF16>
 cudaError_t launch_tc_kernel(const StageArgs &a, const TcState &st, int *flag, cudaStream_t s) {
   using T = TC<N>;
   static_assert(T::SMEM <= 232448, "tensor-core tile does not fit in shared memory");
-  auto kern = k_stage_tc<N, MODE, BF16>;
+  auto kern = k_stage_tc<N, MODE, BF16, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
   if (e != cudaSuccess) return e;
   const int ntiles = int((a.K + kTileElems - 1) / kTileElems);
   const int grid = ntiles < st.sms ? ntiles : st.sms;
-  kern<<<grid, kThreads, T::SMEM, s>>>(a, reinterpret_cast<const uint4 *>(st.d_ops), ntiles, flag);
+  kern<<<grid, kThreads, T::SMEM, s>>>(a, reinterpret_cast<const uint4 *>(st.d_ops), ntiles, flag, EnsLaunch{});
   return cudaGetLastError();
+}
+
+// Cooperative launch of the multi-step form: one block per SM, all resident.
+template <int N, bool BF16>
+cudaError_t launch_tc_ens_kernel(const StageArgs &a, const TcState &st, const EnsLaunch &ens, int *flag,
+                                 cudaStream_t s) {
+  using T = TC<N>;
+  auto kern = k_stage_tc<N, MODE_LSERK, BF16, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+  if (e != cudaSuccess) return e;
+  const int ntiles = int((a.K + kTileElems - 1) / kTileElems);
+  const int grid = ntiles < st.sms ? ntiles : st.sms;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = T::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a, reinterpret_cast<const uint4 *>(st.d_ops), ntiles, flag, ens);
+}
+
+template <int N>
+cudaError_t launch_tc_ens_order(bool bf16, const StageArgs &a, const TcState &st, const EnsLaunch &ens, int *flag,
+                                cudaStream_t s) {
+  return bf16 ? launch_tc_ens_kernel<N, true>(a, st, ens, flag, s) : launch_tc_ens_kernel<N, false>(a, st, ens, flag, s);
 }
 
 template <int N>
@@ -666,6 +745,27 @@ void tc_free(dg_ctx *ctx) {
     delete st;
   }
   ctx->tc = nullptr;
+}
+
+bool tc_ensemble_supported(const dg_ctx *ctx) {
+  return ctx->tc != nullptr && ctx->N >= 1 && ctx->N <= 5 &&
+         (ctx->precision == DG_BF16X3 || ctx->precision == DG_FP16X3);
+}
+
+cudaError_t launch_tc_ensemble(dg_ctx *ctx, const StageArgs &a, const StageCoeffs &rk, float *u_a, float *u_b,
+                               int nsteps, GridBarrier *gb, cudaStream_t s) {
+  const TcState *st = static_cast<const TcState *>(ctx->tc);
+  if (!st || !tc_ensemble_supported(ctx)) return cudaErrorNotSupported;
+  const bool bf16 = ctx->precision == DG_BF16X3;
+  int *flag = ctx->d_flag + 1;
+  const EnsLaunch ens{rk, u_a, u_b, nsteps, gb};
+  switch (ctx->N) {
+  case 1: return launch_tc_ens_order<1>(bf16, a, *st, ens, flag, s);
+  case 2: return launch_tc_ens_order<2>(bf16, a, *st, ens, flag, s);
+  case 3: return launch_tc_ens_order<3>(bf16, a, *st, ens, flag, s);
+  case 4: return launch_tc_ens_order<4>(bf16, a, *st, ens, flag, s);
+  default: return launch_tc_ens_order<5>(bf16, a, *st, ens, flag, s);
+  }
 }
 
 cudaError_t launch_stage_tc(dg_ctx *ctx, int mode, const StageArgs &a) {

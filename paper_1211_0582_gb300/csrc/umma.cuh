@@ -77,6 +77,9 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 
 // Make generic-proxy shared-memory writes visible to the async proxy (MMA reads).
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// The same between the generic and the async proxy for global memory (bulk
+// stores of one stage before, bulk loads of the next stage after a grid barrier).
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // 32 lanes x 32 bits, 8 consecutive columns per thread.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {

@@ -1,6 +1,8 @@
 """GPU checks of the ensemble form: many meshes of uneven size, own materials
 and own time steps, advanced together in one persistent launch (replayed from
-a CUDA graph) must reproduce what each mesh does alone, and the FP64 oracle."""
+a CUDA graph) must reproduce what each mesh does alone, and the FP64 oracle.
+Both forms: FP32 on the CUDA cores (tuned elements per block) and, in
+split-precision contexts, the tensor-core stage (20-element tiles)."""
 import numpy as np
 import pytest
 import torch
@@ -27,11 +29,12 @@ def initial(s_single, i):
     return W.gaussian_pulse(x, y, z, seed=7, index=i) + 0.1 * W.cavity_mode(x, y, z, 0.0)
 
 
-def run_pair(N, ns, steps):
+def run_pair(N, ns, steps, precision="fp32"):
     mem = members(ns, N)
-    ens = dg.Solver(N).upload_ensemble([m[0] for m in mem], [m[1] for m in mem], [m[2] for m in mem])
+    ens = dg.Solver(N, precision=precision).upload_ensemble([m[0] for m in mem], [m[1] for m in mem],
+                                                            [m[2] for m in mem])
     off = ens.ensemble_layout()
-    singles = [dg.Solver(N).upload(*m[0], eps=m[1]) for m in mem]
+    singles = [dg.Solver(N, precision=precision).upload(*m[0], eps=m[1]) for m in mem]
     u0 = [initial(s, i) for i, s in enumerate(singles)]
     u = torch.cat([s.to_device(u) for s, u in zip(singles, u0)], dim=1).contiguous()
     res = torch.zeros_like(u)
@@ -57,6 +60,35 @@ def test_ensemble_matches_separate_runs(steps):
     assert ens.ensemble_graph_used()
     best, eb, ms = ens.ensemble_tuning()
     assert best in eb and max(ms) > 0
+
+
+@pytest.mark.parametrize("steps", [3, 2])
+@pytest.mark.parametrize("precision,N", [("bf16x3", 3), ("fp16x3", 4), ("fp16x3", 5)])
+def test_tc_ensemble_matches_separate_runs(precision, N, steps):
+    # the tensor-core form in one persistent launch against each mesh advanced
+    # alone by per-stage tensor-core launches (FP16: the per-tile flux scale
+    # differs where a tile spans two meshes, within the split's error)
+    ens, off, u, singles, outs, u0, mem = run_pair(N, [2, 4, 3], steps, precision)
+    for i, s in enumerate(singles):
+        got = u[:, off[i]:off[i + 1]]
+        err = float((got - outs[i]).norm() / outs[i].norm())
+        print(f"{precision} N={N} steps={steps} member {i}: rel diff {err:.2e}")
+        assert err < 1e-6, (i, err)
+    assert ens.ensemble_graph_used()
+    best, eb, ms = ens.ensemble_tuning()
+    assert best == 20 and eb[0] == 20 and ms[0] > 0 and max(eb[1:]) == 0
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 2e-4), ("fp16x3", 1e-5)])
+def test_tc_ensemble_member_matches_oracle(precision, tol):
+    N, steps = 3, 2
+    ens, off, u, singles, outs, u0, mem = run_pair(N, [3, 2], steps, precision)
+    for i in range(2):
+        (VX, VY, VZ, EToV), eps, dt = mem[i]
+        m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps.astype(np.float64))
+        ref, _ = m.lserk(u0[i], dt, steps)
+        got = u[:, off[i]:off[i + 1], :m.Np].double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
 
 
 def test_ensemble_member_matches_oracle():

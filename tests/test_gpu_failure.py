@@ -5,8 +5,9 @@ the kernels give up on their bounded waits, set the device flag and return;
 dg_sync then reports DG_ERR_TIMEOUT, and with the default limit restored the
 same context reproduces an undisturbed run bit for bit. Covered: the
 tensor-core stage with resident operators (N=3), the one with operators
-streamed through shared memory (N=6), and the persistent ensemble launch with
-its grid barrier (replayed from a CUDA graph before and after).
+streamed through shared memory (N=6), and the persistent ensemble launches
+(FP32 and tensor-core forms) with their grid barrier (replayed from a CUDA
+graph before and after).
 """
 import numpy as np
 import pytest
@@ -48,15 +49,15 @@ def test_tensor_core_wait_timeout_reports_and_recovers(N, precision):
     assert np.array_equal(s.from_device(u), ref)
 
 
-def test_ensemble_grid_barrier_timeout_reports_and_recovers():
-    N = 2
+@pytest.mark.parametrize("N,precision", [(2, "fp32"), (3, "fp16x3")])
+def test_ensemble_grid_barrier_timeout_reports_and_recovers(N, precision):
     meshes, eps, dts = [], [], []
     for i, n in enumerate((2, 3)):
         VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=10 + i)
         meshes.append((VX, VY, VZ, EToV))
         eps.append(W.element_eps(EToV.shape[0], seed=100 + i))
         dts.append(0.5 / n / N ** 2)
-    ens = dg.Solver(N).upload_ensemble(meshes, eps, dts)
+    ens = dg.Solver(N, precision=precision).upload_ensemble(meshes, eps, dts)
     off = ens.ensemble_layout()
     x, y, z = ens.node_coords()
     u0 = W.gaussian_pulse(x, y, z, seed=7)
