@@ -427,7 +427,7 @@ def run_ensemble(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     N = 4
-    ns = W.ensemble_sizes(64, seed=3)
+    ns = W.ensemble_sizes(args.ens_meshes, seed=3)
     meshes, epss, dts = [], [], []
     for i, n in enumerate(ns):
         VX, VY, VZ, EToV = W.kuhn_cube(int(n), jitter=0.1, seed=10 + i)
@@ -475,7 +475,7 @@ def run_ensemble(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 1,
             "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "ensemble of 64 jittered cube meshes, n^3x6 with n in {8..20}, N=4, "
+            "config": {"workload": f"ensemble of {len(meshes)} jittered cube meshes, n^3x6 with n in {{8..20}}, N=4, "
                                    "eps U[1,4] per element, Gaussian pulse, LSERK4 with per-mesh dt",
                        "meshes": len(meshes), "K_total": Ktot, "dof": dof},
             "persistent_graph": {"gdof_s": value, "ms_per_step": ms / steps, "graph_replay": graph,
@@ -568,6 +568,7 @@ def main():
     ap.add_argument("--workload", choices=["cavity", "precision", "ensemble", "adjoint"], default="cavity",
                     help="cavity: 24^3 N=5 LSERK4 (headline); precision: split vs FP32 error and speed; "
                          "ensemble: 64 meshes in one persistent launch; adjoint: gradient cost and check")
+    ap.add_argument("--ens-meshes", type=int, default=64, help="meshes in the ensemble workload")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the stage kernel (from a capture), if known")
     args = ap.parse_args()

@@ -92,8 +92,10 @@ def test_lserk_step_parity(N):
     assert rel_l2(s.from_device(ud), ref4) < TOL_FP32
 
 
-def test_energy_matches_oracle():
-    s, m = setup_pair(4, 3)
+@pytest.mark.parametrize("N,n", [(1, 3), (4, 3), (5, 3), (7, 2)])
+def test_energy_matches_oracle(N, n):
+    # tiles of 256 / (Np_pad / 4) field rows; these sizes leave a ragged last tile
+    s, m = setup_pair(N, n)
     u = random_fields(m.shape, 9)
     E = s.energy(s.to_device(u))
     Eo = m.energy(u)
