@@ -62,10 +62,11 @@ def bytes_per_element(N: int, Npad: int) -> float:
     return (4 * 4 + 3) / 5 * 6 * Npad * 4 + 64 + 64 + 32
 
 
-# DRAM bytes per launch of the dominant stage kernel from one ncu capture of the
-# default workload (profiles/k_stage_tc_fp16x3_n5_24cube.md); None where the
-# kernel changed since its counters were taken or none were taken.
-NCU_TRAFFIC = {("fp32", 5, 24): 241.824256e6 + 174.203648e6}
+# DRAM bytes (read + write) per launch of the stage kernel, the mean over the
+# five stages of one step, from ncu captures (profiles/k_stage_tc_fp16x3_n5_24cube.md,
+# k_stage_simt_fp32_n5_24cube.md, k_stage_tc_streamed_fp16x3_n7_16cube.md); keyed by
+# (precision, N, hexahedra per edge); absent where no capture of the current kernel exists.
+NCU_TRAFFIC = {("fp16x3", 5, 24): 387.630e6, ("fp32", 5, 24): 391.294e6, ("fp16x3", 7, 16): 223.448e6}
 
 
 def measured_peaks():
