@@ -79,6 +79,17 @@ def test_tc_ensemble_matches_separate_runs(precision, N, steps):
     assert best == 20 and eb[0] == 20 and ms[0] > 0 and max(eb[1:]) == 0
 
 
+def test_split_precision_ensemble_above_n5_uses_fp32_form():
+    # the persistent tensor-core form covers N <= 5; at N = 6 a split-precision
+    # context advances the ensemble with the FP32 form (tuned elements per block)
+    ens, off, u, singles, outs, u0, mem = run_pair(6, [2, 2], 2, "fp16x3")
+    for i, s in enumerate(singles):
+        err = float((u[:, off[i]:off[i + 1]] - outs[i]).norm() / outs[i].norm())
+        assert err < 1e-5, (i, err)
+    best, eb, ms = ens.ensemble_tuning()
+    assert best in eb and best != 20 and min(eb) > 0
+
+
 @pytest.mark.parametrize("precision,tol", [("bf16x3", 2e-4), ("fp16x3", 1e-5)])
 def test_tc_ensemble_member_matches_oracle(precision, tol):
     N, steps = 3, 2
