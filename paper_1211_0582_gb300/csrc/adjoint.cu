@@ -60,7 +60,8 @@ struct AdjCfg {
   static constexpr int EB2 = 80 / D::NQ > 0 ? 80 / D::NQ : 1; // elements per volume block (measured best)
   static constexpr int NT2 = (EB2 * D::NQ + 31) / 32 * 32;
   static constexpr size_t SMEM1 = size_t(6) * EB1 * D::NPP * 4;
-  static constexpr size_t SMEM2 = (size_t(6) * EB2 * D::NPP * 3 + EB2) * 4 + ((200 * D::NFP + 15) / 16) * 16;
+  static constexpr size_t SMEM2 = size_t(EB2) * 4 * 64 + (size_t(6) * EB2 * D::NPP * 3 + EB2) * 4 +
+                                  ((200 * D::NFP + 15) / 16) * 16;
 };
 
 __device__ __forceinline__ void cross3(const float *a, const float *b, float *c) {
@@ -75,14 +76,15 @@ __device__ __forceinline__ void cross3(const float *a, const float *b, float *c)
 // trace (ep, hp). With flux_E = (Zp/Zs) n x dH - (alpha/Zs) n x n x dE and
 // flux_H = -(Yp/Ys) n x dE - (alpha/Ys) n x n x dH, dq = q+ - q-, and
 // (n x .)^T = -(n x .), (n x n x .)^T = n x n x .
-__device__ __forceinline__ void flux_transpose(const float *n, const float *g, float Zm, float Zp, float Ym, float Yp,
-                                               float alpha, float *ep, float *hp) {
+// The face's zs = 1/(Zm+Zp) and ys = 1/(Ym+Yp) are given (they depend only on
+// the face, so they are formed once per face, not per face node).
+__device__ __forceinline__ void flux_transpose_w(const float *n, const float *g, float Zp, float Yp, float zs,
+                                                 float ys, float alpha, float *ep, float *hp) {
   float nE[3], nH[3], nnE[3], nnH[3];
   cross3(n, g, nE);
   cross3(n, g + 3, nH);
   cross3(n, nE, nnE);
   cross3(n, nH, nnH);
-  const float zs = 1.f / (Zm + Zp), ys = 1.f / (Ym + Yp);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     hp[c] = -(Zp * zs) * nE[c] - (alpha * ys) * nnH[c];
@@ -90,14 +92,14 @@ __device__ __forceinline__ void flux_transpose(const float *n, const float *g, f
   }
 }
 
-// <g, d flux / d(weights)>: returns the contractions with the partial
-// derivatives in Zm, Zp, Ym, Yp of the (unscaled) flux at one face node.
-__device__ __forceinline__ void flux_weight_partials(const float *n, const float *qm, const float *qp, float Zm,
-                                                     float Zp, float Ym, float Yp, float alpha, const float *g,
-                                                     float &sZm, float &sZp, float &sYm, float &sYp) {
-  float f[6];
-  maxwell_flux(make_float4(n[0], n[1], n[2], 1.f), qm, qp, Zm, Zp, Ym, Yp, alpha, f);
-  float dE[3], dH[3], nxdE[3], nxdH[3];
+// <g, d flux / d(weights)>: the contractions of the face data g with the
+// partial derivatives in Zm, Zp, Ym, Yp of the (unscaled) flux at one face
+// node, with the face's zs = 1/(Zm+Zp), ys = 1/(Ym+Yp) given: the flux
+// (weights zs and -ys) and n x dE, n x dH are formed once and shared.
+__device__ __forceinline__ void flux_weight_partials_w(const float *n, const float *qm, const float *qp, float Zp,
+                                                       float Yp, float zs, float ys, float alpha, const float *g,
+                                                       float &sZm, float &sZp, float &sYm, float &sYp) {
+  float dE[3], dH[3], nxdE[3], nxdH[3], v[3], f[6];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     dE[c] = qp[c] - qm[c];
@@ -105,7 +107,17 @@ __device__ __forceinline__ void flux_weight_partials(const float *n, const float
   }
   cross3(n, dE, nxdE);
   cross3(n, dH, nxdH);
-  const float zs = 1.f / (Zm + Zp), ys = 1.f / (Ym + Yp);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c] = Zp * dH[c] - alpha * nxdE[c];
+  cross3(n, v, f);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c] = Yp * dE[c] + alpha * nxdH[c];
+  cross3(n, v, f + 3);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    f[c] *= zs;
+    f[c + 3] *= -ys;
+  }
   sZm = sZp = sYm = sYp = 0.f;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -190,7 +202,10 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
   using C = AdjCfg<N>;
   constexpr int NP = D::NP, NPP = D::NPP, NQ = D::NQ, NFF = D::NFF, NFP = D::NFP, EB = C::EB2, NT = C::NT2;
   extern __shared__ float4 smem4[];
-  float *s_v = reinterpret_cast<float *>(smem4); // W lr   [6][EB][NPP]
+  // per face of the block's elements: {n, 1/(Z-+Z+)}, {Z-, Z+, Y-, Y+},
+  // {1/(Y-+Y+), dZ-/deps, dY-/deps, connection kind}, {neighbour element, wall}
+  float4 *s_face = smem4;                                 // [EB * 4][4]
+  float *s_v = reinterpret_cast<float *>(smem4 + EB * 16); // W lr   [6][EB][NPP]
   float *s_w = s_v + 6 * EB * NPP;               // surface contributions [6][EB][NPP]
   float *s_us = s_w + 6 * EB * NPP;              // stage state u_s of the block's elements [6][EB][NPP]
   float *s_gr = s_us + 6 * EB * NPP;             // gradient partial per element [EB]
@@ -203,6 +218,22 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
   for (int i = tid; i < NFF + 2 * kConnKinds * NFP; i += NT)
     s_fm[i] = i < NFF ? a.fmask[i] : i < NFF + kConnKinds * NFP ? a.nbrtab[i - NFF] : a.nbrface[i - NFF - kConnKinds * NFP];
   for (int i = tid; i < EB; i += NT) s_gr[i] = 0.f;
+  for (int t = tid; t < EB * 4; t += NT) {
+    const int e = t >> 2, f = t & 3;
+    const int64_t k = k0 + e;
+    if (k >= a.K) continue;
+    const int2 cn = __ldg(a.fconn + k * 4 + f);
+    const float4 nf = __ldg(a.fgeo + k * 4 + f);
+    const float Zk = __ldg(a.geo + k * G_STRIDE + G_Z), Yk = __ldg(a.geo + k * G_STRIDE + G_Y);
+    const bool wall = cn.y == kBoundaryConn;
+    const int64_t k2 = wall ? k : cn.x;
+    const float Z2 = wall ? Zk : __ldg(a.geo + k2 * G_STRIDE + G_Z), Y2 = wall ? Yk : __ldg(a.geo + k2 * G_STRIDE + G_Y);
+    const float ek = 1.f / __ldg(a.geo + k * G_STRIDE + G_IEPS);
+    s_face[t * 4 + 0] = make_float4(nf.x, nf.y, nf.z, 1.f / (Zk + Z2));
+    s_face[t * 4 + 1] = make_float4(Zk, Z2, Yk, Y2);
+    s_face[t * 4 + 2] = make_float4(1.f / (Yk + Y2), -Zk / (2.f * ek), Yk / (2.f * ek), __int_as_float(cn.y));
+    s_face[t * 4 + 3] = make_float4(__int_as_float(int(k2)), __int_as_float(wall ? 1 : 0), 0.f, 0.f);
+  }
   for (int idx = tid; idx < 6 * EB * NQ; idx += NT) {
     const int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
     const int e = rem / NQ, q = rem - e * NQ;
@@ -247,24 +278,24 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
     const int e = it / NFF, fm = it - e * NFF, f = fm / NFP, m = fm - f * NFP;
     const int64_t k = k0 + e;
     if (k >= a.K) continue;
-    const int2 cn = __ldg(a.fconn + k * 4 + f);
-    const float4 nf = __ldg(a.fgeo + k * 4 + f);
-    const float n[3] = {nf.x, nf.y, nf.z};
-    const float Zk = __ldg(a.geo + k * G_STRIDE + G_Z), Yk = __ldg(a.geo + k * G_STRIDE + G_Y);
-    const bool wall = cn.y == kBoundaryConn;
-    const int64_t k2 = wall ? k : cn.x;
-    const float Z2 = wall ? Zk : __ldg(a.geo + k2 * G_STRIDE + G_Z), Y2 = wall ? Yk : __ldg(a.geo + k2 * G_STRIDE + G_Y);
+    const float4 *fr = s_face + (e * 4 + f) * 4;
+    const float4 r0 = fr[0], r1 = fr[1], r2 = fr[2], r3 = fr[3];
+    const float n[3] = {r0.x, r0.y, r0.z};
+    const float zs = r0.w, Zk = r1.x, Z2 = r1.y, Yk = r1.z, Y2 = r1.w, ys = r2.x;
+    const int cny = __float_as_int(r2.w);
+    const int64_t k2 = __float_as_int(r3.x);
+    const bool wall = __float_as_int(r3.y) != 0;
     float gk[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) gk[c] = a.g[(c * a.K + k) * NFF + fm];
     float ep[3], hp[3], acc[6];
-    flux_transpose(n, gk, Zk, Z2, Yk, Y2, a.alpha, ep, hp);
+    flux_transpose_w(n, gk, Z2, Y2, zs, ys, a.alpha, ep, hp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       acc[c] = -ep[c];      // interior side: the E and H Jacobians are the negatives of the exterior ones
       acc[c + 3] = -hp[c];
     }
-    const int fm2 = wall ? 0 : s_nf[cn.y * NFP + m] + (cn.y / 6 % 4) * NFP;
+    const int fm2 = wall ? 0 : s_nf[cny * NFP + m] + (cny / 6 % 4) * NFP;
     float g2[6];
     if (wall) {
       // exterior state E+ = -E-, H+ = H- folds back onto the interior node
@@ -279,7 +310,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
       for (int c = 0; c < 6; ++c) g2[c] = a.g[(c * a.K + k2) * NFF + fm2];
       const float n2[3] = {-n[0], -n[1], -n[2]};
       float ep2[3], hp2[3];
-      flux_transpose(n2, g2, Z2, Zk, Y2, Yk, a.alpha, ep2, hp2);
+      flux_transpose_w(n2, g2, Zk, Yk, zs, ys, a.alpha, ep2, hp2);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         acc[c] += ep2[c];
@@ -290,8 +321,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) atomicAdd(&s_w[(c * EB + e) * NPP + vm], acc[c]);
     if (GRAD) {
-      const float ek = 1.f / __ldg(a.geo + k * G_STRIDE + G_IEPS);
-      const float dZ = -Zk / (2.f * ek), dY = Yk / (2.f * ek);
+      const float dZ = r2.y, dY = r2.z;
       float qm[6], qp[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) qm[c] = s_us[(c * EB + e) * NPP + vm];
@@ -302,7 +332,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
           qp[c + 3] = qm[c + 3];
         }
       } else {
-        const int vn = s_nb[cn.y * NFP + m];
+        const int vn = s_nb[cny * NFP + m];
         const int64_t e2 = k2 - k0; // neighbours inside the block come from shared memory
         if (e2 >= 0 && e2 < EB) {
 #pragma unroll
@@ -313,14 +343,14 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
         }
       }
       float sZm, sZp, sYm, sYp;
-      flux_weight_partials(n, qm, qp, Zk, Z2, Yk, Y2, a.alpha, gk, sZm, sZp, sYm, sYp);
+      flux_weight_partials_w(n, qm, qp, Z2, Y2, zs, ys, a.alpha, gk, sZm, sZp, sYm, sYp);
       float contrib = sZm * dZ + sYm * dY;
       if (wall) {
         contrib += sZp * dZ + sYp * dY; // the mirrored exterior carries the same weights
       } else {
         const float n2[3] = {-n[0], -n[1], -n[2]};
         float tZm, tZp, tYm, tYp;
-        flux_weight_partials(n2, qp, qm, Z2, Zk, Y2, Yk, a.alpha, g2, tZm, tZp, tYm, tYp);
+        flux_weight_partials_w(n2, qp, qm, Zk, Yk, zs, ys, a.alpha, g2, tZm, tZp, tYm, tYp);
         contrib += tZp * dZ + tYp * dY;
       }
       atomicAdd(&s_gr[e], contrib);

@@ -23,30 +23,9 @@ __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpre
 // material jumps):
 //   flux_E = n x (Z+ dH - alpha n x dE) / (Z- + Z+)
 //   flux_H = -n x (Y+ dE + alpha n x dH) / (Y- + Y+)
-// qm/qp: Ex Ey Ez Hx Hy Hz on the interior/exterior side; out: 6 values.
-__device__ __forceinline__ void maxwell_flux(float4 nf, const float *qm, const float *qp, float Zm, float Zp,
-                                             float Ym, float Yp, float alpha, float *out) {
-  const float nx = nf.x, ny = nf.y, nz = nf.z, fs = nf.w;
-  float dEx = qp[0] - qm[0], dEy = qp[1] - qm[1], dEz = qp[2] - qm[2];
-  float dHx = qp[3] - qm[3], dHy = qp[4] - qm[4], dHz = qp[5] - qm[5];
-  // n x dE, n x dH
-  float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
-  float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
-  float wE = fs / (Zm + Zp), wH = -fs / (Ym + Yp);
-  float vx = Zp * dHx - alpha * cEx, vy = Zp * dHy - alpha * cEy, vz = Zp * dHz - alpha * cEz;
-  out[0] = wE * (ny * vz - nz * vy);
-  out[1] = wE * (nz * vx - nx * vz);
-  out[2] = wE * (nx * vy - ny * vx);
-  vx = Yp * dEx + alpha * cHx;
-  vy = Yp * dEy + alpha * cHy;
-  vz = Yp * dEz + alpha * cHz;
-  out[3] = wH * (ny * vz - nz * vy);
-  out[4] = wH * (nz * vx - nx * vz);
-  out[5] = wH * (nx * vy - ny * vx);
-}
-
-// The same flux with the face's precomputed weights
-// w = {Fscale/(Z- + Z+), -Fscale/(Y- + Y+), Z+, Y+}.
+// qm/qp: Ex Ey Ez Hx Hy Hz on the interior/exterior side; out: 6 values;
+// nf: the face normal; w: the face's precomputed weights
+// {Fscale/(Z- + Z+), -Fscale/(Y- + Y+), Z+, Y+}.
 __device__ __forceinline__ void maxwell_flux_w(float4 nf, const float *qm, const float *qp, float4 w, float alpha,
                                                float *out) {
   const float nx = nf.x, ny = nf.y, nz = nf.z;
