@@ -44,6 +44,31 @@ using namespace tcc;
 
 constexpr int kThreads = 512;
 constexpr int kTileElems = 20; // 4 TMEM lane quarters x 5 elements
+
+// Element ranges of the tiles: whole rounds of full tiles (kTileElems elements,
+// `grid` tiles per round), then the remaining elements in tiles of `small`
+// elements, sized so that the last round spreads over the whole grid instead
+// of leaving most CTAs idle behind a few full tiles.
+struct TileMap {
+  int nfull, small, ntiles;
+  __host__ __device__ int64_t start(int t) const {
+    return t < nfull ? int64_t(t) * kTileElems : int64_t(nfull) * kTileElems + int64_t(t - nfull) * small;
+  }
+  __host__ __device__ int size(int t, int64_t K) const {
+    const int64_t k0 = start(t), n = t < nfull ? kTileElems : small;
+    return int(K - k0 < n ? K - k0 : n);
+  }
+};
+
+TileMap make_tiles(int64_t K, int grid) {
+  const int64_t nfull = K / kTileElems / grid * grid;
+  const int64_t rest = K - nfull * kTileElems;
+  int64_t small = (rest + grid - 1) / grid;
+  if (small < 1) small = 1;
+  if (small > kTileElems) small = kTileElems;
+  const int64_t nsmall = (rest + small - 1) / small;
+  return TileMap{int(nfull), int(small), int(nfull + nsmall)};
+}
 constexpr int kMaxTcOrder = 7; // N <= 5 here, N = 6, 7 in tc_stage_streamed.cu
 
 template <int N>
@@ -124,7 +149,7 @@ struct EnsLaunch {
 // gathers through L2 (another SM's L1 may hold a copy from two stages ago).
 template <int N, int MODE, bool BF16, bool ENS>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_stage_tc(StageArgs a, const uint4 *__restrict__ ops, int ntiles, int *err_flag, EnsLaunch ens) {
+    k_stage_tc(StageArgs a, const uint4 *__restrict__ ops, TileMap tm, int *err_flag, EnsLaunch ens) {
   using T = TC<N>;
   constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, FS = T::FS;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -160,8 +185,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   // fields of tile t into the A1 bytes, its face and element data into a
   // slot (one thread; completes on barU)
   auto stage_tile = [&](int t, int slot) {
-    const int64_t kb = int64_t(t) * kTileElems;
-    const uint32_t nb = uint32_t(a.K - kb < kTileElems ? a.K - kb : kTileElems);
+    const int64_t kb = tm.start(t);
+    const uint32_t nb = uint32_t(tm.size(t, a.K));
     const uint32_t rb = nb * NPP * 4;
     uint8_t *fs = smem + T::OFF_FACE + slot * T::FSLOT;
     umma::mbar_arrive_expect_tx(barU, 6u * rb + nb * (64u + 64u + G_STRIDE * 4u + 32u));
@@ -249,13 +274,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       read_res = a.rk_a != 0.f;
     }
     // the stage's first tile (the following ones are staged one tile ahead)
-    if (stager && int(blockIdx.x) < ntiles) {
+    if (stager && int(blockIdx.x) < tm.ntiles) {
       if (ENS) umma::fence_proxy_async_global();
       stage_tile(blockIdx.x, int(phase));
     }
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const int64_t k0 = int64_t(tile) * kTileElems;
-      const int ne = int(a.K - k0 < kTileElems ? a.K - k0 : kTileElems);
+    for (int tile = blockIdx.x; tile < tm.ntiles; tile += gridDim.x) {
+      const int64_t k0 = tm.start(tile);
+      const int ne = tm.size(tile, a.K);
       const uint32_t rowbytes = uint32_t(ne * NPP * 4);
       const int slot = int(phase);
       const uint8_t *fslot = smem + T::OFF_FACE + slot * T::FSLOT;
@@ -413,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // once GEMM1 has read A1, the next tile's fields and face data are staged
       if (stager) {
         ok = umma::mbar_wait_bounded(bar1, phase, wlim);
-        const bool more = ok && tile + int(gridDim.x) < ntiles;
+        const bool more = ok && tile + int(gridDim.x) < tm.ntiles;
         if (more) stage_tile(tile + gridDim.x, slot ^ 1);
         *s_staged = more ? 1 : 0;
       }
@@ -651,9 +676,9 @@ cudaError_t launch_tc_kernel(const StageArgs &a, const TcState &st, int *flag, c
   auto kern = k_stage_tc<N, MODE, BF16, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
   if (e != cudaSuccess) return e;
-  const int ntiles = int((a.K + kTileElems - 1) / kTileElems);
-  const int grid = ntiles < st.sms ? ntiles : st.sms;
-  kern<<<grid, kThreads, T::SMEM, s>>>(a, reinterpret_cast<const uint4 *>(st.d_ops), ntiles, flag, EnsLaunch{});
+  const TileMap tm = make_tiles(a.K, st.sms);
+  const int grid = tm.ntiles < st.sms ? tm.ntiles : st.sms;
+  kern<<<grid, kThreads, T::SMEM, s>>>(a, reinterpret_cast<const uint4 *>(st.d_ops), tm, flag, EnsLaunch{});
   return cudaGetLastError();
 }
 
@@ -665,8 +690,8 @@ cudaError_t launch_tc_ens_kernel(const StageArgs &a, const TcState &st, const En
   auto kern = k_stage_tc<N, MODE_LSERK, BF16, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
   if (e != cudaSuccess) return e;
-  const int ntiles = int((a.K + kTileElems - 1) / kTileElems);
-  const int grid = ntiles < st.sms ? ntiles : st.sms;
+  const TileMap tm = make_tiles(a.K, st.sms);
+  const int grid = tm.ntiles < st.sms ? tm.ntiles : st.sms;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(kThreads);
@@ -677,7 +702,7 @@ cudaError_t launch_tc_ens_kernel(const StageArgs &a, const TcState &st, const En
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, a, reinterpret_cast<const uint4 *>(st.d_ops), ntiles, flag, ens);
+  return cudaLaunchKernelEx(&cfg, kern, a, reinterpret_cast<const uint4 *>(st.d_ops), tm, flag, ens);
 }
 
 template <int N>
