@@ -175,12 +175,15 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   const int cr1 = compact_row(r1);
   const int e1 = cr1 >= 0 ? cr1 / 6 : 0, f1 = cr1 >= 0 ? cr1 % 6 : 0;
   const int kq1 = 4 * ((lane >> 3) & 1) + 8 * (lane >> 4);
-  // flux: blocks of 4 elements x 8 face-node columns of A2, lane -> (element, column)
-  constexpr int KGF = T::K2 / 8;
+  // flux: blocks of 4 elements x 16 face-node columns of A2, lane -> (element,
+  // pair of adjacent columns); Nfp is even at N = 6, 7, so a pair never
+  // straddles two faces
+  static_assert(NFP % 2 == 0, "column pairs need an even number of nodes per face");
+  constexpr int KGF = T::K2 / 16;
   constexpr int NBLK = (kTileS / 4) * KGF;
   constexpr int R2 = (NBLK + kFluxWarps - 1) / kFluxWarps;
-  constexpr int BATCH = 2; // neighbour gathers in flight per thread
-  const int eo = lane >> 3, kk8 = lane & 7;
+  constexpr int BATCH = 1; // blocks whose neighbour gathers are in flight together
+  const int eo = lane >> 3, kp = lane & 7;
   // epilogue: one thread per (element, field) row of the accumulators; a
   // warp reads the TMEM lane quarter warp % 4, quarter 3 without the MMA warp
   // has three warps
@@ -311,35 +314,42 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     }
 
     // ---- 4. neighbour traces and upwind flux (overlaps GEMM1), in registers
-    float fl[R2][6];
+    float fl[R2][2][6];
     uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
     if (warp < kFluxWarps) {
 #pragma unroll
       for (int s0 = 0; s0 < R2; s0 += BATCH) {
-        float qp[BATCH][6];
-        int lidx[BATCH];
+        float qp[BATCH][2][6];
+        int lidx[BATCH][2];
 #pragma unroll
         for (int b = 0; b < BATCH; ++b) {
           const int s = s0 + b;
           const int blk = warp + kFluxWarps * s;
-          const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk8;
-          lidx[b] = -1;
+          const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) qp[b][c] = 0.f;
+          for (int h = 0; h < 2; ++h) {
+            lidx[b][h] = -1;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) qp[b][h][c] = 0.f;
+          }
           if (s < R2 && blk < NBLK && fm < NFF && e < ne) {
             const int f = fm / NFP, mm = fm - f * NFP;
             const float4 r2 = s_face[(e * 4 + f) * 3 + 2];
             const int conn = __float_as_int(r2.y);
             if (conn != kBoundaryConn) {
               const int k2 = __float_as_int(r2.x);
-              const int node = s_nb[conn * NFP + mm];
               const int64_t el = int64_t(k2) - k0;
-              if (el >= 0 && el < ne) {
-                lidx[b] = int(el) * NPP + node;
-              } else {
-                const float *up = a.u + int64_t(k2) * NPP + node;
+              const bool local = el >= 0 && el < ne;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) qp[b][c] = __ldg(up + c * KN);
+              for (int h = 0; h < 2; ++h) {
+                const int node = s_nb[conn * NFP + mm + h];
+                if (local) {
+                  lidx[b][h] = int(el) * NPP + node;
+                } else {
+                  const float *up = a.u + int64_t(k2) * NPP + node;
+#pragma unroll
+                  for (int c = 0; c < 6; ++c) qp[b][h][c] = __ldg(up + c * KN);
+                }
               }
             }
           }
@@ -349,43 +359,38 @@ __global__ void __launch_bounds__(kThreadsS, 1)
           const int s = s0 + b;
           if (s >= R2) break;
           const int blk = warp + kFluxWarps * s;
-          const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk8;
+          const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) fl[s][c] = 0.f;
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fl[s][h][c] = 0.f;
           if (blk < NBLK && fm < NFF && e < ne) {
             const int f = fm / NFP;
             const float4 g0 = s_face[(e * 4 + f) * 3 + 0], w1 = s_face[(e * 4 + f) * 3 + 1];
             const bool wall = __float_as_int(s_face[(e * 4 + f) * 3 + 2].y) == kBoundaryConn;
-            const int vm = s_fm[fm];
-            float qm[6], q[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
+            for (int h = 0; h < 2; ++h) {
+              const int vm = s_fm[fm + h];
+              float qm[6], q[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) q[c] = lidx[b] >= 0 ? s_u[c * FS + lidx[b]] : qp[b][c];
-            if (wall) {
+              for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                q[c] = -qm[c];
-                q[c + 3] = qm[c + 3];
+              for (int c = 0; c < 6; ++c) q[c] = lidx[b][h] >= 0 ? s_u[c * FS + lidx[b][h]] : qp[b][h][c];
+              if (wall) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  q[c] = -qm[c];
+                  q[c + 3] = qm[c + 3];
+                }
               }
+              maxwell_flux_w(g0, qm, q, w1, a.alpha, fl[s][h]);
             }
-            const float nx = g0.x, ny = g0.y, nz = g0.z;
-            const float dEx = q[0] - qm[0], dEy = q[1] - qm[1], dEz = q[2] - qm[2];
-            const float dHx = q[3] - qm[3], dHy = q[4] - qm[4], dHz = q[5] - qm[5];
-            const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
-            const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
-            float vx = w1.z * dHx - a.alpha * cEx, vy = w1.z * dHy - a.alpha * cEy, vz = w1.z * dHz - a.alpha * cEz;
-            fl[s][0] = w1.x * (ny * vz - nz * vy);
-            fl[s][1] = w1.x * (nz * vx - nx * vz);
-            fl[s][2] = w1.x * (nx * vy - ny * vx);
-            vx = w1.w * dEx + a.alpha * cHx, vy = w1.w * dEy + a.alpha * cHy, vz = w1.w * dEz + a.alpha * cHz;
-            fl[s][3] = w1.y * (ny * vz - nz * vy);
-            fl[s][4] = w1.y * (nz * vx - nx * vz);
-            fl[s][5] = w1.y * (nx * vy - ny * vx);
           }
           if constexpr (!BF16) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][c])));
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][h][c])));
           }
         }
       }
@@ -416,19 +421,18 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 #pragma unroll
       for (int s = 0; s < R2; ++s) {
         const int blk = warp + kFluxWarps * s;
-        const int e = 4 * (blk / KGF) + eo, fm = 8 * (blk % KGF) + kk8;
+        const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
         if (blk < NBLK) {
-          const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5)); // the element's six rows share a quarter
+          // the element's six rows share a quarter; a column pair is one
+          // 32-bit word of a core-matrix row
+          const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
 #pragma unroll
-          for (int c = 0; c < 6; c += 2) {
+          for (int c = 0; c < 6; ++c) {
             uint32_t hi, lo;
-            split2<BF16>(fl[s][c] * sc2[c], fl[s][c + 1] * sc2[c + 1], hi, lo);
-            const uint32_t o0 = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
-            const uint32_t o1 = umma::kmajor_offset(r0 + uint32_t(c + 1), uint32_t(fm), uint32_t(T::K2));
-            *reinterpret_cast<uint16_t *>(smem + o0) = uint16_t(hi);
-            *reinterpret_cast<uint16_t *>(smem + o1) = uint16_t(hi >> 16);
-            *reinterpret_cast<uint16_t *>(smem + T::A2B + o0) = uint16_t(lo);
-            *reinterpret_cast<uint16_t *>(smem + T::A2B + o1) = uint16_t(lo >> 16);
+            split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
+            const uint32_t o = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
+            *reinterpret_cast<uint32_t *>(smem + o) = hi;
+            *reinterpret_cast<uint32_t *>(smem + T::A2B + o) = lo;
           }
         }
       }
