@@ -23,6 +23,10 @@
 //
 // Orders N = 1..5 (the operators of N = 6, 7 do not fit in shared memory next
 // to a tile; those orders stream them, see tc_stage_streamed.cu).
+//
+// The same kernel also runs many LSERK stages in one cooperative launch
+// (ensembles of meshes): a grid barrier separates the stages, since a stage
+// reads the neighbours' states that the previous stage wrote.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
