@@ -131,6 +131,23 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_max_ms(ms_local: float, dist, device) -> float:
+    """The job's time: the maximum over the replicas of each one's measured
+    time (a single process returns its own)."""
+    if dist is None:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gdof_s(world: int, dof: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: every replica advances its own copy of the
+    workload, so the job's units are world x 5 stages x DOF x steps."""
+    return world * STAGES * dof * steps / (ms * 1e-3) / 1e9
+
+
 def make_workload(N: int, n: int):
     import workloads as W
     VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
@@ -249,13 +266,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if clocks else None
-    if dist:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * STAGES * dof * args.steps / (ms * 1e-3) / 1e9
+    ms = replica_max_ms(ev0.elapsed_time(ev1), dist, device)
+    value = job_gdof_s(world, dof, args.steps, ms)
     launches = STAGES * args.steps
     launch_ms = ms / launches
 
@@ -299,13 +312,9 @@ def run_ours(args):
         streams[0].wait_stream(streams[j])
     e1.record(streams[0])
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replica_max_ms(e0.elapsed_time(e1), dist, device)
     field_bytes = 6 * K * Npad * 4
-    e2e_value = world * STAGES * dof * e2e_steps / (e2e_ms * 1e-3) / 1e9
+    e2e_value = job_gdof_s(world, dof, e2e_steps, e2e_ms)
 
     # ---- roofline of the dominant kernel (the fused stage kernel)
     peaks, peak_kind = measured_peaks()
