@@ -572,7 +572,7 @@ def main():
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--n", type=int, default=24, help="hexahedra per cube edge")
     ap.add_argument("--e2e-steps", type=int, default=50)
-    ap.add_argument("--e2e-streams", type=int, default=3, help="contexts/streams the end-to-end steps alternate over")
+    ap.add_argument("--e2e-streams", type=int, default=4, help="contexts/streams the end-to-end steps alternate over")
     ap.add_argument("--cpu-sample", type=int, default=50000, help="elements in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["cavity", "precision", "ensemble", "adjoint"], default="cavity",

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT1) k_adj_lift(AdjArgs a) {
   const int tid = threadIdx.x;
   const int64_t k0 = int64_t(blockIdx.x) * EB;
   const int64_t KN = a.K * NPP;
+  pdl_launch_next_and_wait(); // reverse stage after reverse stage
   for (int idx = tid; idx < 6 * EB * NQ; idx += C::NT1) {
     const int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
     const int e = rem / NQ, q = rem - e * NQ;
@@ -234,6 +235,9 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
     s_face[t * 4 + 2] = make_float4(1.f / (Yk + Y2), -Zk / (2.f * ek), Yk / (2.f * ek), __int_as_float(cn.y));
     s_face[t * 4 + 3] = make_float4(__int_as_float(int(k2)), __int_as_float(wall ? 1 : 0), 0.f, 0.f);
   }
+  // the tables and face constants above are static: the previous kernel's
+  // results (lambda, face data, gradient) are read from here on
+  pdl_launch_next_and_wait();
   for (int idx = tid; idx < 6 * EB * NQ; idx += NT) {
     const int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
     const int e = rem / NQ, q = rem - e * NQ;
@@ -426,20 +430,19 @@ cudaError_t launch_adj_order(int which, const AdjArgs &a, cudaStream_t s) {
   if (which == 0) {
     e = cudaFuncSetAttribute(k_adj_lift<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM1));
     if (e != cudaSuccess) return e;
-    k_adj_lift<N><<<unsigned((a.K + C::EB1 - 1) / C::EB1), C::NT1, C::SMEM1, s>>>(a);
+    return launch_pdl(k_adj_lift<N>, dim3(unsigned((a.K + C::EB1 - 1) / C::EB1)), dim3(C::NT1), C::SMEM1, s, a);
   } else {
     const unsigned blocks = unsigned((a.K + C::EB2 - 1) / C::EB2);
     if (a.u_s) {
       e = cudaFuncSetAttribute(k_adj_vol<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
       if (e != cudaSuccess) return e;
-      k_adj_vol<N, true><<<blocks, C::NT2, C::SMEM2, s>>>(a);
+      return launch_pdl(k_adj_vol<N, true>, dim3(blocks), dim3(C::NT2), C::SMEM2, s, a);
     } else {
       e = cudaFuncSetAttribute(k_adj_vol<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
       if (e != cudaSuccess) return e;
-      k_adj_vol<N, false><<<blocks, C::NT2, C::SMEM2, s>>>(a);
+      return launch_pdl(k_adj_vol<N, false>, dim3(blocks), dim3(C::NT2), C::SMEM2, s, a);
     }
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_adj(int N, int which, const AdjArgs &a, cudaStream_t s) {

@@ -78,6 +78,38 @@ extern const double kLserkA[5];
 extern const double kLserkB[5];
 extern const double kLserkC[5];
 
+// Programmatic dependent launch for kernels launched back to back on one
+// stream (the stages of a step). A kernel waits for the previous kernel to
+// complete, with its writes visible, before it reads or writes any data that
+// kernel touches (pdl_wait, after its own setup), and lets the next kernel be
+// launched once each of its blocks has started its last piece of work
+// (pdl_launch_next), so that the next kernel's setup (shared-memory tables,
+// operators, tensor-memory allocation) runs on SMs that free up at the end
+// without holding SMs idle for long while other streams have work. Kernels
+// launched without the attribute are serialised as usual and both return at
+// once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next_and_wait() {
+  pdl_launch_next();
+  pdl_wait();
+}
+
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 } // namespace dgmx
 
 // Library context (opaque to callers).

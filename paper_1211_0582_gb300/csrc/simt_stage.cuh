@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(SimtCfg<N>::NT) k_stage_simt(StageArgs a) {
   extern __shared__ float4 smem4[];
   constexpr int EB = SimtCfg<N>::EB;
   const int64_t ntiles = (a.K + EB - 1) / EB;
+  pdl_wait(); // stage after stage: fields of the previous stage from here on
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (t + int64_t(gridDim.x) >= ntiles) pdl_launch_next(); // this block's last tile
     __syncthreads(); // shared memory of the previous tile is no longer read
     simt_stage_tile<N, MODE, EB, true>(a, t * EB, smem4);
   }
@@ -258,13 +260,9 @@ cudaError_t launch_simt_order(int mode, const StageArgs &a, cudaStream_t s) {
   }
   const int64_t ntiles = (a.K + Cfg::EB - 1) / Cfg::EB, cap = int64_t(per_sm) * sms;
   const unsigned blocks = unsigned(ntiles < cap ? ntiles : cap);
-  if (mode == MODE_RHS)
-    k_stage_simt<N, MODE_RHS><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
-  else if (mode == MODE_LSERK)
-    k_stage_simt<N, MODE_LSERK><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
-  else
-    k_stage_simt<N, MODE_LSERK_STORE><<<blocks, Cfg::NT, Cfg::SMEM, s>>>(a);
-  return cudaGetLastError();
+  if (mode == MODE_RHS) return launch_pdl(k_stage_simt<N, MODE_RHS>, dim3(blocks), dim3(Cfg::NT), Cfg::SMEM, s, a);
+  if (mode == MODE_LSERK) return launch_pdl(k_stage_simt<N, MODE_LSERK>, dim3(blocks), dim3(Cfg::NT), Cfg::SMEM, s, a);
+  return launch_pdl(k_stage_simt<N, MODE_LSERK_STORE>, dim3(blocks), dim3(Cfg::NT), Cfg::SMEM, s, a);
 }
 
 } // namespace dgmx

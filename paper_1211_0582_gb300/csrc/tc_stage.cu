@@ -222,6 +222,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
+  // stage after stage: the setup above may overlap the end of the previous
+  // stage, nothing it wrote is read before this point
+  if constexpr (!ENS) pdl_wait();
 
   // field split: warp w owns operand rows 8w..8w+7 of A1; lane -> (row, half of
   // a K group of 8), so one row's maximum is a reduction over 4 lanes and every
@@ -283,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       stage_tile(blockIdx.x, int(phase));
     }
     for (int tile = blockIdx.x; tile < tm.ntiles; tile += gridDim.x) {
+      if (!ENS && tile + int(gridDim.x) >= tm.ntiles) pdl_launch_next(); // this block's last tile
       const int64_t k0 = tm.start(tile);
       const int ne = tm.size(tile, a.K);
       const uint32_t rowbytes = uint32_t(ne * NPP * 4);
@@ -682,8 +686,8 @@ cudaError_t launch_tc_kernel(const StageArgs &a, const TcState &st, int *flag, c
   if (e != cudaSuccess) return e;
   const TileMap tm = make_tiles(a.K, st.sms);
   const int grid = tm.ntiles < st.sms ? tm.ntiles : st.sms;
-  kern<<<grid, kThreads, T::SMEM, s>>>(a, reinterpret_cast<const uint4 *>(st.d_ops), tm, flag, EnsLaunch{});
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(unsigned(grid)), dim3(kThreads), size_t(T::SMEM), s, a,
+                    reinterpret_cast<const uint4 *>(st.d_ops), tm, flag, EnsLaunch{});
 }
 
 // Cooperative launch of the multi-step form: one block per SM, all resident.

@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
+  // stage after stage: the setup above may overlap the end of the previous
+  // stage, nothing it wrote is read before this point
+  pdl_wait();
 
   // operator stream (issuer only): step j of the periodic slice sequence
   // goes to slot j % kSlots
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (tile + int(gridDim.x) >= ntiles) pdl_launch_next(); // this block's last tile
     const int64_t k0 = int64_t(tile) * kTileS;
     const int ne = int(a.K - k0 < kTileS ? a.K - k0 : kTileS);
     bool ok = true;
@@ -629,8 +633,8 @@ cudaError_t launch_streamed_kernel(const StageArgs &a, const TcState &st, int *f
   if (e != cudaSuccess) return e;
   const int ntiles = int((a.K + kTileS - 1) / kTileS);
   const int grid = ntiles < st.sms ? ntiles : st.sms;
-  kern<<<grid, kThreadsS, T::SMEM, s>>>(a, static_cast<const uint8_t *>(st.d_ops), ntiles, flag);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(unsigned(grid)), dim3(kThreadsS), size_t(T::SMEM), s, a,
+                    static_cast<const uint8_t *>(st.d_ops), ntiles, flag);
 }
 
 template <int N>
