@@ -60,8 +60,8 @@ typedef enum {
   DG_FP32 = 0,   /* FP32 arithmetic on the CUDA cores */
   DG_BF16X3 = 1, /* D and LIFT contractions on tensor cores, BF16 hi+lo split, FP32 accumulate */
   DG_FP16X3 = 2  /* same with FP16 hi+lo split, FP32 accumulate; power-of-two scaled per
-                    (element, field) row of the field operand and per field component of
-                    a tile's flux operand (FP16 range) */
+                    (element, field) row of the field operand and per field type (E, H)
+                    of a tile's flux operand (FP16 range) */
 } dg_precision;
 /* The tensor-core precisions cover N = 1..7: up to N = 5 the split operators
  * stay in shared memory, at N = 6, 7 they are streamed from L2 slice by slice.

@@ -4,7 +4,8 @@
 // tensor cores (tcgen05.mma, accumulators in tensor memory), in split
 // precision: every operand x is stored as a 16-bit pair hi = rn(x),
 // lo = rn(x - hi), and each product is formed as hi*hi + hi*lo + lo*hi with
-// FP32 accumulation (BF16, or FP16 with a power-of-two scale per row).
+// FP32 accumulation (BF16, or FP16 with power-of-two scales: per row for the
+// fields, per field type (E, H) of a tile for the fluxes).
 //
 // Section 2, Fig. (el-local-ops): the field data of many elements is treated
 // as one matrix so that local differentiation and lifting become
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
   float *s_inv1 = reinterpret_cast<float *>(smem + T::OFF_MX);  // A1 row inverse scales (compact rows)
-  uint32_t *s_mx2 = reinterpret_cast<uint32_t *>(s_inv1 + 128); // A2 maxima per field component (float bits)
+  uint32_t *s_mx2 = reinterpret_cast<uint32_t *>(s_inv1 + 128); // A2 maxima of the E and H fluxes (float bits)
   uint64_t *bar1 = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // GEMM1 done
   uint64_t *bar2 = bar1 + 1;                                        // GEMM2 (and all earlier MMAs) done
   uint64_t *barR = bar1 + 2;                                        // residual tile landed
@@ -451,12 +452,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         *s_staged = more ? 1 : 0;
       }
       if constexpr (!BF16) {
-        // one FP16 scale per field component of the tile: |x| as float bits
-        // orders like |x|
+        // one FP16 scale per field type (E, H) of the tile: |x| as float
+        // bits orders like |x|
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const uint32_t m = __reduce_max_sync(0xffffffffu, fmx[c]);
-          if (lane == 0) atomicMax(s_mx2 + c, m);
+        for (int g = 0; g < 2; ++g) {
+          const uint32_t m = __reduce_max_sync(0xffffffffu, max(fmx[3 * g], max(fmx[3 * g + 1], fmx[3 * g + 2])));
+          if (lane == 0) atomicMax(s_mx2 + g, m);
         }
       }
       // the previous tile's bulk stores must have read the A2 bytes
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           sc2[c] = 1.f;
           if constexpr (!BF16) {
             float inv;
-            row_scale(__uint_as_float(s_mx2[c]), sc2[c], inv);
+            row_scale(__uint_as_float(s_mx2[c / 3]), sc2[c], inv);
           }
         }
 #pragma unroll
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float sc;
         const float inv1 = s_inv1[lane_used ? ridx : 0];
         g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
-        row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
+        row_scale(__uint_as_float(s_mx2[fld / 3]), sc, inv2);
       }
       ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
       umma::fence_after_sync();

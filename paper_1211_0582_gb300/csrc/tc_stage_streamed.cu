@@ -399,11 +399,11 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         }
       }
       if constexpr (!BF16) {
-        // one FP16 scale per field component of the tile
+        // one FP16 scale per field type (E, H) of the tile
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const uint32_t m = __reduce_max_sync(0xffffffffu, fmx[c]);
-          if (lane == 0) atomicMax(s_mx2 + c, m);
+        for (int g = 0; g < 2; ++g) {
+          const uint32_t m = __reduce_max_sync(0xffffffffu, max(fmx[3 * g], max(fmx[3 * g + 1], fmx[3 * g + 2])));
+          if (lane == 0) atomicMax(s_mx2 + g, m);
         }
       }
     }
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         sc2[c] = 1.f;
         if constexpr (!BF16) {
           float inv;
-          row_scale(__uint_as_float(s_mx2[c]), sc2[c], inv);
+          row_scale(__uint_as_float(s_mx2[c / 3]), sc2[c], inv);
         }
       }
 #pragma unroll
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       float sc;
       const float inv1 = s_inv1[lane_used ? ridx : 0];
       g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
-      row_scale(__uint_as_float(s_mx2[fld]), sc, inv2);
+      row_scale(__uint_as_float(s_mx2[fld / 3]), sc, inv2);
     }
     // residual of one 8-node chunk of this lane's row (loaded one chunk ahead)
     auto load_res = [&](int ch, float4 &r0, float4 &r1) {
