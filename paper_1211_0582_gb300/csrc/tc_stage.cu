@@ -365,10 +365,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       bool ok = true;
 
-      // ---- 4. upwind flux (overlaps GEMM1), in registers
-      // neighbour traces outside the tile are requested before the field split,
-      // which hides their latency; neighbours inside the tile are read from the
-      // staged fields once they are in place
+      // ---- 4. upwind flux (overlaps GEMM1), in registers: the neighbour traces
+      // outside the tile are requested from L2 first (all of a lane's loads in
+      // flight together); neighbours inside the tile are read from the staged
+      // fields
       float qp[R2][2][6];
       int lidx[R2][2];
 #pragma unroll
