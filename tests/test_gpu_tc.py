@@ -66,6 +66,22 @@ def test_step_ignores_entry_residual(N, precision):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("N", [5, 7])
+def test_fp16_flux_scale_per_field_type(N):
+    # the FP16 flux split takes one power-of-two scale per field type of a tile:
+    # with H about 1/377 of E (SI units, H ~ E / Z0) each type keeps its own
+    # relative accuracy
+    s, m = pair(N, 3, "fp16x3")
+    u = np.random.default_rng(12).standard_normal(m.shape)
+    u[3:] /= 376.73
+    ref = m.rhs(u)
+    got = s.from_device(s.rhs(s.to_device(u)))
+    for sl, name in ((slice(0, 3), "E"), (slice(3, 6), "H")):
+        err = rel_l2(got[sl], ref[sl])
+        print(f"N={N} {name}: rel l2 {err:.3e}")
+        assert err < TOL["fp16x3"]
+
+
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
 def test_tc_smooth_field_and_scaling(precision):
     # a smooth field (strong cancellation in D u) at tiny and large magnitudes:
