@@ -14,6 +14,9 @@
 //   GEMM1  V[(e,f), (d,i)] = sum_j u[(e,f), j] D_d[i, j]        (d = r, s, t)
 //   GEMM2  S[(e,f), i]     = sum_m flux[(e,f), m] LIFT[i, m]
 // (the face-node columns m of GEMM2 are padded to an even count per face).
+// GEMM1's A operand (the split fields) is written to tensor memory with
+// tcgen05.st and read from there; GEMM2's (the split fluxes) goes through
+// shared memory.
 // The operators (B operands) stay resident in shared memory for the whole
 // persistent kernel ("store the matrices, stream the vector data", Section 3).
 // The epilogue reads V and S from TMEM with one thread per row, applies the
@@ -86,17 +89,19 @@ struct TC {
   static constexpr int NFPE = (NFP + 1) / 2 * 2; // A2 columns per face (even: column pairs stay in one face)
   static constexpr int K2 = rup(4 * NFPE, 16);   // GEMM2 reduction length (face-node columns)
   static constexpr int N2 = NB;           // GEMM2 output columns
-  static constexpr int TCOLS = tmem_cols(N1 + N2);
+  static constexpr int CA = rup(N1 + N2, 32);  // TMEM column of the A1 operand (hi, then lo): after V and S
+  static constexpr int TCOLS = tmem_cols(CA + K1);
   static constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staged tiles
-  static constexpr int A1B = 128 * K1 * 2, A2B = 128 * K2 * 2, B1B = N1 * K1 * 2, B2B = N2 * K2 * 2;
-  // A1 hi/lo; between the differentiation GEMM of one tile and the field
-  // split of the next, the same bytes receive the next tile's fields
-  static constexpr int OFF_A1H = 0, OFF_A1L = OFF_A1H + A1B;
+  static constexpr int A2B = 128 * K2 * 2, B1B = N1 * K1 * 2, B2B = N2 * K2 * 2;
+  // fp32 [6][FS]: the next tile's fields, staged by bulk copies (the split
+  // fields, GEMM1's A operand, live in tensor memory from column CA on)
+  static constexpr int STB = rup(6 * FS * 4, 128);
+  static constexpr int OFF_STAGE = 0;
   // A2 hi/lo; between the lifting GEMM of one tile and the flux split of the
   // next, the same bytes hold the tile's results [2][6][FS] for the bulk stores
   static constexpr int OUTB = 12 * FS * 4;
   static constexpr int A2R = 2 * A2B > OUTB ? 2 * A2B : OUTB;
-  static constexpr int OFF_A2H = OFF_A1L + A1B, OFF_A2L = OFF_A2H + A2B;
+  static constexpr int OFF_A2H = OFF_STAGE + STB, OFF_A2L = OFF_A2H + A2B;
   static constexpr int OFF_B1H = OFF_A2H + A2R, OFF_B1L = OFF_B1H + B1B;
   static constexpr int OFF_B2H = OFF_B1L + B1B, OFF_B2L = OFF_B2H + B2B;
   static constexpr int OPS_BYTES = 2 * B1B + 2 * B2B; // contiguous from OFF_B1H
@@ -109,10 +114,10 @@ struct TC {
   static constexpr int FCONN = FELEM + kTileElems * G_STRIDE * 4, FSLOT = FCONN + kTileElems * 4 * 8;
   static constexpr int OFF_FACE = OFF_RES + 6 * FS * 4;
   static constexpr int OFF_TAB = OFF_FACE + 2 * FSLOT;
-  static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16); // [128] A1 row inverse scales, [8] A2 field maxima
-  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32; // mbarriers: GEMM1, GEMM2, residual, next tile; TMEM slot
+  // [128] A1 row inverse scales, [8] A2 field-type maxima, [128] A1 row maxima
+  static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16);
+  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32 + 128 * 4; // mbarriers: GEMM1, GEMM2, residual, next tile; TMEM slot
   static constexpr int SMEM = OFF_BAR + 48;
-  static_assert(6 * FS * 4 <= 2 * A1B, "the staged fields do not fit in the A1 operand");
 };
 
 // Three split products per K step: hi*hi, hi*lo, lo*hi, FP32 accumulation.
@@ -139,6 +144,25 @@ __device__ __forceinline__ void issue_split_gemm(uint32_t d_tmem, uint32_t a_hi,
   }
 }
 
+// The same products with the A operand (hi and lo) in tensor memory: one N
+// chunk; a K step of 16 advances the A address by 8 columns.
+template <bool BF16, int KP, int NR>
+__device__ __forceinline__ void issue_split_gemm_ta(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                                    uint32_t b_lo) {
+  constexpr uint32_t sbo = uint32_t(KP) * 16u;
+  static_assert(NR <= 256, "one N chunk");
+  const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NR));
+  const uint64_t dbh = umma::make_desc(b_hi, 128, sbo), dbl = umma::make_desc(b_lo, 128, sbo);
+#pragma unroll
+  for (int kk = 0; kk < KP / 16; ++kk) {
+    const uint64_t ko = uint64_t(kk) * 16u;
+    const uint32_t ac = uint32_t(8 * kk);
+    umma::mma_f16_ta(d_tmem, a_hi + ac, dbh + ko, idesc, kk > 0 ? 1u : 0u);
+    umma::mma_f16_ta(d_tmem, a_hi + ac, dbl + ko, idesc, 1u);
+    umma::mma_f16_ta(d_tmem, a_lo + ac, dbh + ko, idesc, 1u);
+  }
+}
+
 // Multi-step persistent form (ensembles): stage coefficients, the two state
 // buffers the stages alternate between, the step count and the grid barrier.
 struct EnsLaunch {
@@ -160,12 +184,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) uint8_t smem[];
   float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);       // [6][FS]: fields of the tile
   float *s_res = reinterpret_cast<float *>(smem + T::OFF_RES);   // [6][FS]: residual of the tile
-  float *s_stage = reinterpret_cast<float *>(smem + T::OFF_A1H); // [6][FS]: next tile's fields (in A1)
+  float *s_stage = reinterpret_cast<float *>(smem + T::OFF_STAGE); // [6][FS]: next tile's fields
   float *s_out = reinterpret_cast<float *>(smem + T::OFF_A2H);   // [2][6][FS]: results (in A2)
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
   float *s_inv1 = reinterpret_cast<float *>(smem + T::OFF_MX);  // A1 row inverse scales (compact rows)
   uint32_t *s_mx2 = reinterpret_cast<uint32_t *>(s_inv1 + 128); // A2 maxima of the E and H fluxes (float bits)
+  uint32_t *s_rowmx = s_mx2 + 8; // A1 row maxima (float bits), FP16
   uint64_t *bar1 = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // GEMM1 done
   uint64_t *bar2 = bar1 + 1;                                        // GEMM2 (and all earlier MMAs) done
   uint64_t *barR = bar1 + 2;                                        // residual tile landed
@@ -187,8 +212,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the first LSERK4 stage has a = 0: the residual it overwrites is not read
   bool read_res = MODE == MODE_LSERK && a.rk_a != 0.f;
 
-  // fields of tile t into the A1 bytes, its face and element data into a
-  // slot (one thread; completes on barU)
+  // fields of tile t into the staging buffer, its face and element data into
+  // a slot (one thread; completes on barU)
   auto stage_tile = [&](int t, int slot) {
     const int64_t kb = tm.start(t);
     const uint32_t nb = uint32_t(tm.size(t, a.K));
@@ -203,13 +228,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
 
   // ---- one-time setup
-  for (int i = tid; i < (2 * T::A1B + T::A2R) / 16; i += kThreads)
+  for (int i = tid; i < (T::STB + T::A2R) / 16; i += kThreads)
     reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < T::OPS_BYTES / 16; i += kThreads)
     reinterpret_cast<uint4 *>(smem + T::OFF_B1H)[i] = __ldg(ops + i);
   for (int i = tid; i < NFF + kConnKinds * NFP; i += kThreads)
     s_fm[i] = i < NFF ? a.fmask[i] : a.nbrtab[i - NFF];
-  for (int i = tid; i < 136; i += kThreads) s_inv1[i] = i < 128 ? 1.f : 0.f;
+  for (int i = tid; i < 264; i += kThreads) s_inv1[i] = i < 128 ? 1.f : 0.f;
   if (tid == 0) {
     umma::mbar_init(bar1, 1);
     umma::mbar_init(bar2, 1);
@@ -227,16 +252,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   // stage, nothing it wrote is read before this point
   if constexpr (!ENS) pdl_wait();
 
-  // field split: warp w owns operand rows 8w..8w+7 of A1; lane -> (row, half of
-  // a K group of 8), so one row's maximum is a reduction over 4 lanes and every
-  // half-warp writes one 128-byte core matrix; the padding columns are written
-  // as zeros (the staging overwrote them)
-  constexpr int KG1 = T::K1 / 8;
-  constexpr int R1 = (KG1 + 1) / 2;
-  const int r1 = warp * 8 + (lane & 7);
+  // field split: warp w writes the TMEM lanes of its quarter w % 4 (lane =
+  // operand row) and K values 16 (w / 4) .. +15 of A1 (warps past K1 idle); an
+  // FP16 row maximum is combined over the row's warps in shared memory; the
+  // padding columns are written as zeros
+  const int q1 = warp & 3, p1 = warp >> 2;
+  const int r1 = 32 * q1 + lane;            // operand row = TMEM lane of this warp's quarter
   const int cr1 = compact_row(r1);
   const int e1 = cr1 >= 0 ? cr1 / 6 : 0, f1 = cr1 >= 0 ? cr1 % 6 : 0;
-  const int kq1 = 4 * ((lane >> 3) & 1) + 8 * (lane >> 4); // + 16 s
+  const int kb1 = 16 * p1;                  // this thread's 16 K values
+  const bool a1_part = kb1 < T::K1;         // warp-uniform
+  const uint32_t a1_hi = tmem + uint32_t(T::CA), a1_lo = a1_hi + uint32_t(T::K1 / 2);
+  const uint32_t a1_st = (uint32_t(q1 * 32) << 16) + uint32_t(8 * p1);
   // flux: blocks of 4 elements x 16 columns of A2 (padding columns included,
   // written as zeros), lane -> (element, pair of adjacent columns); column
   // f * NFPE + m holds face node m of face f, so a pair never straddles two
@@ -299,32 +326,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int2 *s_fconn = reinterpret_cast<const int2 *>(fslot + T::FCONN);
 
       // ---- 1. the staged fields into registers; once the previous tile's bulk
-      // stores have read shared memory, the residual copy starts and the fields
-      // go to the tile staging and (split) to the A1 operand
+      // stores have read shared memory, the residual copy starts
       const bool okU = umma::mbar_wait_bounded(barU, phase, wlim);
-      float4 v[R1];
+      float4 v[4];
       float mx = 0.f;
 #pragma unroll
-      for (int s = 0; s < R1; ++s) {
-        const int k = kq1 + 16 * s;
-        v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (cr1 >= 0 && k < NPP && e1 < ne) {
-          v[s] = *reinterpret_cast<const float4 *>(s_stage + f1 * FS + e1 * NPP + k);
+      for (int j = 0; j < 4; ++j) {
+        const int k = kb1 + 4 * j;
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a1_part && cr1 >= 0 && k < NPP && e1 < ne) {
+          v[j] = *reinterpret_cast<const float4 *>(s_stage + f1 * FS + e1 * NPP + k);
           if (k + 3 >= NP) {
-            if (k + 0 >= NP) v[s].x = 0.f;
-            if (k + 1 >= NP) v[s].y = 0.f;
-            if (k + 2 >= NP) v[s].z = 0.f;
-            if (k + 3 >= NP) v[s].w = 0.f;
+            if (k + 0 >= NP) v[j].x = 0.f;
+            if (k + 1 >= NP) v[j].y = 0.f;
+            if (k + 2 >= NP) v[j].z = 0.f;
+            if (k + 3 >= NP) v[j].w = 0.f;
           }
         }
-        if constexpr (!BF16) mx = absmax4(mx, v[s]);
+        if constexpr (!BF16) mx = absmax4(mx, v[j]);
       }
-      float sc1 = 1.f, inv1r = 1.f;
-      if constexpr (!BF16) {
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-        row_scale(mx, sc1, inv1r);
-      }
+      if (!BF16 && a1_part && cr1 >= 0) atomicMax(s_rowmx + r1, __float_as_uint(mx));
       if (__syncthreads_or(!okU)) {
         if (tid == 0) {
           atomicExch(err_flag, 1);
@@ -337,30 +358,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
         for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
       }
-      if (!BF16 && cr1 >= 0 && lane < 8) s_inv1[cr1] = inv1r;
-#pragma unroll
-      for (int s = 0; s < R1; ++s) {
-        const int k = kq1 + 16 * s;
-        if (cr1 >= 0 && k < T::K1) {
-          if (k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[s];
-          float4 w = v[s];
-          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
-          uint2 hi, lo;
-          split2<BF16>(w.x, w.y, hi.x, lo.x);
-          split2<BF16>(w.z, w.w, hi.y, lo.y);
-          const uint32_t off = umma::kmajor_offset(uint32_t(r1), uint32_t(k), uint32_t(T::K1));
-          *reinterpret_cast<uint2 *>(smem + T::OFF_A1H + off) = hi;
-          *reinterpret_cast<uint2 *>(smem + T::OFF_A1L + off) = lo;
+      // ---- 2. the fields to the tile buffer and, split, to the A1 operand in
+      // tensor memory
+      if (a1_part) {
+        float sc1 = 1.f, inv1r = 1.f;
+        if constexpr (!BF16) {
+          if (cr1 >= 0) row_scale(__uint_as_float(s_rowmx[r1]), sc1, inv1r);
+          if (p1 == 0 && cr1 >= 0) s_inv1[cr1] = inv1r;
         }
+        uint32_t hi[8], lo[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = kb1 + 4 * j;
+          if (cr1 >= 0 && k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[j];
+          float4 w = v[j];
+          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+          split2<BF16>(w.x, w.y, hi[2 * j], lo[2 * j]);
+          split2<BF16>(w.z, w.w, hi[2 * j + 1], lo[2 * j + 1]);
+        }
+        umma::tmem_st8(a1_hi + a1_st, hi);
+        umma::tmem_st8(a1_lo + a1_st, lo);
+        umma::tmem_wait_st();
       }
-      umma::fence_proxy_async();
+      umma::fence_before_sync();
       __syncthreads();
+      if (!BF16 && tid < 128) s_rowmx[tid] = 0u;
 
       // ---- 3. local differentiation on the tensor cores (asynchronous)
       if (issuer) {
         umma::fence_after_sync();
-        issue_split_gemm<BF16, T::K1, T::N1>(tmem, sbase + T::OFF_A1H, sbase + T::OFF_A1L, sbase + T::OFF_B1H,
-                                             sbase + T::OFF_B1L);
+        issue_split_gemm_ta<BF16, T::K1, T::N1>(tmem, a1_hi, a1_lo, sbase + T::OFF_B1H, sbase + T::OFF_B1L);
         umma::commit(bar1);
       }
       bool ok = true;
@@ -444,10 +471,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][h][c])));
         }
       }
-      // once GEMM1 has read A1, the next tile's fields and face data are staged
+      // the next tile's fields and face data are staged (issued here rather
+      // than right after step 1: earlier, the copies compete with GEMM1 and the
+      // flux phase for shared memory, which measured slower)
       if (stager) {
-        ok = umma::mbar_wait_bounded(bar1, phase, wlim);
-        const bool more = ok && tile + int(gridDim.x) < tm.ntiles;
+        const bool more = tile + int(gridDim.x) < tm.ntiles;
         if (more) stage_tile(tile + gridDim.x, slot ^ 1);
         *s_staged = more ? 1 : 0;
       }
