@@ -91,6 +91,8 @@ struct TC {
   static constexpr int N2 = NB;           // GEMM2 output columns
   static constexpr int CA = rup(N1 + N2, 32);  // TMEM column of the A1 operand (hi, then lo): after V and S
   static constexpr int TCOLS = tmem_cols(CA + K1);
+  static_assert(CA + K1 <= 512, "accumulators and the A1 operand exceed tensor memory");
+  static_assert(K1 <= 16 * (kThreads / 128), "the field split covers 16 K values per warp, four warps per quarter");
   static constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staged tiles
   static constexpr int A2B = 128 * K2 * 2, B1B = N1 * K1 * 2, B2B = N2 * K2 * 2;
   // fp32 [6][FS]: the next tile's fields, staged by bulk copies (the split
