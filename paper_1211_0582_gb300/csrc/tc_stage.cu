@@ -94,7 +94,17 @@ struct TC {
   static_assert(CA + K1 <= 512, "accumulators and the A1 operand exceed tensor memory");
   static_assert(K1 <= 16 * (kThreads / 128), "the field split covers 16 K values per warp, four warps per quarter");
   static constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staged tiles
-  static constexpr int A2B = 128 * K2 * 2, B1B = N1 * K1 * 2, B2B = N2 * K2 * 2;
+  // A2 in the K-major core-matrix layout with padded strides: 144 bytes
+  // between the core matrices of a row group along K (not 128) and a row-group
+  // stride that is a multiple of 128 bytes. The flux split's 32-bit stores put
+  // lanes kp and kp + 4 into two core matrices of one row; 128 bytes apart they
+  // would share a bank, 144 bytes apart they do not.
+  static constexpr int A2LBO = 144;
+  static constexpr int A2SBO = rup(K2 / 8 * A2LBO, 128);
+  static constexpr int A2B = 16 * A2SBO, B1B = N1 * K1 * 2, B2B = N2 * K2 * 2;
+  static __device__ __forceinline__ uint32_t a2_offset(uint32_t row, uint32_t k) {
+    return (row >> 3) * uint32_t(A2SBO) + (k >> 3) * uint32_t(A2LBO) + (row & 7u) * 16u + (k & 7u) * 2u;
+  }
   // fp32 [6][FS]: the next tile's fields, staged by bulk copies (the split
   // fields, GEMM1's A operand, live in tensor memory from column CA on)
   static constexpr int STB = rup(6 * FS * 4, 128);
@@ -124,13 +134,16 @@ struct TC {
 
 // Three split products per K step: hi*hi, hi*lo, lo*hi, FP32 accumulation.
 // Fully unrolled; the operand descriptors are formed once and advanced along K
-// by adding to their start-address field (256 bytes = 16 in units of 16 bytes;
-// shared-memory addresses stay below 2^18, so the field never carries out).
-template <bool BF16, int KP, int NR>
+// by adding to their start-address field (two core matrices per K step: 256
+// bytes = 16 in units of 16 bytes for B, 2 ALBO bytes for A; shared-memory
+// addresses stay below 2^18, so the field never carries out). B is packed
+// (128-byte core-matrix stride along K); A has the strides ALBO, ASBO.
+template <bool BF16, int KP, int NR, int ALBO, int ASBO>
 __device__ __forceinline__ void issue_split_gemm(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
                                                  uint32_t b_lo) {
   constexpr uint32_t sbo = uint32_t(KP) * 16u;
-  const uint64_t dah = umma::make_desc(a_hi, 128, sbo), dal = umma::make_desc(a_lo, 128, sbo);
+  static_assert(ALBO % 16 == 0 && ASBO % 16 == 0, "descriptor strides are in units of 16 bytes");
+  const uint64_t dah = umma::make_desc(a_hi, ALBO, ASBO), dal = umma::make_desc(a_lo, ALBO, ASBO);
 #pragma unroll
   for (int n0 = 0; n0 < NR; n0 += 256) {
     const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NR - n0 < 256 ? NR - n0 : 256));
@@ -138,10 +151,10 @@ __device__ __forceinline__ void issue_split_gemm(uint32_t d_tmem, uint32_t a_hi,
     const uint64_t dbh = umma::make_desc(b_hi + boff, 128, sbo), dbl = umma::make_desc(b_lo + boff, 128, sbo);
 #pragma unroll
     for (int kk = 0; kk < KP / 16; ++kk) {
-      const uint64_t ko = uint64_t(kk) * 16u;
-      umma::mma_f16(d_tmem + uint32_t(n0), dah + ko, dbh + ko, idesc, kk > 0 ? 1u : 0u);
-      umma::mma_f16(d_tmem + uint32_t(n0), dah + ko, dbl + ko, idesc, 1u);
-      umma::mma_f16(d_tmem + uint32_t(n0), dal + ko, dbh + ko, idesc, 1u);
+      const uint64_t ko = uint64_t(kk) * 16u, ka = uint64_t(kk) * uint64_t(2 * ALBO / 16);
+      umma::mma_f16(d_tmem + uint32_t(n0), dah + ka, dbh + ko, idesc, kk > 0 ? 1u : 0u);
+      umma::mma_f16(d_tmem + uint32_t(n0), dah + ka, dbl + ko, idesc, 1u);
+      umma::mma_f16(d_tmem + uint32_t(n0), dal + ka, dbh + ko, idesc, 1u);
     }
   }
 }
@@ -517,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = 0; c < 6; ++c) {
               uint32_t hi, lo;
               split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
-              const uint32_t o = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
+              const uint32_t o = T::a2_offset(r0 + uint32_t(c), uint32_t(fm));
               *reinterpret_cast<uint32_t *>(smem + T::OFF_A2H + o) = hi;
               *reinterpret_cast<uint32_t *>(smem + T::OFF_A2L + o) = lo;
             }
@@ -531,8 +544,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // from GEMM1: chain rule (eq. dg-reference-matrices) and curls
       if (issuer) {
         umma::fence_after_sync();
-        issue_split_gemm<BF16, T::K2, T::N2>(tmem + uint32_t(T::N1), sbase + T::OFF_A2H, sbase + T::OFF_A2L,
-                                             sbase + T::OFF_B2H, sbase + T::OFF_B2L);
+        issue_split_gemm<BF16, T::K2, T::N2, T::A2LBO, T::A2SBO>(tmem + uint32_t(T::N1), sbase + T::OFF_A2H,
+                                                                 sbase + T::OFF_A2L, sbase + T::OFF_B2H,
+                                                                 sbase + T::OFF_B2L);
         umma::commit(bar2);
       }
       const bool live = lane_used && e_loc < ne;
