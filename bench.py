@@ -63,10 +63,10 @@ def bytes_per_element(N: int, Npad: int) -> float:
 
 
 # DRAM bytes (read + write) per launch of the stage kernel, the mean over the
-# five stages of one step, from ncu captures (profiles/k_stage_simt_fp32_n5_24cube.md,
-# k_stage_tc_streamed_fp16x3_n7_16cube.md); keyed by
-# (precision, N, hexahedra per edge); absent where no capture of the current kernel exists.
-NCU_TRAFFIC = {("fp32", 5, 24): 391.472e6, ("fp16x3", 7, 16): 219.047e6}
+# five stages of one step, from an ncu capture (profiles/k_stage_simt_fp32_n5_24cube.md);
+# keyed by (precision, N, hexahedra per edge); absent where no capture of the
+# current kernel exists.
+NCU_TRAFFIC = {("fp32", 5, 24): 391.472e6}
 
 
 def measured_peaks():

@@ -62,7 +62,15 @@ struct TS {
   static constexpr int STREAM = PER * SL;
   static constexpr int TCOLS = tmem_cols(4 * NB);
   static constexpr int FS = kTileS * NPP + 4; // padded field-block stride of the staged fields
-  static constexpr int A1B = 128 * K1 * 2, A2B = 128 * K2 * 2;
+  // A2 with padded core-matrix strides (144 bytes along K, a multiple of 128
+  // bytes between row groups), so that the flux split's stores of lanes kp
+  // and kp + 4 (two core matrices of one row) fall into different banks
+  static constexpr int A2LBO = 144;
+  static constexpr int A2SBO = rup(K2 / 8 * A2LBO, 128);
+  static constexpr int A1B = 128 * K1 * 2, A2B = 16 * A2SBO;
+  static __device__ __forceinline__ uint32_t a2_offset(uint32_t row, uint32_t k) {
+    return (row >> 3) * uint32_t(A2SBO) + (k >> 3) * uint32_t(A2LBO) + (row & 7u) * 16u + (k & 7u) * 2u;
+  }
   static constexpr int AREG = 2 * (A1B > A2B ? A1B : A2B); // A1 hi/lo, later A2 hi/lo
   static constexpr int OFF_RING = AREG;
   static constexpr int OFF_U = OFF_RING + kSlots * SL;           // fp32 [6][FS]
@@ -434,7 +442,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
           for (int c = 0; c < 6; ++c) {
             uint32_t hi, lo;
             split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
-            const uint32_t o = umma::kmajor_offset(r0 + uint32_t(c), uint32_t(fm), uint32_t(T::K2));
+            const uint32_t o = T::a2_offset(r0 + uint32_t(c), uint32_t(fm));
             *reinterpret_cast<uint32_t *>(smem + o) = hi;
             *reinterpret_cast<uint32_t *>(smem + T::A2B + o) = lo;
           }
@@ -448,7 +456,8 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     if (issuer) {
       umma::fence_after_sync();
       const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NB));
-      const uint64_t ah0 = umma::make_desc(sbase, 128, T::K2 * 16), al0 = umma::make_desc(sbase + T::A2B, 128, T::K2 * 16);
+      const uint64_t ah0 = umma::make_desc(sbase, T::A2LBO, T::A2SBO);
+      const uint64_t al0 = umma::make_desc(sbase + T::A2B, T::A2LBO, T::A2SBO);
       const uint32_t dt = tmem + uint32_t(3 * NB);
       for (int g = 0; g < T::NS2; ++g) {
         ok = consume([&](uint32_t b) {
@@ -456,7 +465,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
           for (int j = 0; j < T::G2; ++j) {
             const int kk = g * T::G2 + j;
             if (kk >= T::KS2) break;
-            const uint64_t ko = uint64_t(kk) * 16u;
+            const uint64_t ko = uint64_t(kk) * uint64_t(2 * T::A2LBO / 16); // two core matrices of A2
             const uint32_t sb = b + uint32_t(j * T::SUB);
             const uint64_t bh = umma::make_desc(sb, 128, 256), bl = umma::make_desc(sb + uint32_t(NB * 32), 128, 256);
             umma::mma_f16(dt, ah0 + ko, bh, idesc, kk > 0 ? 1u : 0u);
