@@ -63,7 +63,7 @@ def bytes_per_element(N: int, Npad: int) -> float:
 
 
 # DRAM bytes (read + write) per launch of the stage kernel, the mean over the
-# five stages of one step, from an ncu capture (profiles/k_stage_simt_fp32_n5_24cube.md);
+# five stages of one step, from an ncu capture of the current kernel;
 # keyed by (precision, N, hexahedra per edge); absent where no capture of the
 # current kernel exists.
 NCU_TRAFFIC = {("fp32", 5, 24): 391.472e6}

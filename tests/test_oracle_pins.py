@@ -377,3 +377,163 @@ def test_misfit_gradient_finite_differences():
     Jm, _, _ = m.misfit_gradient(u0 - h * du, dt, steps, recv, Eref, eps=eps)
     fd = (Jp - Jm) / (2 * h)
     assert abs(fd - np.vdot(gu, du)) < 1e-6 * abs(fd)
+
+
+# ---------------------------------------------------------------- energy (closed forms)
+def _tet_volumes(VX, VY, VZ, EToV):
+    P = np.stack([VX, VY, VZ], 1)[EToV]
+    return np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6.0
+
+
+def _gauss_tet(q):
+    """Collapsed (Duffy) Gauss-Legendre rule on the unit simplex
+    {a, b, c >= 0, a + b + c <= 1}: exact for polynomials of degree <= 2q - 3."""
+    x, w = np.polynomial.legendre.leggauss(q)
+    x, w = (x + 1) / 2, w / 2
+    xi, eta, zeta = np.meshgrid(x, x, x, indexing="ij")
+    wt = w[:, None, None] * w[None, :, None] * w[None, None, :] * (1 - xi) ** 2 * (1 - eta)
+    return xi.ravel(), ((1 - xi) * eta).ravel(), ((1 - xi) * (1 - eta) * zeta).ravel(), wt.ravel()
+
+
+def _materials(K):
+    eps = W.element_eps(K, seed=2).astype(np.float64)
+    mu = W.element_eps(K, seed=9, lo=0.5, hi=3.0).astype(np.float64)
+    return eps, mu
+
+
+def test_energy_piecewise_constant_fields_closed_form():
+    # A field constant on each element: E_h = 1/2 sum_k |T_k| (eps_k |E_k|^2 + mu_k |H_k|^2),
+    # with |T_k| from the raw vertices. Fails if J_k is dropped, eps and mu are
+    # swapped, or either weights the wrong rows.
+    N = 3
+    VX, VY, VZ, EToV = W.kuhn_cube(3, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    eps, mu = _materials(K)
+    m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps, mu=mu)
+    amp = 2.0 * W.uniform(11, 6 * K).reshape(6, K) - 1.0
+    u = np.repeat(amp[:, :, None], m.Np, axis=2)
+    vol = _tet_volumes(VX, VY, VZ, EToV)
+    want = 0.5 * np.sum(vol * (eps * (amp[:3] ** 2).sum(0) + mu * (amp[3:] ** 2).sum(0)))
+    assert abs(m.energy(u) - want) < 1e-13 * want
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_energy_polynomial_field_exact_integral(N):
+    # For a global polynomial field of degree <= N the nodal interpolant is
+    # exact and M integrates the squares exactly: E_h equals the integral of
+    # 1/2 (eps |E|^2 + mu |H|^2) over the mesh, here by an independent Gauss rule.
+    VX, VY, VZ, EToV = W.kuhn_cube(2, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    eps, mu = _materials(K)
+    m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps, mu=mu)
+
+    def fields(x, y, z):
+        return np.stack([1 + x * y, z * z - x, x * y * z, y - z * z, x * x * z, 0.5 + y ** 3])
+
+    x, y, z = m.coords()
+    u = fields(x, y, z)
+    a, b, c, wq = _gauss_tet(N + 3)
+    P = np.stack([VX, VY, VZ], 1)[EToV]
+    want = 0.0
+    for k in range(K):
+        v0, e1, e2, e3 = P[k, 0], P[k, 1] - P[k, 0], P[k, 2] - P[k, 0], P[k, 3] - P[k, 0]
+        X = v0[:, None] + e1[:, None] * a + e2[:, None] * b + e3[:, None] * c
+        f = fields(X[0], X[1], X[2])
+        dens = eps[k] * (f[:3] ** 2).sum(0) + mu[k] * (f[3:] ** 2).sum(0)
+        want += 0.5 * abs(np.linalg.det(np.stack([e1, e2, e3]))) * (wq @ dens)
+    assert abs(m.energy(u) - want) < 1e-12 * want
+
+
+# ---------------------------------------------------------------- receiver traces
+@pytest.fixture(scope="module")
+def small_run():
+    N = 2
+    VX, VY, VZ, EToV = W.kuhn_cube(2, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    eps = W.element_eps(K, seed=2).astype(np.float64)
+    m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps)
+    x, y, z = m.coords()
+    u0 = W.gaussian_pulse(x, y, z)
+    recv = W.receivers(K, m.Np, 16, 4)
+    return m, eps, u0, recv, 0.01, 5
+
+
+def test_receiver_traces_sampled_at_the_end_of_each_step(small_run):
+    # traces[n] is E at the receivers after n + 1 full LSERK4 steps (not at
+    # stages, not before the step); checked against the pinned stepper.
+    m, eps, u0, recv, dt, steps = small_run
+    tr = m.receiver_traces(u0, dt, steps, recv, eps=eps)
+    assert tr.shape == (steps, 3, recv.size)
+    for n in range(steps):
+        u, _ = m.lserk(u0, dt, n + 1)
+        np.testing.assert_allclose(tr[n], u[:3].reshape(3, -1)[:, recv], rtol=1e-14, atol=1e-15)
+    # one step fewer or more would be a different state
+    u_early, _ = m.lserk(u0, dt, 1)
+    assert np.abs(tr[1] - u_early[:3].reshape(3, -1)[:, recv]).max() > 1e-6
+
+
+def test_misfit_of_own_traces_is_zero_and_sums_squares(small_run):
+    # J(eps; Eref = traces(eps)) = 0 exactly (same run, same sampling instants);
+    # a known offset d of the reference gives J = sum d^2 (no factor 1/2).
+    m, eps, u0, recv, dt, steps = small_run
+    tr = m.receiver_traces(u0, dt, steps, recv, eps=eps)
+    J, _, _ = m.misfit_gradient(u0, dt, steps, recv, tr, eps=eps)
+    assert J == 0.0
+    d = 1e-3 * (2.0 * W.uniform(12, tr.size).reshape(tr.shape) - 1.0)
+    J2, _, _ = m.misfit_gradient(u0, dt, steps, recv, tr + d, eps=eps)
+    assert abs(J2 - np.sum(d * d)) < 1e-12 * np.sum(d * d)
+
+
+# ---------------------------------------------------------------- time-step size
+def _stability_polynomial():
+    """Coefficients of R(z) = sum_j g_j z^j of the LSERK4 scheme, g_j = B A^(j-1) 1."""
+    A, B = _butcher()
+    return [1.0] + [B @ np.linalg.matrix_power(A, j - 1) @ np.ones(5) for j in range(1, 6)]
+
+
+def _extreme_eigenvalues(m, alpha):
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    n = 6 * m.K * m.Np
+
+    def mv(x):
+        x = np.asarray(x)
+        if np.iscomplexobj(x):
+            return (m.rhs(np.ascontiguousarray(x.real).reshape(m.shape), alpha).ravel()
+                    + 1j * m.rhs(np.ascontiguousarray(x.imag).reshape(m.shape), alpha).ravel())
+        return m.rhs(np.ascontiguousarray(x).reshape(m.shape), alpha).ravel()
+
+    op = sla.LinearOperator((n, n), matvec=mv, dtype=np.float64)
+    out = []
+    for which in ("LM", "LI"):  # largest modulus, largest imaginary part
+        out.append(sla.eigs(op, k=4, which=which, return_eigenvectors=False, tol=1e-6, maxiter=20000,
+                            v0=np.ones(n)))
+    return np.concatenate(out)
+
+
+def test_cfl_half_inside_the_lserk4_stability_region():
+    # dt = CFL h / N^2 with CFL = 0.5 on the unit-cube mesh with 4^3 hexahedra, N = 3:
+    # the extreme eigenvalues of the semi-discrete operator, scaled by dt, lie
+    # inside |R(z)| <= 1 with margin. Central flux (imaginary spectrum):
+    # dt rho <= 0.8 x the imaginary-axis limit of R. Upwind flux (largest
+    # eigenvalues on the negative real axis): |R(dt lambda)| <= 0.5 and
+    # dt rho <= 0.8 x the real-axis limit.
+    g = _stability_polynomial()
+    # the scheme is fourth order: R agrees with exp(z) through z^4
+    np.testing.assert_allclose(g[:5], [1 / math.factorial(j) for j in range(5)], atol=1e-12)
+    R = lambda z: sum(g[j] * z ** j for j in range(6))
+    ys = np.linspace(0.0, 6.0, 60001)
+    y_lim = ys[np.argmax(np.abs(R(1j * ys)) > 1 + 1e-13) - 1]
+    xs = np.linspace(0.0, -8.0, 80001)
+    x_lim = -xs[np.argmax(np.abs(R(xs)) > 1 + 1e-13) - 1]
+    assert 3.3 < y_lim < 3.4 and 4.6 < x_lim < 4.7
+    N, n = 3, 4
+    VX, VY, VZ, EToV = W.kuhn_cube(n)
+    m = O.Mesh(N, VX, VY, VZ, EToV)
+    dt = 0.5 * (1.0 / n) / N ** 2
+    lc = _extreme_eigenvalues(m, 0.0)
+    assert np.abs(lc.real).max() < 1e-6 * np.abs(lc).max()  # central: skew in the M_eps inner product
+    assert dt * np.abs(lc).max() <= 0.8 * y_lim
+    lu = _extreme_eigenvalues(m, 1.0)
+    assert lu.real.max() < 1e-8
+    assert np.abs(R(dt * lu)).max() <= 0.5
+    assert dt * np.abs(lu).max() <= 0.8 * x_lim
