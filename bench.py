@@ -344,6 +344,8 @@ def run_ours(args):
         "gpu_launches": launches, "roofline": roof, "clocks": clk,
         "kernel_ms_per_launch": launch_ms, "energy_after": energy,
     }
+    if rank == 0 and world == 1 and not args.no_precisions:
+        line["precisions"] = precision_legs(args, stream, headline=(s, args.precision))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs, ne, *_ = cpu_oracle_rate(N, n, args.cpu_sample)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -353,6 +355,77 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def precision_legs(args, stream, headline=None):
+    """The metric's comparison on its two workloads, each in FP32 (CUDA cores),
+    BF16x3 and FP16x3 (tensor cores): throughput over args.steps LSERK4 steps
+    (device-resident, CUDA events) and the relative l2 error against the FP64
+    oracle after the workload's full run (500 steps at N=5, 200 at N=7), over
+    the 65,536 node values stored by tests/golden/make_precision_refs.py (a
+    data file written by the oracle; nothing of the oracle runs here).
+    `headline` = (solver, precision) reuses the headline context for its precision."""
+    import numpy as np
+
+    import paper_1211_0582_gb300 as dg
+    import workloads as W
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_precision_refs as R
+    peaks, peak_kind = measured_peaks()
+    out = {}
+    for name in ("cavity_n5_24cube_500steps", "precision_n7_32cube_200steps"):
+        c, mesh, eps, dt = R.setup(name)
+        try:
+            ref = R.load(name)
+        except OSError:
+            ref = None
+        N, K = c["N"], mesh[3].shape[0]
+        leg = {"workload": f"{c['n']}^3x6 = {K} jittered tets, N={N}, "
+                           f"{'eps U[1,4] per element' if eps is not None else 'eps=mu=1'}, cavity-mode start, "
+                           f"upwind, LSERK4 dt=0.5h/N^2",
+               "error_reference": None if ref is None else str(ref["source"]),
+               "error_steps": c["steps"], "error_samples": None if ref is None else int(ref["idx"].size)}
+        u0_host = None
+        for prec in ("fp32", "bf16x3", "fp16x3"):
+            if headline is not None and headline[1] == prec and N == args.order and c["n"] == args.n \
+                    and eps is None:
+                sv = headline[0]
+            else:
+                sv = dg.Solver(N, precision=prec, stream=stream).upload(*mesh, eps=eps)
+            if u0_host is None:
+                x, y, z = sv.node_coords()
+                u0_host = W.cavity_mode(x, y, z, 0.0)
+                del x, y, z
+            u, r = sv.to_device(u0_host), sv.zeros()
+            sv.step(u, r, dt, args.warmup)
+            ms = _timed(lambda: sv.step(u, r, dt, args.steps), stream)
+            dof = 6 * sv.Np * K
+            launch_ms = ms / (STAGES * args.steps)
+            e = {"gdof_s": STAGES * dof * args.steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / args.steps}
+            if prec == "fp32":
+                peak_tf = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+                e["alu_frac"] = flops_per_element(N) * K / (launch_ms * 1e-3) / 1e12 / peak_tf
+            else:
+                e["hbm_frac"] = bytes_per_element(N, sv.Npad) * K / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+            if ref is not None:
+                u, r = sv.to_device(u0_host), sv.zeros()
+                sv.step(u, r, dt, c["steps"])
+                sv.sync()
+                got = u[:, :, :sv.Np].reshape(-1)[torch_index(ref["idx"], u.device)].double().cpu().numpy()
+                e["rel_l2_vs_fp64"] = float(np.linalg.norm(got - ref["ref"]) / np.linalg.norm(ref["ref"]))
+                e["max_abs_err_rel_to_max"] = float(np.abs(got - ref["ref"]).max() / float(ref["max_full"]))
+            leg[prec] = e
+            del u, r
+            if sv is not (headline[0] if headline else None):
+                del sv
+        leg["speedup_vs_fp32"] = {p: leg[p]["gdof_s"] / leg["fp32"]["gdof_s"] for p in ("bf16x3", "fp16x3")}
+        out[f"N{N}_{c['n']}cube"] = leg
+    return out
+
+
+def torch_index(idx, device):
+    import torch
+    return torch.as_tensor(idx, dtype=torch.int64, device=device)
 
 
 def _timed(fn, stream):
@@ -575,6 +648,8 @@ def main():
     ap.add_argument("--e2e-streams", type=int, default=4, help="contexts/streams the end-to-end steps alternate over")
     ap.add_argument("--cpu-sample", type=int, default=50000, help="elements in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precisions", action="store_true",
+                    help="skip the FP32 / BF16x3 / FP16x3 comparison at N=5 (24^3) and N=7 (32^3)")
     ap.add_argument("--workload", choices=["cavity", "precision", "ensemble", "adjoint"], default="cavity",
                     help="cavity: 24^3 N=5 LSERK4 (headline); precision: split vs FP32 error and speed; "
                          "ensemble: 64 meshes in one persistent launch; adjoint: gradient cost and check")

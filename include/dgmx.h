@@ -130,8 +130,20 @@ int dg_rhs(dg_ctx *ctx, const float *u, float *rhs, float alpha);
  * res is not read (a_1 = 0: the first stage overwrites it), on exit res holds
  * the last stage's residual.
  * Uses a library-owned scratch field vector for the stage ping-pong.
- * Errors: DG_ERR_ARG, DG_ERR_CUDA. */
+ * With the non-finite check enabled (dg_set_nonfinite_check), u and res are
+ * scanned for NaN/Inf after the last stage, the stream is synchronised and
+ * DG_ERR_NONFINITE is returned if one is found (the fields are left as the
+ * stages wrote them).
+ * Errors: DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NONFINITE (check enabled). */
 int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);
+
+/* Failure detection on the stepping path: enabled != 0 makes every following
+ * dg_step / dg_step_noalloc call with nsteps > 0 check the state u and the
+ * residual res for NaN or Inf after its last stage (one extra read of both
+ * field vectors, then a stream synchronisation) and return DG_ERR_NONFINITE
+ * if one is found; 0 (the default) turns the check off, leaving the calls
+ * asynchronous. Needs no mesh. Errors: DG_ERR_ARG (ctx NULL). */
+int dg_set_nonfinite_check(dg_ctx *ctx, int enabled);
 
 /* Same as dg_step, but allocates no device memory in any form: the stage
  * ping-pong buffer is a fixed array inside the library's device image instead
@@ -142,12 +154,13 @@ int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alph
  * variant of the LSERK4 driver.)
  * Limit: 6 * K * Np_pad <= 4,194,304 floats (16 MiB, e.g. N=5 with K <= 12,483);
  * larger meshes get DG_ERR_ARG. Every GPU that loads the library holds the
- * 16 MiB array until the process exits. The first call on a device looks up
- * the array's device address (with that device current); make that first call
- * before any stream capture. All calls share the array and it keeps the last
+ * 16 MiB array until the process exits. Every call looks up the array's
+ * device address in the current context (the first lookup on a device may
+ * load the library's device code there: make the first call before any
+ * stream capture). All calls share the array and it keeps the last
  * call's contents (nothing in it needs to start at zero); calls whose work
- * overlaps on the GPU race on it. u, res, dt, nsteps, alpha and the errors are
- * those of dg_step. */
+ * overlaps on the GPU race on it. u, res, dt, nsteps, alpha, the non-finite
+ * check (dg_set_nonfinite_check) and the errors are those of dg_step. */
 int dg_step_noalloc(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha);
 
 /* Ensembles of independent meshes (uneven sizes, own materials, own time
@@ -243,7 +256,9 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * the choice. Inputs (DEVICE): u0 [6][K][Np_pad], eps (K, or NULL = current),
  * recv (R), Eref [nsteps][3][R] FP32. Outputs: *J (HOST double), dJ_deps
  * (DEVICE, K doubles, reduced in FP64; may be NULL), dJ_du0 (DEVICE field
- * vector; may be NULL). FP32 CUDA-core kernels regardless of the context's
+ * vector; may be NULL). With both gradient outputs NULL only the forward run
+ * and the misfit are computed (no checkpoints, no reverse sweep; segment
+ * length reported as 0). FP32 CUDA-core kernels regardless of the context's
  * precision. Device memory: about (nsteps/ckpt_every + 7.5 ckpt_every + 8)
  * field vectors. Synchronises. Errors: DG_ERR_ARG (also ckpt_every < 0),
  * DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE. */

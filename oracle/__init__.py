@@ -19,32 +19,49 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_use_omp = False
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _ip64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, IEEE arithmetic, no host-specific flags)."""
-    stale = (not os.path.exists(_OUT)) or force or any(
-        os.path.getmtime(p) > os.path.getmtime(_OUT) for p in (_SRC, _HDR))
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, IEEE arithmetic, no host-specific flags).
+    openmp=True builds the same source with OpenMP (elements of a right-hand
+    side split over threads, per-element arithmetic unchanged) for long
+    reference runs; the default build is single-threaded."""
+    out = _OUT_OMP if openmp else _OUT
+    stale = (not os.path.exists(out)) or force or any(
+        os.path.getmtime(p) > os.path.getmtime(out) for p in (_SRC, _HDR))
     if stale:
-        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-        tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared"]
+                              + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def use_openmp() -> None:
+    """Load the OpenMP build instead of the single-threaded one (call before
+    the first oracle call of the process; the thread count follows
+    OMP_NUM_THREADS)."""
+    global _use_omp
+    with _lock:
+        if _lib is not None and not _use_omp:
+            raise RuntimeError("oracle: the single-threaded build is already loaded")
+        _use_omp = True
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(build(openmp=_use_omp))
             L.or_error.restype = C.c_char_p
             L.or_np.argtypes = [C.c_int]
             L.or_nfp.argtypes = [C.c_int]

@@ -59,6 +59,7 @@ def lib():
             L.dg_sync.argtypes = [vp]
             L.dg_set_wait_limit.argtypes = [vp, C.c_longlong]
             L.dg_step_noalloc.argtypes = [vp, vp, vp, dbl, i32, flt]
+            L.dg_set_nonfinite_check.argtypes = [vp, i32]
             L.dg_rhs_transpose.argtypes = [vp, vp, vp, flt]
             L.dg_ensemble_upload.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
             L.dg_ensemble_layout.argtypes = [vp, C.POINTER(i32), vp]
@@ -181,16 +182,19 @@ class Solver:
                                              _t_ptr(out)))
         return out
 
-    def adjoint(self, u0, recv, Eref, dt: float, nsteps: int, ckpt_every: int = 20, eps=None, alpha: float = 1.0):
+    def adjoint(self, u0, recv, Eref, dt: float, nsteps: int, ckpt_every: int = 20, eps=None, alpha: float = 1.0,
+                gradients: bool = True):
         """Misfit J (float) and its gradients (dJ/deps FP64 [K], dJ/du0 [6][K][Np_pad]).
-        ckpt_every = 0 lets the library choose the segment length from the free device memory."""
+        ckpt_every = 0 lets the library choose the segment length from the free device memory.
+        gradients=False computes J alone (forward run only) and returns (J, None, None)."""
         import torch
         J = C.c_double()
-        g_eps = torch.empty(self.K, dtype=torch.float64, device=u0.device)
-        g_u0 = torch.empty_like(u0)
+        g_eps = torch.empty(self.K, dtype=torch.float64, device=u0.device) if gradients else None
+        g_u0 = torch.empty_like(u0) if gradients else None
         self._check(lib().dg_adjoint_step(self._h, _t_ptr(u0), None if eps is None else _t_ptr(eps), float(dt),
                                           int(nsteps), int(ckpt_every), float(alpha), _t_ptr(recv), recv.numel(),
-                                          _t_ptr(Eref), C.byref(J), _t_ptr(g_eps), _t_ptr(g_u0)))
+                                          _t_ptr(Eref), C.byref(J), None if g_eps is None else _t_ptr(g_eps),
+                                          None if g_u0 is None else _t_ptr(g_u0)))
         return J.value, g_eps, g_u0
 
     def adjoint_segment_steps(self) -> int:
@@ -242,6 +246,10 @@ class Solver:
     def sync(self):
         self._check(lib().dg_sync(self._h))
 
+    def set_nonfinite_check(self, enabled: bool = True):
+        """dg_step checks u and res for NaN/Inf after its last stage (synchronising)."""
+        self._check(lib().dg_set_nonfinite_check(self._h, 1 if enabled else 0))
+
     def set_wait_limit(self, cycles: int):
         """Device-side wait limit in SM cycles (0 = default, about one second)."""
         self._check(lib().dg_set_wait_limit(self._h, int(cycles)))
@@ -254,10 +262,11 @@ class Solver:
 
 class ReceiverMisfit:
     """torch.autograd.Function: J(u0, eps) = sum over steps and receivers of
-    |E - E_ref|^2 for an LSERK4 run. The forward pass calls dg_adjoint_step,
-    which returns the misfit together with its exact discrete gradients (the
-    library's hand-written adjoint); backward scales the saved gradients by the
-    incoming gradient of J."""
+    |E - E_ref|^2 for an LSERK4 run. When u0 or eps requires a gradient the
+    forward pass calls dg_adjoint_step, which returns the misfit together with
+    its exact discrete gradients (the library's hand-written adjoint), and
+    backward scales the saved gradients by the incoming gradient of J;
+    otherwise the forward pass runs the forward sweep alone."""
 
     @staticmethod
     def _fn():
@@ -266,9 +275,11 @@ class ReceiverMisfit:
         class _Misfit(torch.autograd.Function):
             @staticmethod
             def forward(ctx, u0, eps, solver, recv, Eref, dt, nsteps, ckpt_every, alpha):
-                J, g_eps, g_u0 = solver.adjoint(u0.contiguous(), recv, Eref, dt, nsteps, ckpt_every,
-                                                eps=eps.contiguous(), alpha=alpha)
-                ctx.save_for_backward(g_u0, g_eps)
+                want = bool(ctx.needs_input_grad[0] or ctx.needs_input_grad[1])
+                J, g_eps, g_u0 = solver.adjoint(u0.detach().contiguous(), recv, Eref, dt, nsteps, ckpt_every,
+                                                eps=eps.detach().contiguous(), alpha=alpha, gradients=want)
+                if want:
+                    ctx.save_for_backward(g_u0, g_eps)
                 return torch.tensor(J, dtype=torch.float64, device=u0.device)
 
             @staticmethod

@@ -681,6 +681,44 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   cudaStream_t s = ctx->stream;
   AdjWorkspace &ws = workspace(ctx);
 
+  if (!dJ_deps && !dJ_du0) {
+    // misfit only: the forward run and the receiver residuals, no checkpoints
+    // and no reverse sweep
+    float *u = ws.get<float>(0, fl), *nxt = ws.get<float>(1, fl), *res = ws.get<float>(2, fl);
+    float *resid = ws.get<float>(6, size_t(nsteps) * 3 * R);
+    double *Jd = ws.get<double>(7, 1);
+    if (!u || !nxt || !res || !resid || !Jd) return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed");
+    cudaError_t e = cudaMemcpyAsync(u, u0, fl * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(res, 0, fl * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Jd, 0, sizeof(double), s);
+    StageArgs sa = stage_base(ctx, alpha, dt);
+    sa.res = res;
+    const unsigned rb = unsigned((3 * R + 255) / 256);
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+        sa.u = u;
+        sa.u_out = nxt;
+        sa.rk_a = float(kLserkA[st]);
+        sa.rk_b = float(kLserkB[st]);
+        e = launch_stage_simt(ctx->N, MODE_LSERK, sa, s);
+        std::swap(u, nxt);
+      }
+      if (e == cudaSuccess) {
+        k_recv_residual<<<rb, 256, 0, s>>>(u, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R,
+                                           Eref + int64_t(n) * 3 * R, resid + int64_t(n) * 3 * R, Jd);
+        e = cudaGetLastError();
+      }
+    }
+    double Jh = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&Jh, Jd, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_adjoint_step: ") + cudaGetErrorString(e));
+    ctx->adj_segment = 0;
+    if (J) *J = Jh;
+    if (!std::isfinite(Jh)) return fail(ctx, DG_ERR_NONFINITE, "dg_adjoint_step: misfit is not finite");
+    return DG_OK;
+  }
+
   // steps per segment: given, or (0) as many as half of the device memory
   // that is free or already held for segment storage can take
   int C = ckpt_every;

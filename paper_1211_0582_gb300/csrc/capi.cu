@@ -353,28 +353,12 @@ int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alph
   if (!aligned16(u) || !aligned16(res)) return set_err(ctx, DG_ERR_ARG, "dg_step: fields must be 16-byte aligned");
   if (overlap(u, res, field_bytes(ctx))) return set_err(ctx, DG_ERR_ARG, "dg_step: u and res overlap");
   if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(alpha)) return set_err(ctx, DG_ERR_ARG, "dg_step: bad dt/nsteps/alpha");
-  StageArgs a = base_args(ctx);
-  a.alpha = alpha;
-  a.dt = float(dt);
-  a.res = res;
-  const float *cur = u;
-  float *nxt = ctx->d_scratch;
-  for (int step = 0; step < nsteps; ++step)
-    for (int st = 0; st < 5; ++st) {
-      a.u = cur;
-      a.u_out = nxt;
-      a.rk_a = float(kLserkA[st]);
-      a.rk_b = float(kLserkB[st]);
-      cudaError_t e = launch_stage(ctx, MODE_LSERK, a);
-      if (e != cudaSuccess) return cuda_err(ctx, e, "dg_step");
-      float *prev = const_cast<float *>(cur);
-      cur = nxt;
-      nxt = prev;
-    }
-  if (cur != u) {
-    cudaError_t e = cudaMemcpyAsync(u, cur, field_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "dg_step");
-  }
+  return lserk_drive(ctx, u, res, dt, nsteps, alpha, ctx->d_scratch, "dg_step");
+}
+
+int dg_set_nonfinite_check(dg_ctx *ctx, int enabled) {
+  if (!ctx) return DG_ERR_ARG;
+  ctx->check_nonfinite = enabled ? 1 : 0;
   return DG_OK;
 }
 
@@ -423,6 +407,47 @@ int dg_energy(dg_ctx *ctx, const float *u, double *E_out) {
 } // extern "C"
 
 namespace dgmx {
+
+int lserk_drive(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha, float *pingpong,
+                const char *who) {
+  StageArgs a = base_args(ctx);
+  a.alpha = alpha;
+  a.dt = float(dt);
+  a.res = res;
+  const float *cur = u;
+  float *nxt = pingpong;
+  for (int step = 0; step < nsteps; ++step)
+    for (int st = 0; st < 5; ++st) {
+      a.u = cur;
+      a.u_out = nxt;
+      a.rk_a = float(kLserkA[st]);
+      a.rk_b = float(kLserkB[st]);
+      cudaError_t e = launch_stage(ctx, MODE_LSERK, a);
+      if (e != cudaSuccess) return cuda_err(ctx, e, who);
+      float *prev = const_cast<float *>(cur);
+      cur = nxt;
+      nxt = prev;
+    }
+  if (cur != u) {
+    cudaError_t e = cudaMemcpyAsync(u, cur, field_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, who);
+  }
+  if (ctx->check_nonfinite && nsteps > 0) {
+    int *flag = ctx->d_flag + 3;
+    int bad = 0;
+    const int64_t n = int64_t(field_bytes(ctx) / sizeof(float));
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = launch_nonfinite_check(u, n, flag, ctx->stream);
+    if (e == cudaSuccess) e = launch_nonfinite_check(res, n, flag, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, who);
+    if (bad)
+      return set_err(ctx, DG_ERR_NONFINITE,
+                     std::string(who) + ": the state or the residual holds a NaN or an infinity after the last stage");
+  }
+  return DG_OK;
+}
 
 cudaError_t launch_stage_simt(int N, int mode, const StageArgs &a, cudaStream_t s) {
   switch (N) {

@@ -71,6 +71,17 @@ cudaError_t ensemble_reset_barrier(dg_ctx *ctx);
 void ensemble_drop_graph(dg_ctx *ctx);
 cudaError_t launch_energy(int N, int64_t K, int Npad, const float *u, const float *geo, const double *M,
                           double *out, cudaStream_t s);
+// Sets *flag (device int) to 1 if any of the nfloats values at u (16-byte
+// aligned, nfloats a multiple of 4) is a NaN or an infinity; never clears it.
+cudaError_t launch_nonfinite_check(const float *u, int64_t nfloats, int *flag, cudaStream_t s);
+// The LSERK4 driver shared by dg_step and dg_step_noalloc: nsteps steps of the
+// fused stage kernel on ctx's stream with the stage ping-pong through
+// `pingpong` (a device field vector distinct from u and res), the final state
+// copied back into u, and, when ctx->check_nonfinite is set, the non-finite
+// check of u and res (synchronising). `who` names the entry point in errors.
+// Arguments are validated by the caller. Returns a dg_status.
+int lserk_drive(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha, float *pingpong,
+                const char *who);
 
 // Five-stage fourth-order low-storage Runge-Kutta coefficients (Carpenter &
 // Kennedy 1994, 2N storage).
@@ -136,6 +147,7 @@ struct dg_ctx {
   double *d_red = nullptr;     // reduction outputs
   int *d_flag = nullptr;
   long long wait_limit = 0;    // device-wait limit in SM cycles for the stage kernels (0 = default)
+  int check_nonfinite = 0;     // dg_step: check u and res for NaN/Inf after the last stage
   void *tc = nullptr;          // tensor-core operator buffers (precision != DG_FP32)
   void *ens = nullptr;         // ensemble state (dg_ensemble_upload)
   void *adj = nullptr;         // adjoint / receiver-trace work buffers (grown on demand)

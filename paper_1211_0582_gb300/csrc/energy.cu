@@ -71,7 +71,29 @@ __global__ void __launch_bounds__(kEnergyThreads)
   if ((tid & 31) == 0 && total != 0.0) atomicAdd(out, total);
 }
 
+// Sets *flag to 1 if any of the n4 float4 values holds a NaN or an infinity.
+__global__ void __launch_bounds__(256) k_nonfinite(const float4 *__restrict__ u, int64_t n4, int *flag) {
+  bool bad = false;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+    const float4 v = __ldg(u + i);
+    bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
+}
+
 } // namespace
+
+cudaError_t launch_nonfinite_check(const float *u, int64_t nfloats, int *flag, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t n4 = nfloats / 4;
+  int64_t blocks = (n4 + 255) / 256;
+  if (blocks > int64_t(sms) * 8) blocks = int64_t(sms) * 8;
+  if (blocks < 1) blocks = 1;
+  k_nonfinite<<<unsigned(blocks), 256, 0, s>>>(reinterpret_cast<const float4 *>(u), n4, flag);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_energy(int N, int64_t K, int Npad, const float *u, const float *geo, const double *M, double *out,
                           cudaStream_t s) {

@@ -16,7 +16,6 @@
 // entry it later reads, so nothing needs clearing. Calls whose work overlaps on
 // the GPU (two streams, two contexts) race on the array.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/dgmx.h"
@@ -27,28 +26,18 @@ namespace dgmx {
 namespace {
 
 constexpr size_t kNoAllocFloats = size_t(4) << 20; // 16 MiB of FP32
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float g_stage_scratch[kNoAllocFloats];
 
-std::mutex g_mu;
-float *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the array on the current device, looked up once per
-// device (the name is a host-side stand-in and must never reach a kernel).
+// Device address of the array in the current context. The array's name is a
+// host-side stand-in and must never reach a kernel; its device address is
+// looked up on every call (cheap next to the stage launches), so a device
+// reset or another context on the same device never sees a stale address.
 cudaError_t scratch_for_current_device(float **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_stage_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_stage_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<float *>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<float *>(p);
   return cudaSuccess;
 }
 
@@ -82,39 +71,5 @@ extern "C" int dg_step_noalloc(dg_ctx *ctx, float *u, float *res, double dt, int
   float *scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_step_noalloc: ") + cudaGetErrorString(e));
-
-  StageArgs a{};
-  a.geo = ctx->d_geo;
-  a.fgeo = ctx->d_fgeo;
-  a.fconn = ctx->d_fconn;
-  a.fmat = ctx->d_fmat;
-  a.wait_limit = ctx->wait_limit;
-  a.DT = ctx->d_DT;
-  a.LT = ctx->d_LT;
-  a.fmask = ctx->d_tab;
-  a.nbrtab = ctx->d_tab + 4 * ctx->ops.Nfp;
-  a.K = ctx->K;
-  a.alpha = alpha;
-  a.dt = float(dt);
-  a.res = res;
-  const float *cur = u;
-  float *nxt = scratch;
-  for (int step = 0; step < nsteps; ++step)
-    for (int st = 0; st < 5; ++st) {
-      a.u = cur;
-      a.u_out = nxt;
-      a.rk_a = float(kLserkA[st]);
-      a.rk_b = float(kLserkB[st]);
-      e = ctx->precision == DG_FP32 ? launch_stage_simt(ctx->N, MODE_LSERK, a, ctx->stream)
-                                    : launch_stage_tc(ctx, MODE_LSERK, a);
-      if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_step_noalloc: ") + cudaGetErrorString(e));
-      float *prev = const_cast<float *>(cur);
-      cur = nxt;
-      nxt = prev;
-    }
-  if (cur != u) {
-    e = cudaMemcpyAsync(u, cur, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
-    if (e != cudaSuccess) return fail(ctx, DG_ERR_CUDA, std::string("dg_step_noalloc: ") + cudaGetErrorString(e));
-  }
-  return DG_OK;
+  return lserk_drive(ctx, u, res, dt, nsteps, alpha, scratch, "dg_step_noalloc");
 }

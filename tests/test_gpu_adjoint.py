@@ -81,6 +81,35 @@ def test_adjoint_gradient_matches_oracle_discrete_adjoint():
     assert rel(s.from_device(g_u0), go_u0) < 1e-4
 
 
+def test_receiver_misfit_autograd_function():
+    # torch.autograd.Function over dg_adjoint_step: backward gives the adjoint's
+    # gradients scaled by dJ (here 1), equal to the oracle's discrete adjoint;
+    # a forward pass with no input requiring a gradient runs the forward sweep
+    # alone and gives the same misfit
+    N, n, steps, ck = 4, 6, 12, 5
+    s, m, eps, eps_t, u0, u0d, recv, rd, Eref, dt = _misfit_problem(N, n, steps)
+    epsd = torch.as_tensor(eps, device="cuda")
+    J_ref, ge_ref, gu_ref = s.adjoint(u0d, rd, Eref, dt, steps, ck, eps=epsd)
+    u_in = u0d.clone().requires_grad_(True)
+    e_in = epsd.clone().requires_grad_(True)
+    J = dg.ReceiverMisfit.apply(u_in, e_in, s, rd, Eref, dt, steps, ck)
+    assert J.dtype == torch.float64 and abs(float(J) - J_ref) <= 1e-12 * J_ref
+    (3.0 * J).backward()
+    assert torch.allclose(u_in.grad, 3.0 * gu_ref, rtol=1e-6, atol=1e-12 * float(gu_ref.abs().max()))
+    assert torch.allclose(e_in.grad.double(), 3.0 * ge_ref, rtol=1e-6, atol=1e-12 * float(ge_ref.abs().max()))
+    Jo, go_eps, go_u0 = m.misfit_gradient(u0, dt, steps, recv, Eref.double().cpu().numpy(),
+                                          eps=eps.astype(np.float64))
+    assert rel(e_in.grad.double().cpu().numpy() / 3.0, go_eps) < 1e-4
+    assert rel(s.from_device(u_in.grad) / 3.0, go_u0) < 1e-4
+    with torch.no_grad():
+        J0 = dg.ReceiverMisfit.apply(u0d, epsd, s, rd, Eref, dt, steps, ck)
+    assert s.adjoint_segment_steps() == 0  # no checkpoints: the forward sweep alone
+    assert abs(float(J0) - J_ref) <= 1e-6 * J_ref
+    J1 = dg.ReceiverMisfit.apply(u0d, epsd, s, rd, Eref, dt, steps, ck)  # inputs without requires_grad
+    assert not J1.requires_grad and s.adjoint_segment_steps() == 0
+    assert abs(float(J1) - Jo) < 1e-5 * Jo
+
+
 def test_adjoint_segmentations_agree():
     # 4^3 x 6 tets at N=4, 12 steps: one-step segments (everything recomputed),
     # segments of 5 aligned to the end (2 + 5 + 5, the last one stored by the

@@ -81,3 +81,30 @@ def test_ensemble_grid_barrier_timeout_reports_and_recovers(N, precision):
     ens.sync()
     assert np.array_equal(ens.from_device(u), ref)
     assert off[-1] == u.shape[1]
+
+
+@pytest.mark.parametrize("N,precision", [(3, "fp32"), (4, "fp16x3"), (7, "bf16x3")])
+def test_step_reports_nonfinite_state(N, precision):
+    # a NaN planted in the initial state (on the host) spreads through the
+    # stages; with the check on, dg_step returns DG_ERR_NONFINITE, with it off
+    # it returns DG_OK; a clean state passes the check
+    VX, VY, VZ, EToV = W.kuhn_cube(3, jitter=0.1, seed=1)
+    s = dg.Solver(N, precision=precision).upload(VX, VY, VZ, EToV)
+    x, y, z = s.node_coords()
+    u0 = W.cavity_mode(x, y, z, 0.0)
+    dt = 0.5 / 3 / N ** 2
+    s.set_nonfinite_check(True)
+    u, r = s.to_device(u0), s.zeros()
+    s.step(u, r, dt, 2)
+    assert torch.isfinite(u).all()
+    bad = u0.copy()
+    bad[4, 17, 3] = np.nan
+    u, r = s.to_device(bad), s.zeros()
+    with pytest.raises(dg.DGError) as ei:
+        s.step(u, r, dt, 1)
+    assert ei.value.code == -4 and "NaN" in str(ei.value)
+    s.set_nonfinite_check(False)
+    u, r = s.to_device(bad), s.zeros()
+    s.step(u, r, dt, 1)
+    s.sync()
+    assert not torch.isfinite(u).all()

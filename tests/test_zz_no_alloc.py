@@ -52,3 +52,40 @@ def test_noalloc_rejects_meshes_beyond_its_fixed_scratch():
     u, r = s.zeros(), s.zeros()
     assert _noalloc(s, u, r, 1e-3, 1) == -1
     assert b"16 MiB" in dg.lib().dg_last_error(s._h)
+
+
+def test_noalloc_allocates_nothing_and_ignores_stale_scratch():
+    # The fixed array is shared and keeps the previous call's contents: a call
+    # that fills it with non-finite values (an N=2 mesh whose state holds NaN
+    # and Inf) must not leak into a later N=4 run, whose padded rows (Np=35,
+    # Np_pad=36) differ from N=2's. And a call performs no device allocation:
+    # the free device memory is unchanged across calls on a new mesh and order
+    # (the first call of the process may load the library's device code).
+    import torch
+    n = 6
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    s2 = dg.Solver(2).upload(VX, VY, VZ, EToV)
+    x, y, z = s2.node_coords()
+    poison = W.cavity_mode(x, y, z, 0.0)
+    poison[1] = np.nan
+    poison[4] = np.inf
+    u2, r2 = s2.to_device(poison), s2.zeros()
+    assert _noalloc(s2, u2, r2, 1e-3, 3) == 0, dg.lib().dg_last_error(s2._h)
+    s2.sync()
+    assert not torch.isfinite(u2).all()
+    s4 = dg.Solver(4, precision="fp16x3").upload(VX, VY, VZ, EToV, eps=W.element_eps(EToV.shape[0], seed=2))
+    x, y, z = s4.node_coords()
+    u0 = W.cavity_mode(x, y, z, 0.0)
+    dt = 0.5 / n / 16
+    ua, ra = s4.to_device(u0), s4.zeros()
+    ub, rb = s4.to_device(u0), s4.zeros()
+    s4.step(ua, ra, dt, 3)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert _noalloc(s4, ub, rb, dt, 3) == 0, dg.lib().dg_last_error(s4._h)
+    s4.sync()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert torch.isfinite(ub).all()
+    a, b = s4.from_device(ua), s4.from_device(ub)
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a)

@@ -127,15 +127,16 @@ def cavity_mode(x, y, z, t: float, a=CAVITY_AMPLITUDE):
     return np.stack([Ex, Ey, Ez, Hx, Hy, Hz])
 
 
-def gaussian_pulse(x, y, z, seed: int = 7, index: int = 0):
+def gaussian_pulse(x, y, z, seed: int = 7, index: int = 0, width: float | None = None):
     """Divergence-free pulse E0 = curl(p g), g = exp(-|x-c|^2 / w^2), H0 = 0.
 
     c in [0.3, 0.7]^3, w in [0.05, 0.15], p a unit vector; all drawn from
-    splitmix64(seed) at offset 7*index. curl(p g) = grad(g) x p.
+    splitmix64(seed) at offset 7*index (width, if given, replaces the drawn w).
+    curl(p g) = grad(g) x p.
     """
     U = uniform(seed, 7 * (index + 1))[7 * index:]
     c = 0.3 + 0.4 * U[0:3]
-    w = 0.05 + 0.10 * U[3]
+    w = 0.05 + 0.10 * U[3] if width is None else float(width)
     p = 2.0 * U[4:7] - 1.0
     p = p / np.linalg.norm(p)
     dx, dy, dz = x - c[0], y - c[1], z - c[2]
