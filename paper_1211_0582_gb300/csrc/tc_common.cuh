@@ -21,6 +21,7 @@ __host__ __device__ constexpr int tmem_cols(int x) {
 struct TcState {
   void *d_ops = nullptr;
   int sms = 0;
+  int form = 1; // N <= 5 stage: 1 single-tile resident form (default), 0 warp-specialised
 };
 
 // hi/lo split of two FP32 values into packed 16-bit pairs (x0 in the low half).

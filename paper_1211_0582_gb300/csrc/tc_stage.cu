@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -90,8 +91,9 @@ struct TC {
   static constexpr int K2 = rup(4 * NFPE, 16);   // GEMM2 reduction length (face-node columns)
   static constexpr int N2 = NB;           // GEMM2 output columns
   static constexpr int CA = rup(N1 + N2, 32);  // TMEM column of the A1 operand (hi, then lo): after V and S
-  static constexpr int TCOLS = tmem_cols(CA + K1);
-  static_assert(CA + K1 <= 512, "accumulators and the A1 operand exceed tensor memory");
+  static constexpr int CU = CA + K1;           // TMEM columns of the tile's fields (FP32) for the update
+  static constexpr int TCOLS = tmem_cols(CU + K1);
+  static_assert(CU + K1 <= 512, "accumulators, the A1 operand and the fields exceed tensor memory");
   static_assert(K1 <= 16 * (kThreads / 128), "the field split covers 16 K values per warp, four warps per quarter");
   static constexpr int FS = kTileElems * NPP + 4; // padded field-block stride of the staged tiles
   // A2 in the K-major core-matrix layout with padded strides: 144 bytes
@@ -105,20 +107,26 @@ struct TC {
   static __device__ __forceinline__ uint32_t a2_offset(uint32_t row, uint32_t k) {
     return (row >> 3) * uint32_t(A2SBO) + (k >> 3) * uint32_t(A2LBO) + (row & 7u) * 16u + (k & 7u) * 2u;
   }
-  // fp32 [6][FS]: the next tile's fields, staged by bulk copies (the split
-  // fields, GEMM1's A operand, live in tensor memory from column CA on)
-  static constexpr int STB = rup(6 * FS * 4, 128);
-  static constexpr int OFF_STAGE = 0;
   // A2 hi/lo; between the lifting GEMM of one tile and the flux split of the
   // next, the same bytes hold the tile's results [2][6][FS] for the bulk stores
   static constexpr int OUTB = 12 * FS * 4;
   static constexpr int A2R = 2 * A2B > OUTB ? 2 * A2B : OUTB;
-  static constexpr int OFF_A2H = OFF_STAGE + STB, OFF_A2L = OFF_A2H + A2B;
+  static constexpr int OFF_A2H = 0, OFF_A2L = OFF_A2H + A2B;
   static constexpr int OFF_B1H = OFF_A2H + A2R, OFF_B1L = OFF_B1H + B1B;
   static constexpr int OFF_B2H = OFF_B1L + B1B, OFF_B2L = OFF_B2H + B2B;
   static constexpr int OPS_BYTES = 2 * B1B + 2 * B2B; // contiguous from OFF_B1H
-  static constexpr int OFF_U = OFF_B2L + B2B;          // fp32 [6][FS]: fields of the tile
-  static constexpr int OFF_RES = OFF_U + 6 * FS * 4;   // fp32 [6][FS]: residual of the tile
+  // fp32 [6][FS] fields of the tile, staged by bulk copies (the split
+  // fields, GEMM1's A operand, and the fields themselves for the update live
+  // in tensor memory). N <= 4: two such buffers by tile parity, the next
+  // tile's fields staged during the flux phase; N = 5: one buffer, the next
+  // tile staged once the flux phase is over. The single buffer keeps the
+  // shared memory under the 196 KB carveout: the larger L1 that leaves holds
+  // more of the neighbour traces (measured faster at N = 5; at N <= 4 the
+  // second buffer's earlier staging wins and the carveout is smaller anyway).
+  static constexpr bool PINGPONG = N <= 4;
+  static constexpr int UB = rup(6 * FS * 4, 128);
+  static constexpr int OFF_U = OFF_B2L + B2B;
+  static constexpr int OFF_RES = OFF_U + (PINGPONG ? 2 : 1) * UB; // fp32 [6][FS]: residual of the tile
   // face and element data of a tile, two slots (current tile, next tile):
   // float4 fgeo[80] {n, Fscale}, float4 fmat[80] flux weights,
   // float geo[20][G_STRIDE], int2 fconn[80]
@@ -126,9 +134,10 @@ struct TC {
   static constexpr int FCONN = FELEM + kTileElems * G_STRIDE * 4, FSLOT = FCONN + kTileElems * 4 * 8;
   static constexpr int OFF_FACE = OFF_RES + 6 * FS * 4;
   static constexpr int OFF_TAB = OFF_FACE + 2 * FSLOT;
-  // [128] A1 row inverse scales, [8] A2 field-type maxima, [128] A1 row maxima
+  // [128] A1 row inverse scales, [2 * kTileElems] A2 largest exponents per
+  // element and field type (E, H), [128] A1 row maxima
   static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16);
-  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32 + 128 * 4; // mbarriers: GEMM1, GEMM2, residual, next tile; TMEM slot
+  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 2 * kTileElems * 4 + 128 * 4; // mbarriers: GEMM1, GEMM2, residual, next tile; TMEM slot
   static constexpr int SMEM = OFF_BAR + 48;
 };
 
@@ -197,15 +206,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   using T = TC<N>;
   constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, FS = T::FS;
   extern __shared__ __align__(1024) uint8_t smem[];
-  float *s_u = reinterpret_cast<float *>(smem + T::OFF_U);       // [6][FS]: fields of the tile
+  float *s_ub = reinterpret_cast<float *>(smem + T::OFF_U);      // [2][6][FS]: fields by tile parity
   float *s_res = reinterpret_cast<float *>(smem + T::OFF_RES);   // [6][FS]: residual of the tile
-  float *s_stage = reinterpret_cast<float *>(smem + T::OFF_STAGE); // [6][FS]: next tile's fields
   float *s_out = reinterpret_cast<float *>(smem + T::OFF_A2H);   // [2][6][FS]: results (in A2)
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
   float *s_inv1 = reinterpret_cast<float *>(smem + T::OFF_MX);  // A1 row inverse scales (compact rows)
-  uint32_t *s_mx2 = reinterpret_cast<uint32_t *>(s_inv1 + 128); // A2 maxima of the E and H fluxes (float bits)
-  uint32_t *s_rowmx = s_mx2 + 8; // A1 row maxima (float bits), FP16
+  uint32_t *s_ex2 = reinterpret_cast<uint32_t *>(s_inv1 + 128); // A2 largest exponent per element and field type
+  uint32_t *s_rowmx = s_ex2 + 2 * kTileElems; // A1 row maxima (float bits), FP16
   uint64_t *bar1 = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // GEMM1 done
   uint64_t *bar2 = bar1 + 1;                                        // GEMM2 (and all earlier MMAs) done
   uint64_t *barR = bar1 + 2;                                        // residual tile landed
@@ -227,15 +235,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the first LSERK4 stage has a = 0: the residual it overwrites is not read
   bool read_res = MODE == MODE_LSERK && a.rk_a != 0.f;
 
-  // fields of tile t into the staging buffer, its face and element data into
-  // a slot (one thread; completes on barU)
+  // fields of tile t into the tile buffer, its face and element data into a
+  // slot (one thread; completes on barU)
   auto stage_tile = [&](int t, int slot) {
     const int64_t kb = tm.start(t);
     const uint32_t nb = uint32_t(tm.size(t, a.K));
     const uint32_t rb = nb * NPP * 4;
     uint8_t *fs = smem + T::OFF_FACE + slot * T::FSLOT;
+    float *su = s_ub + (T::PINGPONG ? slot : 0) * (T::UB / 4);
     umma::mbar_arrive_expect_tx(barU, 6u * rb + nb * (64u + 64u + G_STRIDE * 4u + 32u));
-    for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_stage + f * FS, a.u + f * KN + kb * NPP, rb, barU);
+    for (int f = 0; f < 6; ++f) umma::bulk_g2s(su + f * FS, a.u + f * KN + kb * NPP, rb, barU);
     umma::bulk_g2s(fs + T::FGEO, a.fgeo + kb * 4, nb * 64u, barU);
     umma::bulk_g2s(fs + T::FMAT, a.fmat + kb * 4, nb * 64u, barU);
     umma::bulk_g2s(fs + T::FELEM, a.geo + kb * G_STRIDE, nb * G_STRIDE * 4u, barU);
@@ -243,13 +252,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
 
   // ---- one-time setup
-  for (int i = tid; i < (T::STB + T::A2R) / 16; i += kThreads)
-    reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < T::A2R / 16; i += kThreads)
+    reinterpret_cast<uint4 *>(smem + T::OFF_A2H)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < T::OPS_BYTES / 16; i += kThreads)
     reinterpret_cast<uint4 *>(smem + T::OFF_B1H)[i] = __ldg(ops + i);
   for (int i = tid; i < NFF + kConnKinds * NFP; i += kThreads)
     s_fm[i] = i < NFF ? a.fmask[i] : a.nbrtab[i - NFF];
-  for (int i = tid; i < 264; i += kThreads) s_inv1[i] = i < 128 ? 1.f : 0.f;
+  for (int i = tid; i < 256 + 2 * kTileElems; i += kThreads) s_inv1[i] = i < 128 ? 1.f : 0.f;
   if (tid == 0) {
     umma::mbar_init(bar1, 1);
     umma::mbar_init(bar2, 1);
@@ -339,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float4 *s_fmat = reinterpret_cast<const float4 *>(fslot + T::FMAT);
       const float *s_geo = reinterpret_cast<const float *>(fslot + T::FELEM);
       const int2 *s_fconn = reinterpret_cast<const int2 *>(fslot + T::FCONN);
+      const float *s_u = s_ub + (T::PINGPONG ? slot : 0) * (T::UB / 4); // this tile's fields
 
       // ---- 1. the staged fields into registers; once the previous tile's bulk
       // stores have read shared memory, the residual copy starts
@@ -350,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int k = kb1 + 4 * j;
         v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (a1_part && cr1 >= 0 && k < NPP && e1 < ne) {
-          v[j] = *reinterpret_cast<const float4 *>(s_stage + f1 * FS + e1 * NPP + k);
+          v[j] = *reinterpret_cast<const float4 *>(s_u + f1 * FS + e1 * NPP + k);
           if (k + 3 >= NP) {
             if (k + 0 >= NP) v[j].x = 0.f;
             if (k + 1 >= NP) v[j].y = 0.f;
@@ -381,11 +391,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (cr1 >= 0) row_scale(__uint_as_float(s_rowmx[r1]), sc1, inv1r);
           if (p1 == 0 && cr1 >= 0) s_inv1[cr1] = inv1r;
         }
-        uint32_t hi[8], lo[8];
+        uint32_t hi[8], lo[8], raw[16];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int k = kb1 + 4 * j;
-          if (cr1 >= 0 && k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[j];
+          raw[4 * j] = __float_as_uint(v[j].x), raw[4 * j + 1] = __float_as_uint(v[j].y);
+          raw[4 * j + 2] = __float_as_uint(v[j].z), raw[4 * j + 3] = __float_as_uint(v[j].w);
           float4 w = v[j];
           if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
           split2<BF16>(w.x, w.y, hi[2 * j], lo[2 * j]);
@@ -393,6 +403,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         umma::tmem_st8(a1_hi + a1_st, hi);
         umma::tmem_st8(a1_lo + a1_st, lo);
+        // the fields themselves, for the update, in tensor memory from CU on
+        umma::tmem_st8(tmem + uint32_t(T::CU) + (uint32_t(q1 * 32) << 16) + uint32_t(kb1), raw);
+        umma::tmem_st8(tmem + uint32_t(T::CU) + (uint32_t(q1 * 32) << 16) + uint32_t(kb1 + 8), raw + 8);
         umma::tmem_wait_st();
       }
       umma::fence_before_sync();
@@ -446,7 +459,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       float fl[R2][2][6];
-      uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
       for (int s = 0; s < R2; ++s) {
         const int blk = warp + 16 * s;
@@ -480,49 +492,66 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if constexpr (!BF16) {
+          // FP16: one scale per element and field type (E, H), from the
+          // largest exponent over the element's fluxes of that type: the
+          // exponents of the lane's E and H fluxes packed into one word, the
+          // bytewise maximum over the 8 lanes of the element, one
+          // shared-memory maximum per element, type and block
+          if (blk < NBLK) { // warp-uniform
+            uint32_t mE = 0u, mH = 0u;
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][h][c])));
+              for (int c = 0; c < 3; ++c) {
+                mE = max(mE, __float_as_uint(fabsf(fl[s][h][c])));
+                mH = max(mH, __float_as_uint(fabsf(fl[s][h][c + 3])));
+              }
+            uint32_t wx = ((mE >> 23) & 0xFFu) | (((mH >> 23) & 0xFFu) << 8);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) wx = __vmaxu4(wx, __shfl_xor_sync(0xffffffffu, wx, o));
+            if (kp == 0 && e < kTileElems) {
+              atomicMax(s_ex2 + 2 * e, wx & 0xFFu);
+              atomicMax(s_ex2 + 2 * e + 1, (wx >> 8) & 0xFFu);
+            }
+          }
         }
       }
-      // the next tile's fields and face data are staged (issued here rather
-      // than right after step 1: earlier, the copies compete with GEMM1 and the
-      // flux phase for shared memory, which measured slower)
-      if (stager) {
+      // the next tile's fields and face data: into the other slot during the
+      // flux phase (N <= 4), or over this tile's once every thread is done
+      // with them (N = 5)
+      if (T::PINGPONG && stager) {
         const bool more = tile + int(gridDim.x) < tm.ntiles;
         if (more) stage_tile(tile + gridDim.x, slot ^ 1);
         *s_staged = more ? 1 : 0;
       }
-      if constexpr (!BF16) {
-        // one FP16 scale per field type (E, H) of the tile: |x| as float
-        // bits orders like |x|
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const uint32_t m = __reduce_max_sync(0xffffffffu, max(fmx[3 * g], max(fmx[3 * g + 1], fmx[3 * g + 2])));
-          if (lane == 0) atomicMax(s_mx2 + g, m);
-        }
-      }
+      // this tile's fields, face and element data are rewritten by the staging
+      umma::fence_proxy_async();
       // the previous tile's bulk stores must have read the A2 bytes
       if (storer) umma::bulk_wait_read_all();
       __syncthreads();
+      if (!T::PINGPONG && stager) {
+        const bool more = tile + int(gridDim.x) < tm.ntiles;
+        if (more) stage_tile(tile + gridDim.x, slot ^ 1);
+        *s_staged = more ? 1 : 0;
+      }
 
       // ---- 5. split the face fluxes into the A2 operand
       {
-        float sc2[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          sc2[c] = 1.f;
-          if constexpr (!BF16) {
-            float inv;
-            row_scale(__uint_as_float(s_mx2[c / 3]), sc2[c], inv);
-          }
-        }
 #pragma unroll
         for (int s = 0; s < R2; ++s) {
           const int blk = warp + 16 * s;
           const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
           if (blk < NBLK) {
+            float sc2[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sc2[c] = 1.f;
+            if constexpr (!BF16) {
+              float inv;
+              row_scale(__uint_as_float(s_ex2[2 * e] << 23), sc2[0], inv);
+              row_scale(__uint_as_float(s_ex2[2 * e + 1] << 23), sc2[3], inv);
+              sc2[1] = sc2[2] = sc2[0];
+              sc2[4] = sc2[5] = sc2[3];
+            }
             // the six rows of element e lie in one TMEM lane quarter; a column
             // pair is one 32-bit word of a core-matrix row
             const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
@@ -564,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float sc;
         const float inv1 = s_inv1[lane_used ? ridx : 0];
         g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
-        row_scale(__uint_as_float(s_mx2[fld / 3]), sc, inv2);
+        row_scale(__uint_as_float(s_ex2[lane_used ? 2 * e_loc + fld / 3 : 0] << 23), sc, inv2);
       }
       ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
       umma::fence_after_sync();
@@ -616,10 +645,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ch = ch0 + c;
         if (ch >= ch1) break;
         const int i0 = ch * 8;
-        float lf[8];
+        float lf[8], uold[8];
         umma::tmem_ld8(lane_taddr + uint32_t(T::N1 + i0), lf);
+        if (MODE != MODE_RHS) umma::tmem_ld8(lane_taddr + uint32_t(T::CU + i0), uold);
         umma::tmem_wait_ld();
         umma::reg_fence8(lf);
+        if (MODE != MODE_RHS) umma::reg_fence8(uold);
         if (live) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -634,8 +665,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               } else {
                 const float4 rs = read_res ? *reinterpret_cast<const float4 *>(s_res + soff + i)
                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 uo = *reinterpret_cast<const float4 *>(s_u + soff + i);
-                const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
+                const float rsv[4] = {rs.x, rs.y, rs.z, rs.w};
+                const float uov[4] = {uold[4 * h], uold[4 * h + 1], uold[4 * h + 2], uold[4 * h + 3]};
                 float nr[4], nu[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -666,7 +697,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         umma::bulk_commit();
       }
-      if (!BF16 && tid < 8) s_mx2[tid] = 0u;
+      if (!BF16 && tid < 2 * kTileElems) s_ex2[tid] = 0u;
       phase ^= 1u;
       if (read_res) rphase ^= 1u;
     }
@@ -687,6 +718,661 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (storer) umma::bulk_wait_all();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, T::TCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised form of one stage (N <= 5): two tiles in flight per SM.
+//
+// The single-tile kernel above runs the phases of a tile (field split, flux,
+// flux split, volume terms, epilogue) one after another with the whole CTA,
+// and most of them wait on latency (L2 gathers, shared memory, barriers).
+// Here the CTA is split into roles that work on consecutive tiles at once:
+//   warps 0-7   (E) volume terms and epilogue of tile t, and the field split
+//               (GEMM1's A operand, in tensor memory) of tile t+1; two warps
+//               per TMEM lane quarter, each with half of the columns;
+//   warps 8-15  (F) upwind flux of tile t+1 and its split into GEMM2's A
+//               operand (shared memory);
+//   warp 16     one thread issues the MMAs: GEMM1(t) once E has split tile t
+//               and read V(t-1); GEMM2(t) once F has written A2(t) and E has
+//               read the lifted flux of tile t-2 (two accumulator slots);
+//   warp 17     one thread writes the results of each tile back with bulk
+//               stores (the epilogue leaves them in place of the tile's
+//               residual and fields in shared memory) and stages the fields,
+//               face data and residual of the tiles ahead.
+// Hand-offs between roles are mbarriers (arrive / wait), within a role named
+// barriers. Fields and face data are double-buffered (tile slots), the
+// residual single-buffered (reloaded once the previous tile's results have
+// been read out), GEMM2's accumulator double-buffered in tensor memory.
+// Every wait is bounded; a wait that runs out raises a CTA-wide abort flag
+// that ends the waits of the other roles, each role leaves its loop together
+// (the named barriers carry the vote), work already in flight is drained and
+// the kernel returns with the error flag set.
+//
+// FP16 split: the field operand is scaled per (element, field) row as above;
+// the flux operand per (element, field) row as well (a power of two from the
+// largest exponent in the row), so a quiet element next to a loud one keeps
+// its own relative accuracy.
+#ifndef DGMX_WS_FLUX_WARPS
+#define DGMX_WS_FLUX_WARPS 10
+#endif
+constexpr int kWsE = 8, kWsF = DGMX_WS_FLUX_WARPS;
+
+// Optional per-role timestamps (build with -DDGMX_WS_TIMING; off in the
+// library): SM clock cycles since the block's start at fixed points of each
+// role, per block and tile, read back with dgmx_ws_trace().
+constexpr int kTraceTiles = 32, kTraceEvents = 32, kTraceBlocks = 160;
+#ifdef DGMX_WS_TIMING
+__device__ uint32_t g_ws_trace[kTraceBlocks * kTraceTiles * kTraceEvents];
+#define WS_MARK(t, ev)                                                                                              \
+  do {                                                                                                              \
+    if ((t) < kTraceTiles && blockIdx.x < kTraceBlocks)                                                             \
+      g_ws_trace[(blockIdx.x * kTraceTiles + (t)) * kTraceEvents + (ev)] = uint32_t(clock64() - ws_t0);             \
+  } while (0)
+#else
+#define WS_MARK(t, ev) \
+  do {                 \
+  } while (0)
+#endif
+constexpr int kWsThreads = (kWsE + kWsF + 2) * 32;
+constexpr int kBarIdE = 1, kBarIdF = 2;
+
+template <int N>
+struct TW {
+  using T = TC<N>;
+  static constexpr int FS = T::FS;
+  static constexpr int UB = rup(6 * FS * 4, 128);         // one [6][FS] FP32 field block
+  static constexpr int OFF_OPS = 0;                       // B1 hi/lo, B2 hi/lo (as the resident kernel)
+  static constexpr int OFF_A2H = rup(T::OPS_BYTES, 128), OFF_A2L = OFF_A2H + T::A2B;
+  static constexpr int OFF_U = OFF_A2H + 2 * T::A2B;     // two tile slots of fields (results in place)
+  static constexpr int OFF_RES = OFF_U + 2 * UB;         // residual of a tile (results in place)
+  static constexpr int OFF_FACE = OFF_RES + UB;          // two tile slots of face and element data
+  static constexpr int OFF_TAB = OFF_FACE + 2 * T::FSLOT;
+  // [128] A1 inverse row scales (compact rows), [128] A1 row maxima (float
+  // bits), [2][128] A2 row maxima (exponent fields), one set per tile slot
+  static constexpr int OFF_MX = OFF_TAB + rup(T::NFF + kConnKinds * T::NFP, 16);
+  static constexpr int OFF_BAR = OFF_MX + 4 * 128 * 4;
+  static constexpr int SMEM = OFF_BAR + 12 * 8 + 16;
+  // tensor memory: V [0, N1), GEMM2 slots [N1, N1 + 2 NB), A1 hi/lo from CA
+  static constexpr int CS = T::N1;
+  static constexpr int CA = rup(T::N1 + 2 * T::NB, 32);
+  static constexpr int TCOLS = tmem_cols(CA + T::K1);
+  static_assert(CA + T::K1 <= 512, "accumulators and the A1 operand exceed tensor memory");
+  static_assert(T::K1 % 16 == 0, "each E part splits a multiple of 8 K values");
+  static_assert(SMEM <= 232448, "warp-specialised tile does not fit in shared memory");
+};
+
+template <int N, int MODE, bool BF16>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_stage_tcw(StageArgs a, const uint4 *__restrict__ ops, TileMap tm, int *err_flag) {
+  using T = TC<N>;
+  using L = TW<N>;
+  constexpr int NP = T::NP, NFP = T::NFP, NPP = T::NPP, NFF = T::NFF, FS = T::FS;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float *s_ub = reinterpret_cast<float *>(smem + L::OFF_U);
+  float *s_res = reinterpret_cast<float *>(smem + L::OFF_RES);
+  const uint8_t *s_fm = smem + L::OFF_TAB;
+  const uint8_t *s_nb = s_fm + NFF;
+  float *s_inv1 = reinterpret_cast<float *>(smem + L::OFF_MX);
+  uint32_t *s_rowmx = reinterpret_cast<uint32_t *>(s_inv1 + 128);
+  uint32_t *s_rowex2 = s_rowmx + 128; // [2][128]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::OFF_BAR);
+  uint64_t *barU = bars + 0;   // [2] fields and face data of a tile slot landed
+  uint64_t *barR = bars + 2;   // residual of a tile landed
+  uint64_t *bar1 = bars + 3;   // GEMM1 of a tile complete
+  uint64_t *bar2 = bars + 4;   // [2] GEMM2 of a tile complete (per accumulator slot)
+  uint64_t *barA1 = bars + 6;  // E: A1 of a tile written, V of the previous tile read
+  uint64_t *barA2 = bars + 7;  // F: A2 of a tile written
+  uint64_t *barEpi = bars + 8; // [2] E: results of a tile in shared memory, its GEMM2 slot read
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 12);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(bars + 12) + 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t KN = a.K * NPP;
+  const uint32_t sbase = umma::smem_u32(smem);
+  const long long wlim = umma::wait_cycles(a.wait_limit);
+  const bool read_res = MODE == MODE_LSERK && a.rk_a != 0.f;
+  const int ntile = (tm.ntiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
+  auto gtile = [&](int t) { return int(blockIdx.x) + t * int(gridDim.x); };
+  auto face_slot = [&](int t) { return smem + L::OFF_FACE + (t & 1) * T::FSLOT; };
+  auto u_slot = [&](int t) { return s_ub + (t & 1) * (L::UB / 4); };
+
+  // ---- one-time setup (may overlap the end of the previous stage)
+  for (int i = tid; i < T::OPS_BYTES / 16; i += kWsThreads)
+    reinterpret_cast<uint4 *>(smem + L::OFF_OPS)[i] = __ldg(ops + i);
+  for (int i = tid; i < 2 * T::A2B / 16; i += kWsThreads)
+    reinterpret_cast<uint4 *>(smem + L::OFF_A2H)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < NFF + kConnKinds * NFP; i += kWsThreads)
+    smem[L::OFF_TAB + i] = i < NFF ? a.fmask[i] : a.nbrtab[i - NFF];
+  for (int i = tid; i < 4 * 128; i += kWsThreads) s_inv1[i] = i < 128 ? 1.f : 0.f;
+  if (tid == 0) {
+    for (int b = 0; b < 10; ++b) umma::mbar_init(bars + b, 1);
+    *s_abort = 0;
+    umma::fence_mbar_init();
+  }
+  if (warp == 0) umma::tmem_alloc(tslot, L::TCOLS);
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  pdl_wait(); // nothing the previous stage writes is read before this point
+#ifdef DGMX_WS_TIMING
+  const long long ws_t0 = clock64();
+#endif
+
+  if (warp < kWsE) {
+    // =================== E: field split, volume terms, epilogue
+    const int q = warp & 3, p = warp >> 2;
+    const int r = 32 * q + lane, cr = compact_row(r);
+    const int e1 = cr >= 0 ? cr / 6 : 0, f1 = cr >= 0 ? cr % 6 : 0;
+    constexpr int KP1 = T::K1 / 2; // K values of A1 per part
+    const int kb1 = KP1 * p;
+    const uint32_t a1_hi = tmem + uint32_t(L::CA), a1_lo = a1_hi + uint32_t(T::K1 / 2);
+    const uint32_t a1_st = (uint32_t(q * 32) << 16) + uint32_t(KP1 / 2 * p);
+    const bool lane_used = lane < 30;
+    const int ep = lane_used ? lane / 6 : 4;
+    const int fld = lane_used ? lane % 6 : 5;
+    const int comp = fld % 3;
+    const bool isE = fld < 3;
+    const int src1 = ep * 6 + (isE ? 3 : 0) + (comp + 2) % 3;
+    const int src2 = ep * 6 + (isE ? 3 : 0) + (comp + 1) % 3;
+    const int dl1 = (comp + 2) % 3, dl2 = (comp + 1) % 3;
+    const int e_loc = q * 5 + ep;
+    const int ridx = e_loc * 6 + fld;
+    const int soff = fld * FS + e_loc * NPP;
+    const uint32_t lane_taddr = tmem + (uint32_t(q * 32) << 16);
+    constexpr int NCH = (NP + 7) / 8;
+    constexpr int CPP = (NCH + 1) / 2;
+    const int ch0 = p * CPP;
+    const int ch1 = (p + 1) * CPP < NCH ? (p + 1) * CPP : NCH;
+    uint32_t rph = 0;
+
+    // the fields of tile t, split, into A1 (tensor memory); false if a wait
+    // ran out anywhere in the role
+    auto split = [&](int t) -> bool {
+      const bool okw = umma::mbar_wait_or_abort(barU + (t & 1), uint32_t(t >> 1) & 1u, wlim, s_abort);
+      if (tid == 0) WS_MARK(t, 3);
+      const int ne = tm.size(gtile(t), a.K);
+      const float *su = u_slot(t);
+      auto load4 = [&](int k) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (okw && cr >= 0 && k < NPP && e1 < ne) {
+          v = *reinterpret_cast<const float4 *>(su + f1 * FS + e1 * NPP + k);
+          if (k + 3 >= NP) {
+            if (k + 0 >= NP) v.x = 0.f;
+            if (k + 1 >= NP) v.y = 0.f;
+            if (k + 2 >= NP) v.z = 0.f;
+            if (k + 3 >= NP) v.w = 0.f;
+          }
+        }
+        return v;
+      };
+      float sc1 = 1.f;
+      if constexpr (!BF16) {
+        // FP16: the row's largest magnitude over both parts first
+        float mx = 0.f;
+#pragma unroll
+        for (int j = 0; j < KP1 / 4; ++j) mx = absmax4(mx, load4(kb1 + 4 * j));
+        if (cr >= 0) atomicMax(s_rowmx + r, __float_as_uint(mx));
+        umma::named_sync(kBarIdE, kWsE * 32);
+        float inv1r = 1.f;
+        if (cr >= 0) row_scale(__uint_as_float(s_rowmx[r]), sc1, inv1r);
+        if (p == 0 && cr >= 0) s_inv1[cr] = inv1r;
+      }
+      // eight K values (four 32-bit columns of hi and of lo) at a time
+#pragma unroll
+      for (int c = 0; c < KP1 / 8; ++c) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          float4 w = load4(kb1 + 8 * c + 4 * j);
+          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+          split2<BF16>(w.x, w.y, hi[2 * j], lo[2 * j]);
+          split2<BF16>(w.z, w.w, hi[2 * j + 1], lo[2 * j + 1]);
+        }
+        umma::tmem_st4(a1_hi + a1_st + uint32_t(4 * c), hi);
+        umma::tmem_st4(a1_lo + a1_st + uint32_t(4 * c), lo);
+      }
+      umma::tmem_wait_st();
+      umma::fence_before_sync();
+      const bool fail = umma::named_any(kBarIdE, kWsE * 32, !okw);
+      if (!BF16 && p == 0) s_rowmx[r] = 0u; // every row's maximum has been read
+      if (!fail && tid == 0) umma::mbar_arrive(barA1);
+      if (tid == 0) WS_MARK(t, 4);
+      return !fail;
+    };
+
+    bool failed = ntile > 0 && !split(0);
+    for (int t = 0; t < ntile && !failed; ++t) {
+      if (t + 1 == ntile) pdl_launch_next();
+      const int slot = t & 1;
+      const int ne = tm.size(gtile(t), a.K);
+      const float *s_geo = reinterpret_cast<const float *>(face_slot(t) + T::FELEM);
+      float *su = u_slot(t);
+      // ---- volume terms from GEMM1: chain rule (eq. dg-reference-matrices) and curls
+      if (tid == 0) WS_MARK(t, 0);
+      bool ok = umma::mbar_wait_or_abort(bar1, uint32_t(t) & 1u, wlim, s_abort);
+      if (tid == 0) WS_MARK(t, 1);
+      umma::fence_after_sync();
+      const bool live = lane_used && e_loc < ne;
+      float g1r = 0.f, g1s = 0.f, g1t = 0.f, g2r = 0.f, g2s = 0.f, g2t = 0.f, w = 0.f, dtk = a.dt;
+      if (live) {
+        const float *g = s_geo + e_loc * G_STRIDE;
+        if (a.dt_geo) dtk = g[G_DT];
+        g1r = g[G_RX + dl1], g1s = g[G_SX + dl1], g1t = g[G_TX + dl1];
+        g2r = g[G_RX + dl2], g2s = g[G_SX + dl2], g2t = g[G_TX + dl2];
+        w = g[isE ? G_IEPS : G_IMU];
+      }
+      if constexpr (!BF16) {
+        const float inv1 = s_inv1[lane_used ? ridx : 0];
+        g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
+      }
+      float vol[CPP][8];
+#pragma unroll
+      for (int c = 0; c < CPP; ++c) {
+        const int ch = ch0 + c;
+        if (ch >= ch1) break;
+        const int i0 = ch * 8;
+        float ur[8], us[8], ut[8];
+        umma::tmem_ld8(lane_taddr + uint32_t(i0), ur);
+        umma::tmem_ld8(lane_taddr + uint32_t(T::NB + i0), us);
+        umma::tmem_ld8(lane_taddr + uint32_t(2 * T::NB + i0), ut);
+        umma::tmem_wait_ld();
+        umma::reg_fence8(ur);
+        umma::reg_fence8(us);
+        umma::reg_fence8(ut);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+          const float p1 = g1r * ur[n] + g1s * us[n] + g1t * ut[n];
+          const float p2 = g2r * ur[n] + g2s * us[n] + g2t * ut[n];
+          const float v1 = __shfl_sync(0xffffffffu, p1, src1);
+          const float v2 = __shfl_sync(0xffffffffu, p2, src2);
+          vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
+        }
+      }
+      umma::fence_before_sync();
+      if (umma::named_any(kBarIdE, kWsE * 32, !ok)) { // V read out by every E thread
+        failed = true;
+        break;
+      }
+      if (tid == 0) WS_MARK(t, 2);
+      // ---- the next tile's fields into A1 (GEMM1 of this tile is complete)
+      if (t + 1 < ntile && !split(t + 1)) {
+        failed = true;
+        break;
+      }
+      // ---- epilogue: lifted flux, material scale, update, in place
+      ok = umma::mbar_wait_or_abort(bar2 + slot, uint32_t(t >> 1) & 1u, wlim, s_abort);
+      if (read_res) {
+        ok = umma::mbar_wait_or_abort(barR, rph, wlim, s_abort) && ok;
+        rph ^= 1u;
+      }
+      if (tid == 0) WS_MARK(t, 5);
+      umma::fence_after_sync();
+      float inv2 = 1.f;
+      if constexpr (!BF16) {
+        float sc;
+        row_scale(__uint_as_float(s_rowex2[slot * 128 + r] << 23), sc, inv2);
+      }
+      const uint32_t s_taddr = lane_taddr + uint32_t(L::CS + slot * T::NB);
+#pragma unroll
+      for (int c = 0; c < CPP; ++c) {
+        const int ch = ch0 + c;
+        if (ch >= ch1) break;
+        const int i0 = ch * 8;
+        float lf[8];
+        umma::tmem_ld8(s_taddr + uint32_t(i0), lf);
+        umma::tmem_wait_ld();
+        umma::reg_fence8(lf);
+        if (live && ok) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int i = i0 + 4 * h;
+            if (i < NPP) {
+              float r4[4];
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq)
+                r4[qq] = (i + qq < NP) ? (vol[c][4 * h + qq] + lf[4 * h + qq] * inv2) * w : 0.f;
+              float4 *rp = reinterpret_cast<float4 *>(s_res + soff + i);
+              if (MODE == MODE_RHS) {
+                *rp = make_float4(r4[0], r4[1], r4[2], r4[3]);
+              } else {
+                const float4 rs = read_res ? *rp : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 *up = reinterpret_cast<float4 *>(su + soff + i);
+                const float4 uo = *up;
+                const float rsv[4] = {rs.x, rs.y, rs.z, rs.w}, uov[4] = {uo.x, uo.y, uo.z, uo.w};
+                float nr[4], nu[4];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                  const bool pad = i + qq >= NP;
+                  nr[qq] = pad ? 0.f : fmaf(a.rk_a, rsv[qq], dtk * r4[qq]);
+                  nu[qq] = pad ? 0.f : fmaf(a.rk_b, nr[qq], uov[qq]);
+                }
+                *rp = make_float4(nr[0], nr[1], nr[2], nr[3]);
+                *up = make_float4(nu[0], nu[1], nu[2], nu[3]);
+              }
+            }
+          }
+        }
+      }
+      umma::fence_proxy_async(); // results are read by the bulk stores
+      umma::fence_before_sync();
+      if (umma::named_any(kBarIdE, kWsE * 32, !ok)) {
+        failed = true;
+        break;
+      }
+      if (!BF16 && p == 0) s_rowex2[slot * 128 + r] = 0u; // slot reused two tiles on
+      umma::named_sync(kBarIdE, kWsE * 32);
+      if (tid == 0) umma::mbar_arrive(barEpi + slot);
+      if (tid == 0) WS_MARK(t, 6);
+    }
+    if (failed && tid == 0) {
+      *s_abort = 1;
+      atomicExch(err_flag, 1);
+    }
+  } else if (warp < kWsE + kWsF) {
+    // =================== F: upwind flux and its split into A2
+    const int fw = warp - kWsE;
+    constexpr int NFPE = T::NFPE;
+    constexpr int KGF = T::K2 / 16;
+    constexpr int NBLK = (kTileElems / 4) * KGF;
+    constexpr int R2 = (NBLK + kWsF - 1) / kWsF;
+    const int eo = lane >> 3, kp = lane & 7;
+    bool failed = false;
+    for (int t = 0; t < ntile; ++t) {
+      if (t + 1 == ntile) pdl_launch_next();
+      const int slot = t & 1;
+      const int64_t k0 = tm.start(gtile(t));
+      const int ne = tm.size(gtile(t), a.K);
+      const uint8_t *fs = face_slot(t);
+      const float4 *s_fgeo = reinterpret_cast<const float4 *>(fs + T::FGEO);
+      const float4 *s_fmat = reinterpret_cast<const float4 *>(fs + T::FMAT);
+      const int2 *s_fconn = reinterpret_cast<const int2 *>(fs + T::FCONN);
+      const float *su = u_slot(t);
+      if (tid == kWsE * 32) WS_MARK(t, 8);
+      bool ok = umma::mbar_wait_or_abort(barU + slot, uint32_t(t >> 1) & 1u, wlim, s_abort);
+      if (tid == kWsE * 32) WS_MARK(t, 9);
+      // A2 is free once the previous tile's GEMM2 has completed
+      bool a2free = t == 0;
+      auto wait_a2 = [&]() {
+        if (tid == kWsE * 32) WS_MARK(t, 10);
+        if (!a2free)
+          ok = umma::mbar_wait_or_abort(bar2 + ((t - 1) & 1), uint32_t((t - 1) >> 1) & 1u, wlim, s_abort) && ok;
+        umma::fence_after_sync();
+        a2free = true;
+        if (tid == kWsE * 32) WS_MARK(t, 11);
+      };
+      // one column pair of the six rows of element e into A2 (a 32-bit word
+      // per row; the six rows lie in one TMEM lane quarter)
+      auto store_a2 = [&](int e, int fm, const float (*flv)[6], const float *sc) {
+        const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          uint32_t hi, lo;
+          split2<BF16>(flv[0][c] * sc[c], flv[1][c] * sc[c], hi, lo);
+          const uint32_t o = T::a2_offset(r0 + uint32_t(c), uint32_t(fm));
+          *reinterpret_cast<uint32_t *>(smem + L::OFF_A2H + o) = hi;
+          *reinterpret_cast<uint32_t *>(smem + L::OFF_A2L + o) = lo;
+        }
+      };
+      constexpr int RF = BF16 ? 2 : R2; // FP16 holds every block's fluxes until the row scales are known
+      float fl[RF][2][6];
+#pragma unroll
+      for (int s0 = 0; s0 < R2; s0 += 2) {
+        // neighbour traces of two blocks: outside the tile from L2 (all loads
+        // in flight together), inside the tile from the staged fields
+        float qp[2][2][6];
+        int lidx[2][2];
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss) {
+          const int s = s0 + ss;
+          const int blk = fw + kWsF * s;
+          const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+          const int f = fm / NFPE, mm = fm - f * NFPE;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            lidx[ss][h] = -1;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) qp[ss][h][c] = 0.f;
+          }
+          if (ok && s < R2 && blk < NBLK && f < 4 && e < ne) {
+            const int2 cn = s_fconn[e * 4 + f];
+            if (cn.y != kBoundaryConn) {
+              const int el = cn.x - int(k0);
+              const bool local = el >= 0 && el < ne;
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                if (mm + h < NFP) {
+                  const int node = s_nb[cn.y * NFP + mm + h];
+                  if (local) {
+                    lidx[ss][h] = el * NPP + node;
+                  } else {
+                    const float *up = a.u + int64_t(cn.x) * NPP + node;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) qp[ss][h][c] = __ldg(up + c * KN);
+                  }
+                }
+              }
+            }
+          }
+        }
+        if constexpr (BF16) {
+          if (s0 == 0) wait_a2();
+        }
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss) {
+          const int s = s0 + ss;
+          if (s >= R2) break;
+          float(*flv)[6] = fl[BF16 ? ss : s];
+          const int blk = fw + kWsF * s;
+          const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+          const int f = fm / NFPE, mm = fm - f * NFPE;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) flv[h][c] = 0.f;
+          if (ok && blk < NBLK && f < 4 && e < ne) {
+            const float4 g0 = s_fgeo[e * 4 + f], w1 = s_fmat[e * 4 + f];
+            const bool wall = s_fconn[e * 4 + f].y == kBoundaryConn;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (mm + h < NFP) {
+                const int vm = s_fm[f * NFP + mm + h];
+                float qm[6], q[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) qm[c] = su[c * FS + e * NPP + vm];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) q[c] = lidx[ss][h] >= 0 ? su[c * FS + lidx[ss][h]] : qp[ss][h][c];
+                if (wall) {
+#pragma unroll
+                  for (int c = 0; c < 3; ++c) {
+                    q[c] = -qm[c];
+                    q[c + 3] = qm[c + 3];
+                  }
+                }
+                maxwell_flux_w(g0, qm, q, w1, a.alpha, flv[h]);
+              }
+            }
+          }
+          if constexpr (BF16) {
+            const float one[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+            if (blk < NBLK) store_a2(e, fm, flv, one);
+          }
+        }
+      }
+      if constexpr (!BF16) {
+        // FP16: the largest exponent of each (element, field) row of A2: per
+        // lane the exponents of its six fields packed into two words, the
+        // maximum over the 8 lanes of an element (bytewise), one shared-memory
+        // maximum per row and block
+#pragma unroll
+        for (int s = 0; s < R2; ++s) {
+          const int blk = fw + kWsF * s;
+          if (blk >= NBLK) break; // warp-uniform
+          uint32_t ex[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+            ex[c] = (max(__float_as_uint(fabsf(fl[s][0][c])), __float_as_uint(fabsf(fl[s][1][c]))) >> 23) & 0xFFu;
+          uint32_t w0 = ex[0] | (ex[1] << 8) | (ex[2] << 16) | (ex[3] << 24), w1 = ex[4] | (ex[5] << 8);
+#pragma unroll
+          for (int o = 1; o < 8; o <<= 1) {
+            w0 = __vmaxu4(w0, __shfl_xor_sync(0xffffffffu, w0, o));
+            w1 = __vmaxu4(w1, __shfl_xor_sync(0xffffffffu, w1, o));
+          }
+          const int e = 4 * (blk / KGF) + eo;
+          if (kp == 0) {
+            const int r0 = 32 * (e / 5) + 6 * (e % 5);
+            uint32_t *rx = s_rowex2 + slot * 128 + r0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicMax(rx + c, (w0 >> (8 * c)) & 0xFFu);
+            atomicMax(rx + 4, w1 & 0xFFu);
+            atomicMax(rx + 5, (w1 >> 8) & 0xFFu);
+          }
+        }
+        wait_a2();
+        if (umma::named_any(kBarIdF, kWsF * 32, !ok)) { // also completes the row maxima
+          failed = true;
+          break;
+        }
+        // ---- split the face fluxes into A2 with the row scales
+#pragma unroll
+        for (int s = 0; s < R2; ++s) {
+          const int blk = fw + kWsF * s;
+          if (blk >= NBLK) break;
+          const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+          const int r0 = 32 * (e / 5) + 6 * (e % 5);
+          float sc[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            float inv;
+            row_scale(__uint_as_float(s_rowex2[slot * 128 + r0 + c] << 23), sc[c], inv);
+          }
+          store_a2(e, fm, fl[s], sc);
+        }
+      } else {
+        if (umma::named_any(kBarIdF, kWsF * 32, !ok)) {
+          failed = true;
+          break;
+        }
+      }
+      umma::fence_proxy_async();
+      umma::named_sync(kBarIdF, kWsF * 32);
+      if (tid == kWsE * 32) umma::mbar_arrive(barA2);
+      if (tid == kWsE * 32) WS_MARK(t, 12);
+    }
+    if (failed && tid == kWsE * 32) {
+      *s_abort = 1;
+      atomicExch(err_flag, 1);
+    }
+  } else if (warp == kWsE + kWsF) {
+    // =================== MMA issue (one thread)
+    if (lane == 0) {
+      int n1 = 0, n2 = 0;
+      bool failed = false;
+      for (int t = 0; t < ntile; ++t) {
+        if (t + 1 == ntile) pdl_launch_next();
+        if (!umma::mbar_wait_or_abort(barA1, uint32_t(t) & 1u, wlim, s_abort)) {
+          failed = true;
+          break;
+        }
+        WS_MARK(t, 16);
+        umma::fence_after_sync();
+        issue_split_gemm_ta<BF16, T::K1, T::N1>(tmem, tmem + uint32_t(L::CA), tmem + uint32_t(L::CA + T::K1 / 2),
+                                                 sbase + L::OFF_OPS, sbase + L::OFF_OPS + T::B1B);
+        umma::commit(bar1);
+        ++n1;
+        WS_MARK(t, 17);
+        if (!umma::mbar_wait_or_abort(barA2, uint32_t(t) & 1u, wlim, s_abort) ||
+            (t >= 2 && !umma::mbar_wait_or_abort(barEpi + (t & 1), uint32_t((t - 2) >> 1) & 1u, wlim, s_abort))) {
+          failed = true;
+          break;
+        }
+        WS_MARK(t, 18);
+        umma::fence_after_sync();
+        issue_split_gemm<BF16, T::K2, T::N2, T::A2LBO, T::A2SBO>(
+            tmem + uint32_t(L::CS + (t & 1) * T::NB), sbase + L::OFF_A2H, sbase + L::OFF_A2L,
+            sbase + L::OFF_OPS + 2 * T::B1B, sbase + L::OFF_OPS + 2 * T::B1B + T::B2B);
+        umma::commit(bar2 + (t & 1));
+        ++n2;
+        WS_MARK(t, 19);
+      }
+      // drain: the last MMAs complete before tensor memory is released
+      if (n1 > 0) umma::mbar_wait_bounded(bar1, uint32_t(n1 - 1) & 1u);
+      for (int sl = 0; sl < 2; ++sl) {
+        const int last = n2 - 1 - ((n2 - 1 - sl) & 1); // last GEMM2 issued into this slot
+        if (last >= 0) umma::mbar_wait_bounded(bar2 + sl, uint32_t(last >> 1) & 1u);
+      }
+      if (failed) atomicExch(err_flag, 1);
+    } else {
+      if (ntile > 0) pdl_launch_next();
+    }
+  } else {
+    // =================== bulk stores out, staging in (one thread)
+    if (lane == 0) {
+      auto stage = [&](int t) {
+        const int64_t kb = tm.start(gtile(t));
+        const uint32_t nb = uint32_t(tm.size(gtile(t), a.K));
+        const uint32_t rb = nb * NPP * 4;
+        uint8_t *fs = face_slot(t);
+        float *su = u_slot(t);
+        uint64_t *b = barU + (t & 1);
+        umma::mbar_arrive_expect_tx(b, 6u * rb + nb * (64u + 64u + G_STRIDE * 4u + 32u));
+        for (int f = 0; f < 6; ++f) umma::bulk_g2s(su + f * FS, a.u + f * KN + kb * NPP, rb, b);
+        umma::bulk_g2s(fs + T::FGEO, a.fgeo + kb * 4, nb * 64u, b);
+        umma::bulk_g2s(fs + T::FMAT, a.fmat + kb * 4, nb * 64u, b);
+        umma::bulk_g2s(fs + T::FELEM, a.geo + kb * G_STRIDE, nb * G_STRIDE * 4u, b);
+        umma::bulk_g2s(fs + T::FCONN, a.fconn + kb * 4, nb * 32u, b);
+      };
+      auto load_res = [&](int t) {
+        const int64_t kb = tm.start(gtile(t));
+        const uint32_t rb = uint32_t(tm.size(gtile(t), a.K)) * NPP * 4;
+        umma::mbar_arrive_expect_tx(barR, 6u * rb);
+        for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_res + f * FS, a.res + f * KN + kb * NPP, rb, barR);
+      };
+      int staged = 0, nres = 0;
+      if (ntile > 0) stage(0), ++staged;
+      if (ntile > 1) stage(1), ++staged;
+      if (read_res && ntile > 0) load_res(0), ++nres;
+      bool failed = false;
+      for (int t = 0; t < ntile; ++t) {
+        if (t + 1 == ntile) pdl_launch_next();
+        if (!umma::mbar_wait_or_abort(barEpi + (t & 1), uint32_t(t >> 1) & 1u, wlim, s_abort)) {
+          failed = true;
+          break;
+        }
+        WS_MARK(t, 24);
+        const int64_t k0 = tm.start(gtile(t));
+        const uint32_t rowbytes = uint32_t(tm.size(gtile(t), a.K)) * NPP * 4;
+        const float *su = u_slot(t);
+        for (int f = 0; f < 6; ++f) {
+          if (MODE == MODE_RHS) {
+            umma::bulk_s2g(a.rhs + f * KN + k0 * NPP, s_res + f * FS, rowbytes);
+          } else {
+            umma::bulk_s2g(a.res + f * KN + k0 * NPP, s_res + f * FS, rowbytes);
+            umma::bulk_s2g(a.u_out + f * KN + k0 * NPP, su + f * FS, rowbytes);
+          }
+        }
+        umma::bulk_commit();
+        WS_MARK(t, 25);
+        umma::bulk_wait_read_all(); // the residual buffer and this slot may be refilled
+        WS_MARK(t, 26);
+        if (read_res && t + 1 < ntile) load_res(t + 1), ++nres;
+        if (t + 2 < ntile) stage(t + 2), ++staged;
+      }
+      umma::bulk_wait_all();
+      // drain: copies still in flight land before shared memory is released
+      for (int sl = 0; sl < 2; ++sl) {
+        const int last = staged - 1 - ((staged - 1 - sl) & 1); // last tile staged into this slot
+        if (last >= 0) umma::mbar_wait_bounded(barU + sl, uint32_t(last >> 1) & 1u);
+      }
+      if (nres > 0) umma::mbar_wait_bounded(barR, uint32_t(nres - 1) & 1u);
+      if (failed) atomicExch(err_flag, 1);
+    } else {
+      if (ntile > 0) pdl_launch_next();
+    }
+  }
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, L::TCOLS);
 }
 
 // Host: the operators in the canonical K-major operand layout, hi then lo.
@@ -735,6 +1421,18 @@ cudaError_t launch_tc_kernel(const StageArgs &a, const TcState &st, int *flag, c
                     reinterpret_cast<const uint4 *>(st.d_ops), tm, flag, EnsLaunch{});
 }
 
+template <int N, int MODE, bool BF16>
+cudaError_t launch_tcw_kernel(const StageArgs &a, const TcState &st, int *flag, cudaStream_t s) {
+  using L = TW<N>;
+  auto kern = k_stage_tcw<N, MODE, BF16>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+  if (e != cudaSuccess) return e;
+  const TileMap tm = make_tiles(a.K, st.sms);
+  const int grid = tm.ntiles < st.sms ? tm.ntiles : st.sms;
+  return launch_pdl(kern, dim3(unsigned(grid)), dim3(kWsThreads), size_t(L::SMEM), s, a,
+                    reinterpret_cast<const uint4 *>(st.d_ops), tm, flag);
+}
+
 // Cooperative launch of the multi-step form: one block per SM, all resident.
 template <int N, bool BF16>
 cudaError_t launch_tc_ens_kernel(const StageArgs &a, const TcState &st, const EnsLaunch &ens, int *flag,
@@ -766,6 +1464,13 @@ cudaError_t launch_tc_ens_order(bool bf16, const StageArgs &a, const TcState &st
 
 template <int N>
 cudaError_t launch_tc_order(int mode, bool bf16, const StageArgs &a, const TcState &st, int *flag, cudaStream_t s) {
+  if (st.form == 0) {
+    if (mode == MODE_RHS)
+      return bf16 ? launch_tcw_kernel<N, MODE_RHS, true>(a, st, flag, s)
+                  : launch_tcw_kernel<N, MODE_RHS, false>(a, st, flag, s);
+    return bf16 ? launch_tcw_kernel<N, MODE_LSERK, true>(a, st, flag, s)
+                : launch_tcw_kernel<N, MODE_LSERK, false>(a, st, flag, s);
+  }
   if (mode == MODE_RHS)
     return bf16 ? launch_tc_kernel<N, MODE_RHS, true>(a, st, flag, s) : launch_tc_kernel<N, MODE_RHS, false>(a, st, flag, s);
   return bf16 ? launch_tc_kernel<N, MODE_LSERK, true>(a, st, flag, s)
@@ -773,6 +1478,12 @@ cudaError_t launch_tc_order(int mode, bool bf16, const StageArgs &a, const TcSta
 }
 
 } // namespace
+
+#ifdef DGMX_WS_TIMING
+extern "C" int dgmx_ws_trace(uint32_t *host) {
+  return int(cudaMemcpyFromSymbol(host, g_ws_trace, sizeof(g_ws_trace)));
+}
+#endif
 
 int tc_prepare(dg_ctx *ctx) {
   if (ctx->N > kMaxTcOrder) {
@@ -801,6 +1512,10 @@ int tc_prepare(dg_ctx *ctx) {
   }
   TcState *st = new TcState();
   st->sms = prop.multiProcessorCount;
+  // N <= 5: the single-tile form unless DGMX_TC_FORM=ws asks for the
+  // warp-specialised one (two tiles in flight; measured slower at N = 4, 5)
+  const char *form = std::getenv("DGMX_TC_FORM");
+  st->form = (form && std::strcmp(form, "ws") == 0) ? 0 : 1;
   if (cudaMalloc(&st->d_ops, blk.size()) != cudaSuccess) {
     delete st;
     ctx->err = "tc_prepare: device allocation failed";

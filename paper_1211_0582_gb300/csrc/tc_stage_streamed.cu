@@ -76,9 +76,10 @@ struct TS {
   static constexpr int OFF_U = OFF_RING + kSlots * SL;           // fp32 [6][FS]
   static constexpr int OFF_FACE = OFF_U + 6 * FS * 4;            // float4 [80][3]
   static constexpr int OFF_TAB = OFF_FACE + kTileS * 4 * 48;
-  static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16); // [128] A1 inverse scales, [8] A2 maxima
+  // [128] A1 inverse scales, [2 * kTileS] A2 largest exponents per element and field type (E, H)
+  static constexpr int OFF_MX = OFF_TAB + rup(NFF + kConnKinds * NFP, 16);
   static constexpr int NBAR = 2 + 2 * kSlots;          // GEMM1, GEMM2, full[kSlots], empty[kSlots]
-  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 32;
+  static constexpr int OFF_BAR = OFF_MX + 128 * 4 + 2 * kTileS * 4;
   static constexpr int OFF_TSLOT = OFF_BAR + NBAR * 8;  // TMEM base address
   static constexpr int SMEM = OFF_TSLOT + 16;
   static_assert(4 * NB <= 512, "accumulators exceed tensor memory");
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF;
   float *s_inv1 = reinterpret_cast<float *>(smem + T::OFF_MX);
-  uint32_t *s_mx2 = reinterpret_cast<uint32_t *>(s_inv1 + 128);
+  uint32_t *s_ex2 = reinterpret_cast<uint32_t *>(s_inv1 + 128);
   uint64_t *bar1 = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR); // GEMM1 done
   uint64_t *bar2 = bar1 + 1;                                        // GEMM2 done
   uint64_t *full = bar1 + 2;                                        // ring slot filled
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   // ---- one-time setup
   for (int i = tid; i < T::AREG / 16; i += kThreadsS) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < NFF + kConnKinds * NFP; i += kThreadsS) s_fm[i] = i < NFF ? a.fmask[i] : a.nbrtab[i - NFF];
-  for (int i = tid; i < 136; i += kThreadsS) s_inv1[i] = i < 128 ? 1.f : 0.f;
+  for (int i = tid; i < 128 + 2 * kTileS; i += kThreadsS) s_inv1[i] = i < 128 ? 1.f : 0.f;
   if (tid == 0) {
     umma::mbar_init(bar1, 1);
     umma::mbar_init(bar2, 1);
@@ -327,7 +328,6 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 
     // ---- 4. neighbour traces and upwind flux (overlaps GEMM1), in registers
     float fl[R2][2][6];
-    uint32_t fmx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
     if (warp < kFluxWarps) {
 #pragma unroll
       for (int s0 = 0; s0 < R2; s0 += BATCH) {
@@ -399,19 +399,27 @@ __global__ void __launch_bounds__(kThreadsS, 1)
             }
           }
           if constexpr (!BF16) {
+            // FP16: one scale per element and field type (E, H), from the
+            // largest exponent over the element's fluxes of that type (packed
+            // exponents, bytewise maximum over the element's 8 lanes)
+            if (blk < NBLK) { // warp-uniform
+              uint32_t mE = 0u, mH = 0u;
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+              for (int h = 0; h < 2; ++h)
 #pragma unroll
-              for (int c = 0; c < 6; ++c) fmx[c] = max(fmx[c], __float_as_uint(fabsf(fl[s][h][c])));
+                for (int c = 0; c < 3; ++c) {
+                  mE = max(mE, __float_as_uint(fabsf(fl[s][h][c])));
+                  mH = max(mH, __float_as_uint(fabsf(fl[s][h][c + 3])));
+                }
+              uint32_t wx = ((mE >> 23) & 0xFFu) | (((mH >> 23) & 0xFFu) << 8);
+#pragma unroll
+              for (int o = 1; o < 8; o <<= 1) wx = __vmaxu4(wx, __shfl_xor_sync(0xffffffffu, wx, o));
+              if (kp == 0) {
+                atomicMax(s_ex2 + 2 * e, wx & 0xFFu);
+                atomicMax(s_ex2 + 2 * e + 1, (wx >> 8) & 0xFFu);
+              }
+            }
           }
-        }
-      }
-      if constexpr (!BF16) {
-        // one FP16 scale per field type (E, H) of the tile
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const uint32_t m = __reduce_max_sync(0xffffffffu, max(fmx[3 * g], max(fmx[3 * g + 1], fmx[3 * g + 2])));
-          if (lane == 0) atomicMax(s_mx2 + g, m);
         }
       }
     }
@@ -421,20 +429,21 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 
     // ---- 5. split the face fluxes into the A2 operand
     if (warp < kFluxWarps) {
-      float sc2[6];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        sc2[c] = 1.f;
-        if constexpr (!BF16) {
-          float inv;
-          row_scale(__uint_as_float(s_mx2[c / 3]), sc2[c], inv);
-        }
-      }
 #pragma unroll
       for (int s = 0; s < R2; ++s) {
         const int blk = warp + kFluxWarps * s;
         const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
         if (blk < NBLK) {
+          float sc2[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) sc2[c] = 1.f;
+          if constexpr (!BF16) {
+            float inv;
+            row_scale(__uint_as_float(s_ex2[2 * e] << 23), sc2[0], inv);
+            row_scale(__uint_as_float(s_ex2[2 * e + 1] << 23), sc2[3], inv);
+            sc2[1] = sc2[2] = sc2[0];
+            sc2[4] = sc2[5] = sc2[3];
+          }
           // the element's six rows share a quarter; a column pair is one
           // 32-bit word of a core-matrix row
           const uint32_t r0 = uint32_t(32 * (e / 5) + 6 * (e % 5));
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       float sc;
       const float inv1 = s_inv1[lane_used ? ridx : 0];
       g1r *= inv1, g1s *= inv1, g1t *= inv1, g2r *= inv1, g2s *= inv1, g2t *= inv1;
-      row_scale(__uint_as_float(s_mx2[fld / 3]), sc, inv2);
+      row_scale(__uint_as_float(s_ex2[lane_used ? 2 * e_loc + fld / 3 : 0] << 23), sc, inv2);
     }
     // residual of one 8-node chunk of this lane's row (loaded one chunk ahead)
     auto load_res = [&](int ch, float4 &r0, float4 &r1) {
@@ -584,7 +593,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       }
       umma::bulk_commit();
     }
-    if (!BF16 && tid < 8) s_mx2[tid] = 0u;
+    if (!BF16 && tid < 2 * kTileS) s_ex2[tid] = 0u;
     phase ^= 1u;
   }
   if (issuer) umma::bulk_wait_all();

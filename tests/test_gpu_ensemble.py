@@ -136,3 +136,28 @@ def test_ensemble_full_size_sampled_members():
         s.step(ud, rd, mem[i][2], steps)
         err = float((u[:, off[i]:off[i + 1]] - ud).norm() / ud.norm())
         assert err < 1e-6, (i, err)
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "fp32"])
+def test_ensemble_member_of_small_amplitude_keeps_relative_accuracy(precision):
+    # a member whose fields are 1e-6 of its neighbours' in the concatenated
+    # element order shares tensor-core tiles with a loud member; its result,
+    # relative to its own size, matches the member run alone
+    N = 4
+    mem = members([3, 2, 3], N)
+    ens = dg.Solver(N, precision=precision).upload_ensemble([m[0] for m in mem], [m[1] for m in mem],
+                                                            [m[2] for m in mem])
+    off = ens.ensemble_layout()
+    singles = [dg.Solver(N, precision=precision).upload(*m[0], eps=m[1]) for m in mem]
+    scale = [1.0, 1e-6, 1.0]
+    u0 = [scale[i] * initial(s, i) for i, s in enumerate(singles)]
+    u = torch.cat([s.to_device(v) for s, v in zip(singles, u0)], dim=1).contiguous()
+    res = torch.zeros_like(u)
+    ens.ensemble_step(u, res, 3)
+    ens.sync()
+    ud, rd = singles[1].to_device(u0[1]), singles[1].zeros()
+    singles[1].step(ud, rd, mem[1][2], 3)
+    torch.cuda.synchronize()
+    got = u[:, off[1]:off[2]]
+    err = float((got - ud).norm() / ud.norm())
+    assert err < 1e-5, err

@@ -166,3 +166,90 @@ def test_tc_single_partial_tile(precision, N):
     s.step(ud, rd, 0.5 / N ** 2, 2)
     s.sync()
     assert rel_l2(s.from_device(ud), ref) < TOL[precision]
+
+
+# per-element bars: FP32 path and FP16x3 at FP32 level, BF16x3 at its 16 bits
+ELEM_TOL = {"fp32": 5e-6, "fp16x3": 1e-5, "bf16x3": 2e-4}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "bf16x3"])
+@pytest.mark.parametrize("N,n,width", [(4, 6, 0.05), (5, 6, 0.05), (7, 4, 0.06)])
+def test_rhs_per_element_relative_error_localised_pulse(precision, N, n, width):
+    # A narrow pulse: element amplitudes span 10^15 and more between
+    # neighbours, and the 20 elements of a tile differ by 10^4..10^6. Each
+    # element's error is measured against that element's own largest value
+    # (over its six fields), so a quiet element that shares a tile with a loud
+    # one must keep its own relative accuracy (the FP16 flux scales are per
+    # element and field type). Elements below 1e-20 of the peak are left out
+    # (FP32 itself cannot resolve them).
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    eps = W.element_eps(EToV.shape[0], seed=2)
+    s = dg.Solver(N, precision=precision).upload(VX, VY, VZ, EToV, eps=eps)
+    m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps.astype(np.float64))
+    x, y, z = m.coords()
+    u0 = W.gaussian_pulse(x, y, z, seed=7, width=width)
+    ref = m.rhs(u0)
+    got = s.from_device(s.rhs(s.to_device(u0)))
+    s.sync()
+    amp = np.abs(ref).max(axis=(0, 2))
+    keep = amp > 1e-20 * amp.max()
+    assert keep.sum() > 20 and amp[keep].min() < 1e-8 * amp.max()  # the range the test is about
+    per_elem = np.abs(got - ref).max(axis=(0, 2))[keep] / amp[keep]
+    print(f"{precision} N={N}: per-element max rel {per_elem.max():.2e}, global rel l2 {rel_l2(got, ref):.2e}")
+    assert per_elem.max() < ELEM_TOL[precision]
+
+
+def _ws_solver(N, n, precision, eps=True):
+    # the warp-specialised form of the stage kernel (two tiles in flight per
+    # SM) is chosen per context at mesh upload by DGMX_TC_FORM=ws
+    import os
+    old = os.environ.get("DGMX_TC_FORM")
+    os.environ["DGMX_TC_FORM"] = "ws"
+    try:
+        return pair(N, n, precision, eps)
+    finally:
+        if old is None:
+            os.environ.pop("DGMX_TC_FORM")
+        else:
+            os.environ["DGMX_TC_FORM"] = old
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("N,n", [(2, 3), (3, 4), (4, 3), (5, 4)])
+def test_warp_specialised_form_parity(precision, N, n):
+    s, m = _ws_solver(N, n, precision)
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal(m.shape)
+    for alpha in (1.0, 0.0):
+        got = s.from_device(s.rhs(s.to_device(u), alpha=alpha))
+        assert rel_l2(got, m.rhs(u, alpha)) < TOL[precision]
+    x, y, z = m.coords()
+    u0 = W.gaussian_pulse(x, y, z, seed=7) + W.cavity_mode(x, y, z, 0.0)
+    dt = 0.5 / n / N ** 2
+    ud, rd = s.to_device(u0), s.zeros()
+    s.step(ud, rd, dt, 3)
+    s.sync()
+    ref, _ = m.lserk(u0, dt, 3)
+    assert rel_l2(s.from_device(ud), ref) < TOL[precision]
+
+
+def test_warp_specialised_form_wait_timeout_reports_and_recovers():
+    s, m = _ws_solver(4, 4, "fp16x3")
+    x, y, z = m.coords()
+    u0 = W.cavity_mode(x, y, z, 0.0)
+    dt = 0.5 / 4 / 16
+    ud, rd = s.to_device(u0), s.zeros()
+    s.step(ud, rd, dt, 2)
+    s.sync()
+    ref = s.from_device(ud)
+    s.set_wait_limit(1)
+    ud, rd = s.to_device(u0), s.zeros()
+    s.step(ud, rd, dt, 2)
+    with pytest.raises(dg.DGError) as ei:
+        s.sync()
+    assert ei.value.code == -5
+    s.set_wait_limit(0)
+    ud, rd = s.to_device(u0), s.zeros()
+    s.step(ud, rd, dt, 2)
+    s.sync()
+    assert np.array_equal(s.from_device(ud), ref)
