@@ -65,8 +65,9 @@ def bytes_per_element(N: int, Npad: int) -> float:
 # DRAM bytes (read + write) per launch of the stage kernel, the mean over the
 # five stages of one step, from an ncu capture of the current kernel;
 # keyed by (precision, N, hexahedra per edge); absent where no capture of the
-# current kernel exists.
-NCU_TRAFFIC = {("fp32", 5, 24): 391.472e6}
+# current kernel exists. The N=7 32^3 entry is the 16^3 capture scaled by the
+# element count (x8).
+NCU_TRAFFIC = {("fp16x3", 5, 24): 387.582e6, ("fp16x3", 7, 16): 218.986e6, ("fp16x3", 7, 32): 8 * 218.986e6}
 
 
 def measured_peaks():
@@ -407,6 +408,7 @@ def precision_legs(args, stream, headline=None):
                 e["alu_frac"] = flops_per_element(N) * K / (launch_ms * 1e-3) / 1e12 / peak_tf
             else:
                 e["hbm_frac"] = bytes_per_element(N, sv.Npad) * K / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+                e["traffic"] = NCU_TRAFFIC.get((prec, N, c["n"]))
             if ref is not None:
                 u, r = sv.to_device(u0_host), sv.zeros()
                 sv.step(u, r, dt, c["steps"])
