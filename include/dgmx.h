@@ -60,14 +60,15 @@ typedef enum {
   DG_FP32 = 0,   /* FP32 arithmetic on the CUDA cores */
   DG_BF16X3 = 1, /* D and LIFT contractions on tensor cores, BF16 hi+lo split, FP32 accumulate */
   DG_FP16X3 = 2  /* same with FP16 hi+lo split, FP32 accumulate; power-of-two scaled per
-                    (element, field) row of the field operand and per field type (E, H)
-                    of a tile's flux operand (FP16 range) */
+                    (element, field) row of the field operand and per element and field
+                    type (E, H) of the flux operand (FP16 range) */
 } dg_precision;
-/* The tensor-core precisions cover N = 1..7: up to N = 5 the split operators
+/* The FP32 precision covers N = 1..9. The tensor-core precisions cover
+ * N = 1..7 (DG_ERR_UNSUPPORTED at mesh upload for N = 8, 9): up to N = 5 the split operators
  * stay in shared memory, at N = 6, 7 they are streamed from L2 slice by slice.
  * They need an sm_103 device (GB300). */
 
-/* Create a context for polynomial order N (1..7) and the given arithmetic.
+/* Create a context for polynomial order N (1..9) and the given arithmetic.
  * cuda_stream is a cudaStream_t (may be NULL). *out receives the context.
  * Builds the reference operators on the host and makes no CUDA call; the
  * tensor-core precisions are checked against the device at dg_mesh_upload.

@@ -454,6 +454,8 @@ cudaError_t launch_adj(int N, int which, const AdjArgs &a, cudaStream_t s) {
   case 5: return launch_adj_order<5>(which, a, s);
   case 6: return launch_adj_order<6>(which, a, s);
   case 7: return launch_adj_order<7>(which, a, s);
+  case 8: return launch_adj_order<8>(which, a, s);
+  case 9: return launch_adj_order<9>(which, a, s);
   default: return cudaErrorInvalidValue;
   }
 }

@@ -107,7 +107,7 @@ extern "C" {
 int dg_create(dg_ctx **out, int N, int precision, void *cuda_stream) {
   if (!out) return set_err(nullptr, DG_ERR_ARG, "dg_create: out is NULL");
   *out = nullptr;
-  if (N < 1 || N > kMaxOrder) return set_err(nullptr, DG_ERR_ARG, "dg_create: N must be in 1..7");
+  if (N < 1 || N > kMaxOrder) return set_err(nullptr, DG_ERR_ARG, "dg_create: N must be in 1..9");
   if (precision != DG_FP32 && precision != DG_BF16X3 && precision != DG_FP16X3)
     return set_err(nullptr, DG_ERR_ARG, "dg_create: unknown precision");
   dg_ctx *c = new (std::nothrow) dg_ctx();
@@ -458,6 +458,8 @@ cudaError_t launch_stage_simt(int N, int mode, const StageArgs &a, cudaStream_t 
   case 5: return launch_simt_order<5>(mode, a, s);
   case 6: return launch_simt_order<6>(mode, a, s);
   case 7: return launch_simt_order<7>(mode, a, s);
+  case 8: return launch_simt_order<8>(mode, a, s);
+  case 9: return launch_simt_order<9>(mode, a, s);
   default: return cudaErrorInvalidValue;
   }
 }

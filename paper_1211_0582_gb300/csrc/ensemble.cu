@@ -31,6 +31,8 @@ int ensemble_candidate_eb_n4(int);
 int ensemble_candidate_eb_n5(int);
 int ensemble_candidate_eb_n6(int);
 int ensemble_candidate_eb_n7(int);
+int ensemble_candidate_eb_n8(int);
+int ensemble_candidate_eb_n9(int);
 
 extern template cudaError_t launch_ensemble_order<1>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
 extern template cudaError_t launch_ensemble_order<2>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
@@ -39,6 +41,8 @@ extern template cudaError_t launch_ensemble_order<4>(int, const StageArgs &, con
 extern template cudaError_t launch_ensemble_order<5>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
 extern template cudaError_t launch_ensemble_order<6>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
 extern template cudaError_t launch_ensemble_order<7>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
+extern template cudaError_t launch_ensemble_order<8>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
+extern template cudaError_t launch_ensemble_order<9>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
 
 namespace {
 
@@ -53,7 +57,9 @@ int candidate_eb(int N, int i) {
   case 4: return ensemble_candidate_eb_n4(i);
   case 5: return ensemble_candidate_eb_n5(i);
   case 6: return ensemble_candidate_eb_n6(i);
-  default: return ensemble_candidate_eb_n7(i);
+  case 7: return ensemble_candidate_eb_n7(i);
+  case 8: return ensemble_candidate_eb_n8(i);
+  default: return ensemble_candidate_eb_n9(i);
   }
 }
 
@@ -66,7 +72,9 @@ cudaError_t launch_ensemble(int N, int cand, const StageArgs &a, const StageCoef
   case 4: return launch_ensemble_order<4>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
   case 5: return launch_ensemble_order<5>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
   case 6: return launch_ensemble_order<6>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  default: return launch_ensemble_order<7>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  case 7: return launch_ensemble_order<7>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  case 8: return launch_ensemble_order<8>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  default: return launch_ensemble_order<9>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
   }
 }
 

@@ -7,7 +7,7 @@
 
 namespace dgmx {
 
-constexpr int kMaxOrder = 7;
+constexpr int kMaxOrder = 9; // node indices fit the uint8_t tables up to N = 9 (Np = 220)
 
 inline int num_nodes(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
 inline int num_face_nodes(int N) { return (N + 1) * (N + 2) / 2; }

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_host_operators_match_oracle(N):
     s = dg.Solver(N, stream=None)
     ops = s.operators()
@@ -57,7 +57,7 @@ def test_create_rejects_bad_arguments():
     L = dg.lib()
     h = C.c_void_p()
     assert L.dg_create(C.byref(h), 0, 0, None) == -1
-    assert L.dg_create(C.byref(h), 8, 0, None) == -1
+    assert L.dg_create(C.byref(h), 10, 0, None) == -1
     assert L.dg_create(C.byref(h), 3, 9, None) == -1
     assert b"precision" in L.dg_last_error(None)
     assert L.dg_create(None, 3, 0, None) == -1

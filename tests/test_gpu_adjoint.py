@@ -34,7 +34,7 @@ def setup(N, n, eps_seed=2):
     return s, m, eps
 
 
-@pytest.mark.parametrize("N,n", [(2, 3), (4, 3), (5, 2), (7, 2)])
+@pytest.mark.parametrize("N,n", [(2, 3), (4, 3), (5, 2), (7, 2), (9, 1)])
 def test_transpose_parity_and_identity(N, n):
     s, m, _ = setup(N, n)
     rng = np.random.default_rng(3)

@@ -34,7 +34,7 @@ def random_fields(shape, seed=11):
     return np.random.default_rng(seed).standard_normal(shape)
 
 
-@pytest.mark.parametrize("N,n", [(1, 3), (2, 3), (3, 4), (4, 3), (5, 4), (6, 2), (7, 3)])
+@pytest.mark.parametrize("N,n", [(1, 3), (2, 3), (3, 4), (4, 3), (5, 4), (6, 2), (7, 3), (8, 2), (9, 2)])
 @pytest.mark.parametrize("alpha", [1.0, 0.0])
 def test_rhs_parity(N, n, alpha):
     s, m = setup_pair(N, n)
@@ -92,7 +92,7 @@ def test_lserk_step_parity(N):
     assert rel_l2(s.from_device(ud), ref4) < TOL_FP32
 
 
-@pytest.mark.parametrize("N,n", [(1, 3), (4, 3), (5, 3), (7, 2)])
+@pytest.mark.parametrize("N,n", [(1, 3), (4, 3), (5, 3), (7, 2), (9, 2)])
 def test_energy_matches_oracle(N, n):
     # tiles of 256 / (Np_pad / 4) field rows; these sizes leave a ragged last tile
     s, m = setup_pair(N, n)
@@ -184,3 +184,21 @@ def test_cavity_h_convergence(precision, N):
         # at N=5 the method's error on these meshes is below the FP32 resolution
         # of the state: both runs sit at the FP32 floor
         assert max(errs) < 2e-6
+
+
+@pytest.mark.parametrize("N", [8, 9])
+def test_high_order_step_parity_and_tensor_core_limit(N):
+    # orders 8 and 9 (the paper's multi-GPU runs go up to N = 9): FP32 LSERK4
+    # steps against the oracle on a jittered mesh with eps in [1, 4]; the
+    # tensor-core precisions stop at N = 7 and say so at upload
+    s, m = setup_pair(N, 2)
+    x, y, z = m.coords()
+    u0 = W.cavity_mode(x, y, z, 0.0) + W.gaussian_pulse(x, y, z, seed=7)
+    dt = 0.5 / 2 / N ** 2
+    ud, rd = s.to_device(u0), s.zeros()
+    s.step(ud, rd, dt, 3)
+    ref, _ = m.lserk(u0, dt, 3)
+    assert rel_l2(s.from_device(ud), ref) < TOL_FP32
+    with pytest.raises(dg.DGError) as e:
+        setup_pair(N, 2, precision="fp16x3")
+    assert e.value.code == -6

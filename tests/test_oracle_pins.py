@@ -39,7 +39,7 @@ def _bary(r, s, t):
     return np.stack([-(1 + r + s + t) / 2, (1 + r) / 2, (1 + s) / 2, (1 + t) / 2], 1)
 
 
-@pytest.mark.parametrize("N", [3, 4, 5, 7])
+@pytest.mark.parametrize("N", [3, 4, 5, 7, 9])
 def test_nodes_symmetric_and_edge_lgl(N):
     r, s, t = O.nodes(N)
     L = _bary(r, s, t)
@@ -66,7 +66,7 @@ def _dirichlet(powers, dim):
     return num / math.factorial(sum(powers) + dim) * vol
 
 
-@pytest.mark.parametrize("N", [1, 3, 5, 7])
+@pytest.mark.parametrize("N", [1, 3, 5, 7, 9])
 def test_derivative_exact_on_monomials(N):
     ops = O.operators(N)
     r, s, t = O.nodes(N)
@@ -83,7 +83,7 @@ def test_derivative_exact_on_monomials(N):
     assert err < 1e-11 * max(1, N ** 2)
 
 
-@pytest.mark.parametrize("N", [2, 4, 7])
+@pytest.mark.parametrize("N", [2, 4, 7, 9])
 def test_mass_matrix_integrates_exactly(N):
     ops = O.operators(N)
     L = _bary(*O.nodes(N))
