@@ -60,9 +60,29 @@ struct AdjCfg {
   static constexpr int EB2 = 80 / D::NQ > 0 ? 80 / D::NQ : 1; // elements per volume block (measured best)
   static constexpr int NT2 = (EB2 * D::NQ + 31) / 32 * 32;
   static constexpr size_t SMEM1 = size_t(6) * EB1 * D::NPP * 4;
-  static constexpr size_t SMEM2 = size_t(EB2) * 4 * 64 + (size_t(6) * EB2 * D::NPP * 3 + EB2) * 4 +
+  static constexpr size_t SMEM2 = size_t(EB2) * 4 * 64 + (size_t(6) * EB2 * D::NPP * 2 + EB2) * 4 +
                                   ((200 * D::NFP + 15) / 16) * 16;
 };
+
+// s[e] += v summed over the lanes of the warp that share e: a warp's lanes
+// hold a few consecutive element indices, so for each distinct e the warp sums
+// its lanes' values (shuffle tree) and one lane adds the sum to shared memory
+// (instead of up to 32 lanes adding to one address). Every lane of the warp
+// must call it.
+__device__ __forceinline__ void add_by_element(float *s, int e, float v) {
+  const int lane = threadIdx.x & 31;
+  unsigned rest = 0xffffffffu;
+  while (rest) {
+    const int src = __ffs(rest) - 1;
+    const int e0 = __shfl_sync(0xffffffffu, e, src);
+    const bool mine = e == e0;
+    rest &= ~__ballot_sync(0xffffffffu, mine);
+    float sum = mine ? v : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == src && sum != 0.f) atomicAdd(s + e0, sum);
+  }
+}
 
 __device__ __forceinline__ void cross3(const float *a, const float *b, float *c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
@@ -208,8 +228,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
   float4 *s_face = smem4;                                 // [EB * 4][4]
   float *s_v = reinterpret_cast<float *>(smem4 + EB * 16); // W lr   [6][EB][NPP]
   float *s_w = s_v + 6 * EB * NPP;               // surface contributions [6][EB][NPP]
-  float *s_us = s_w + 6 * EB * NPP;              // stage state u_s of the block's elements [6][EB][NPP]
-  float *s_gr = s_us + 6 * EB * NPP;             // gradient partial per element [EB]
+  float *s_gr = s_w + 6 * EB * NPP;              // gradient partial per element [EB]
   uint8_t *s_fm = reinterpret_cast<uint8_t *>(s_gr + EB);
   uint8_t *s_nb = s_fm + NFF, *s_nf = s_nb + kConnKinds * NFP;
   const int tid = threadIdx.x;
@@ -256,32 +275,35 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
     }
     reinterpret_cast<float4 *>(s_v)[(c * EB + e) * NQ + q] = v;
     reinterpret_cast<float4 *>(s_w)[(c * EB + e) * NQ + q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (GRAD)
-      reinterpret_cast<float4 *>(s_us)[(c * EB + e) * NQ + q] =
-          k < a.K ? *reinterpret_cast<const float4 *>(a.u_s + c * KN + k * NPP + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
 
   // -- eps gradient, term of the 1/eps factor: -(1/eps) <lr_E, rhs_E> = -<W lr_E, rhs_E>
   if (GRAD) {
-    for (int idx = tid; idx < 3 * EB * NQ; idx += NT) {
-      const int c = idx / (EB * NQ), rem = idx - c * (EB * NQ);
+    for (int i0 = 0; i0 < 3 * EB * NQ; i0 += NT) { // whole rounds: every lane takes part in the sums
+      const int idx = i0 + tid;
+      const int rem = idx % (EB * NQ);
       const int e = rem / NQ, q = rem - e * NQ;
-      const int64_t k = k0 + e;
-      if (k >= a.K) continue;
-      const float4 r = *reinterpret_cast<const float4 *>(a.rhs_s + c * KN + k * NPP + 4 * q);
-      const float4 v = reinterpret_cast<const float4 *>(s_v)[(c * EB + e) * NQ + q];
-      atomicAdd(&s_gr[e], -(v.x * r.x + v.y * r.y + v.z * r.z + v.w * r.w));
+      const int c = idx / (EB * NQ);
+      float part = 0.f;
+      if (idx < 3 * EB * NQ && k0 + e < a.K) {
+        const float4 r = *reinterpret_cast<const float4 *>(a.rhs_s + c * KN + (k0 + e) * NPP + 4 * q);
+        const float4 v = reinterpret_cast<const float4 *>(s_v)[(c * EB + e) * NQ + q];
+        part = -(v.x * r.x + v.y * r.y + v.z * r.z + v.w * r.w);
+      }
+      add_by_element(s_gr, e, part);
     }
   }
 
   // -- transposed flux Jacobians (interior side with own g, exterior side with
   //    the neighbour's g at the matching face node) and the weight terms of the
   //    eps gradient, one face node per item
-  for (int it = tid; it < EB * NFF; it += NT) {
-    const int e = it / NFF, fm = it - e * NFF, f = fm / NFP, m = fm - f * NFP;
+  for (int it0 = 0; it0 < EB * NFF; it0 += NT) { // whole rounds: every lane takes part in the sums
+    const int it = it0 + tid;
+    const int e = (it < EB * NFF ? it : EB * NFF - 1) / NFF, fm = it - e * NFF, f = fm / NFP, m = fm - f * NFP;
     const int64_t k = k0 + e;
-    if (k >= a.K) continue;
+    float contrib = 0.f;
+    if (it < EB * NFF && k < a.K) {
     const float4 *fr = s_face + (e * 4 + f) * 4;
     const float4 r0 = fr[0], r1 = fr[1], r2 = fr[2], r3 = fr[3];
     const float n[3] = {r0.x, r0.y, r0.z};
@@ -328,7 +350,7 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
       const float dZ = r2.y, dY = r2.z;
       float qm[6], qp[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) qm[c] = s_us[(c * EB + e) * NPP + vm];
+      for (int c = 0; c < 6; ++c) qm[c] = __ldg(a.u_s + c * KN + k * NPP + vm);
       if (wall) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -337,18 +359,12 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
         }
       } else {
         const int vn = s_nb[cny * NFP + m];
-        const int64_t e2 = k2 - k0; // neighbours inside the block come from shared memory
-        if (e2 >= 0 && e2 < EB) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) qp[c] = s_us[(c * EB + int(e2)) * NPP + vn];
-        } else {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) qp[c] = __ldg(a.u_s + c * KN + k2 * NPP + vn);
-        }
+        for (int c = 0; c < 6; ++c) qp[c] = __ldg(a.u_s + c * KN + k2 * NPP + vn);
       }
       float sZm, sZp, sYm, sYp;
       flux_weight_partials_w(n, qm, qp, Z2, Y2, zs, ys, a.alpha, gk, sZm, sZp, sYm, sYp);
-      float contrib = sZm * dZ + sYm * dY;
+      contrib = sZm * dZ + sYm * dY;
       if (wall) {
         contrib += sZp * dZ + sYp * dY; // the mirrored exterior carries the same weights
       } else {
@@ -357,8 +373,9 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
         flux_weight_partials_w(n2, qp, qm, Zk, Yk, zs, ys, a.alpha, g2, tZm, tZp, tYm, tYp);
         contrib += tZp * dZ + tYp * dY;
       }
-      atomicAdd(&s_gr[e], contrib);
     }
+    }
+    if (GRAD) add_by_element(s_gr, e, contrib);
   }
   __syncthreads();
 
