@@ -64,10 +64,14 @@ def bytes_per_element(N: int, Npad: int) -> float:
 
 # DRAM bytes (read + write) per launch of the stage kernel, the mean over the
 # five stages of one step, from an ncu capture of the current kernel;
-# keyed by (precision, N, hexahedra per edge); absent where no capture of the
-# current kernel exists. The N=7 32^3 entry is the 16^3 capture scaled by the
-# element count (x8).
-NCU_TRAFFIC = {("fp16x3", 5, 24): 387.582e6, ("fp16x3", 7, 16): 218.986e6, ("fp16x3", 7, 32): 8 * 218.986e6}
+# keyed by (precision, N, hexahedra per edge, element order); absent where no
+# capture of the current kernel exists. The N=7 32^3 entries are the 16^3
+# captures scaled by the element count (x8).
+NCU_TRAFFIC = {
+    ("fp16x3", 5, 24, "hilbert"): 391.87e6, ("fp16x3", 5, 24, "lexicographic"): 387.582e6,
+    ("fp16x3", 7, 16, "hilbert"): 219.45e6, ("fp16x3", 7, 16, "lexicographic"): 218.986e6,
+    ("fp16x3", 7, 32, "hilbert"): 8 * 219.45e6, ("fp16x3", 7, 32, "lexicographic"): 8 * 218.986e6,
+}
 
 
 def measured_peaks():
@@ -149,20 +153,20 @@ def job_gdof_s(world: int, dof: int, steps: int, ms: float) -> float:
     return world * STAGES * dof * steps / (ms * 1e-3) / 1e9
 
 
-def make_workload(N: int, n: int):
+def make_workload(N: int, n: int, order: str = "hilbert"):
     import workloads as W
-    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1, order=order)
     return VX, VY, VZ, EToV
 
 
-def cpu_oracle_rate(N: int, n: int, sample_elems: int, reps: int = 1):
+def cpu_oracle_rate(N: int, n: int, sample_elems: int, reps: int = 1, order: str = "hilbert"):
     """Oracle (FP64, single thread) right-hand side on a fixed element sample of
     the same mesh: returns (GDOF/s per RHS, seconds, elements)."""
     import numpy as np
 
     import oracle as O
     import workloads as W
-    VX, VY, VZ, EToV = make_workload(N, n)
+    VX, VY, VZ, EToV = make_workload(N, n, order)
     m = O.Mesh(N, VX, VY, VZ, EToV)
     x, y, z = m.coords()
     u = W.cavity_mode(x, y, z, 0.0)
@@ -183,7 +187,7 @@ def run_reference(args):
     N, n = args.order, args.n
     Np = (N + 1) * (N + 2) * (N + 3) // 6
     # size the per-step sample so that one step (5 RHS evaluations) takes about a second
-    _, t1, e1, m, u, _ = cpu_oracle_rate(N, n, 256)
+    _, t1, e1, m, u, _ = cpu_oracle_rate(N, n, 256, order=args.element_order)
     per_elem = t1 / e1
     sample = int(max(64, min(m.K, 1.0 / (STAGES * per_elem))))
     import numpy as np
@@ -214,7 +218,8 @@ def run_reference(args):
 def config_dict(args, K, Np):
     return {"workload": f"PEC cube cavity, {args.n}^3x6 jittered tets, N={args.order}, upwind, LSERK4",
             "K": int(K), "N": args.order, "Np": Np, "dof": 6 * Np * int(K), "rhs_per_step": STAGES,
-            "precision": args.precision, "l2": "inputs larger than L2 (u, res, u_out: 3 x 6 K Np_pad x 4 B per stage)",
+            "precision": args.precision, "element_order": args.element_order,
+            "l2": "inputs larger than L2 (u, res, u_out: 3 x 6 K Np_pad x 4 B per stage)",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -237,7 +242,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     N, n = args.order, args.n
-    VX, VY, VZ, EToV = make_workload(N, n)
+    VX, VY, VZ, EToV = make_workload(N, n, args.element_order)
     K = EToV.shape[0]
     s = dg.Solver(N, precision=args.precision, stream=stream).upload(VX, VY, VZ, EToV)
     x, y, z = s.node_coords()
@@ -325,13 +330,13 @@ def run_ours(args):
         peak_tf = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         achieved = flops_per_element(N) * K / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": args.traffic or NCU_TRAFFIC.get((args.precision, N, n)),
+                "frac": achieved / peak_tf, "traffic": args.traffic or NCU_TRAFFIC.get((args.precision, N, n, args.element_order)),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
     else:
         peak = peaks["hbm_gbs"]
         achieved = bytes_per_element(N, Npad) * K / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": args.traffic or NCU_TRAFFIC.get((args.precision, N, n)),
+                "traffic": args.traffic or NCU_TRAFFIC.get((args.precision, N, n, args.element_order)),
                 "algorithmic_bytes": bytes_per_element(N, Npad) * K, "peak_source": f"hbm_gbs ({peak_kind})"}
 
     line = {
@@ -351,7 +356,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_precisions:
         line["precisions"] = precision_legs(args, stream, headline=(s, args.precision))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs, ne, *_ = cpu_oracle_rate(N, n, args.cpu_sample)
+        rate, secs, ne, *_ = cpu_oracle_rate(N, n, args.cpu_sample, order=args.element_order)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"1 oracle RHS on {ne} of {K} elements ({secs:.1f} s, FP64, 1 thread)"}
     if rank == 0:
@@ -378,7 +383,7 @@ def precision_legs(args, stream, headline=None):
     peaks, peak_kind = measured_peaks()
     out = {}
     for name in ("cavity_n5_24cube_500steps", "precision_n7_32cube_200steps"):
-        c, mesh, eps, dt = R.setup(name)
+        c, mesh, eps, dt = R.setup(name, args.element_order)
         try:
             ref = R.load(name)
         except OSError:
@@ -386,7 +391,7 @@ def precision_legs(args, stream, headline=None):
         N, K = c["N"], mesh[3].shape[0]
         leg = {"workload": f"{c['n']}^3x6 = {K} jittered tets, N={N}, "
                            f"{'eps U[1,4] per element' if eps is not None else 'eps=mu=1'}, cavity-mode start, "
-                           f"upwind, LSERK4 dt=0.5h/N^2",
+                           f"upwind, LSERK4 dt=0.5h/N^2, {args.element_order} element order",
                "error_reference": None if ref is None else str(ref["source"]),
                "error_steps": c["steps"], "error_samples": None if ref is None else int(ref["idx"].size)}
         u0_host = None
@@ -411,12 +416,13 @@ def precision_legs(args, stream, headline=None):
                 e["alu_frac"] = flops_per_element(N) * K / (launch_ms * 1e-3) / 1e12 / peak_tf
             else:
                 e["hbm_frac"] = bytes_per_element(N, sv.Npad) * K / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
-                e["traffic"] = NCU_TRAFFIC.get((prec, N, c["n"]))
+                e["traffic"] = NCU_TRAFFIC.get((prec, N, c["n"], args.element_order))
             if ref is not None:
                 u, r = sv.to_device(u0_host), sv.zeros()
                 sv.step(u, r, dt, c["steps"])
                 sv.sync()
-                got = u[:, :, :sv.Np].reshape(-1)[torch_index(ref["idx"], u.device)].double().cpu().numpy()
+                idx = R.renumber_samples(ref["idx"], c["n"], args.element_order, sv.Np)
+                got = u[:, :, :sv.Np].reshape(-1)[torch_index(idx, u.device)].double().cpu().numpy()
                 e["rel_l2_vs_fp64"] = float(np.linalg.norm(got - ref["ref"]) / np.linalg.norm(ref["ref"]))
                 e["max_abs_err_rel_to_max"] = float(np.abs(got - ref["ref"]).max() / float(ref["max_full"]))
             leg[prec] = e
@@ -650,6 +656,8 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16x3", "fp16x3"], default="fp16x3")
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--n", type=int, default=24, help="hexahedra per cube edge")
+    ap.add_argument("--element-order", choices=["hilbert", "lexicographic"], default="hilbert",
+                    help="element numbering of the cube mesh (hexahedra along a 3D Hilbert curve, or x fastest)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--e2e-streams", type=int, default=4, help="contexts/streams the end-to-end steps alternate over")
     ap.add_argument("--cpu-sample", type=int, default=50000, help="elements in the oracle CPU sample")

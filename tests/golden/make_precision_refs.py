@@ -53,15 +53,30 @@ def sample_indices(K: int, Np: int) -> np.ndarray:
     return np.unique((W.uniform(SAMPLE_SEED, SAMPLES) * total).astype(np.int64))
 
 
-def setup(name: str):
+def setup(name: str, order: str = "lexicographic"):
     """Mesh, materials, initial field generator and step size of a workload
-    (shared by this script and the benchmark; no method arithmetic)."""
+    (shared by this script and the benchmark; no method arithmetic). The stored
+    samples index the lexicographic element order; `order` renumbers the same
+    elements (each keeps its vertices and its material)."""
     c = CONFIGS[name]
-    VX, VY, VZ, EToV = W.kuhn_cube(c["n"], jitter=0.1, seed=1)
+    VX, VY, VZ, EToV = W.kuhn_cube(c["n"], jitter=0.1, seed=1, order=order)
     K = EToV.shape[0]
-    eps = None if c["eps_seed"] is None else W.element_eps(K, seed=c["eps_seed"])
+    eps = None if c["eps_seed"] is None else \
+        W.element_eps(K, seed=c["eps_seed"])[W.element_permutation(c["n"], order)]
     dt = 0.5 / c["n"] / c["N"] ** 2
     return c, (VX, VY, VZ, EToV), eps, dt
+
+
+def renumber_samples(idx: np.ndarray, n: int, order: str, Np: int) -> np.ndarray:
+    """Flat indices into a [6][K][Np] field vector of kuhn_cube(n) in the
+    lexicographic element order, moved to the numbering of kuhn_cube(n, order=order)."""
+    perm = W.element_permutation(n, order)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    K = perm.size
+    f, rem = np.divmod(idx, K * Np)
+    e, j = np.divmod(rem, Np)
+    return f * K * Np + inv[e] * Np + j
 
 
 def write(name: str) -> None:
