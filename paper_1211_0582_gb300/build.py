@@ -2,7 +2,9 @@
 
 Every translation unit under csrc/ is compiled in parallel into
 _build/*.o and linked into paper_1211_0582_gb300/_build/libdgmx.so. Objects
-are rebuilt when their source or any header changed.
+are rebuilt when their source or any header changed. `defines` and `out_dir`
+make a separate build with extra preprocessor macros (the timing build of
+stage_timing.py: -DDGMX_STAGE_TIMING into _build_timing/).
 """
 from __future__ import annotations
 
@@ -32,16 +34,17 @@ def _headers():
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, defines=(), out_dir: str = OUT_DIR) -> str:
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "libdgmx.so")
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr_time = max((os.path.getmtime(h) for h in _headers()), default=0.0)
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                     "-Xptxas", "-warn-spills"]
+                     "-Xptxas", "-warn-spills"] + [f"-D{d}" for d in defines]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time):
             return obj, ""
         cmd = [nvcc] + common + ["-c", src, "-o", obj + ".tmp"]
@@ -61,11 +64,11 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         for o, log in results:
             if log.strip():
                 print(os.path.basename(o), log, file=sys.stderr)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -528,9 +528,40 @@ int fail(dg_ctx *ctx, int code, const std::string &msg) {
 // context between calls (an optimisation loop calls them many times) and grown
 // on demand; released with the mesh.
 struct AdjWorkspace {
-  static constexpr int kSlots = 16;
+  static constexpr int kSlots = 20;
   void *p[kSlots] = {};
   size_t cap[kSlots] = {};
+  // a second stream for recomputing one checkpoint segment while the reverse
+  // sweep of the next runs, and the events that order the two
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fwd = nullptr, ev_rec[2] = {}, ev_rev[2] = {};
+  bool streams_ready() {
+    if (s2) return true;
+    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s2 = nullptr;
+      return false;
+    }
+    bool ok = cudaEventCreateWithFlags(&ev_fwd, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 2; ++i) {
+      ok = ok && cudaEventCreateWithFlags(&ev_rec[i], cudaEventDisableTiming) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&ev_rev[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      release_streams();
+    }
+    return ok;
+  }
+  void release_streams() {
+    if (s2) cudaStreamSynchronize(s2);
+    for (cudaEvent_t *ev : {&ev_fwd, &ev_rec[0], &ev_rec[1], &ev_rev[0], &ev_rev[1]}) {
+      if (*ev) cudaEventDestroy(*ev);
+      *ev = nullptr;
+    }
+    if (s2) cudaStreamDestroy(s2);
+    s2 = nullptr;
+  }
   template <class T>
   T *get(int slot, size_t count) {
     const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
@@ -548,6 +579,7 @@ struct AdjWorkspace {
     return static_cast<T *>(p[slot]);
   }
   ~AdjWorkspace() {
+    release_streams();
     for (void *q : p)
       if (q) cudaFree(q);
   }
@@ -750,6 +782,10 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
     if (C < 1) C = 1;
   }
   if (C > nsteps) C = nsteps;
+  // with checkpoint segments, two segment buffers: one is recomputed (second
+  // stream) while the reverse sweep reads the other; the automatic size
+  // halves C so that both fit where one would
+  if (ckpt_every == 0 && C < nsteps && C > 1) C /= 2;
   // segments are aligned to the end of the run: all but the first have C
   // steps; the last one is stored during the forward sweep, the others are
   // recomputed from their checkpoints
@@ -767,6 +803,19 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   if (!u || !nxt || !res || !lu || !lr || !g || !resid || !Jd || !grad || !ck || !US || !RS)
     return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed (checkpoints and one segment of stage "
                                  "states are kept in device memory)");
+  // the second segment buffer and the recompute stream's scratch; without
+  // them (no memory, no stream) the segments are recomputed in turn on the
+  // caller's stream
+  float *USb[2] = {US, nullptr}, *RSb[2] = {RS, nullptr}, *res2 = nullptr, *nxt2 = nullptr;
+  bool overlap = nseg > 1 && ws.streams_ready();
+  if (overlap) {
+    USb[1] = ws.get<float>(12, fl * 5 * C);
+    RSb[1] = ws.get<float>(13, hfl * 5 * C);
+    res2 = ws.get<float>(14, fl);
+    nxt2 = ws.get<float>(15, fl);
+    overlap = USb[1] && RSb[1] && res2 && nxt2;
+  }
+  if (!overlap) USb[1] = US, RSb[1] = RS, res2 = res, nxt2 = nxt;
   cudaError_t e = cudaMemcpyAsync(u, u0, fl * 4, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(res, 0, fl * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Jd, 0, sizeof(double), s);
@@ -776,22 +825,23 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   StageArgs sa = stage_base(ctx, alpha, dt);
   const unsigned rb = unsigned((3 * R + 255) / 256);
 
-  // one step of the stored form: every stage state and the E components of
-  // its right-hand side go to the segment buffers (state j of the segment
-  // that starts at checkpoint sg); returns the state after the step
-  auto stored_step = [&](int n, int n0, int sg) -> const float * {
-    sa.res = res;
+  // one step of the stored form on stream `st_`: every stage state and the E
+  // components of its right-hand side go to segment buffer b (state j of the
+  // segment that starts at checkpoint sg); returns the state after the step
+  auto stored_step = [&](int n, int n0, int sg, int b, cudaStream_t st_, float *res_, float *nxt_) -> const float * {
+    StageArgs q = sa;
+    q.res = res_;
     for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
       const size_t j = size_t(n - n0) * 5 + st;
-      sa.u = j == 0 ? ck + fl * sg : US + fl * j;
-      sa.u_out = (j + 1 < size_t(5) * C) ? US + fl * (j + 1) : nxt;
-      sa.rhs = RS + hfl * j;
-      sa.rk_a = float(kLserkA[st]);
-      sa.rk_b = float(kLserkB[st]);
-      e = launch_stage_simt(ctx->N, MODE_LSERK_STORE, sa, s);
+      q.u = j == 0 ? ck + fl * sg : USb[b] + fl * j;
+      q.u_out = (j + 1 < size_t(5) * C) ? USb[b] + fl * (j + 1) : nxt_;
+      q.rhs = RSb[b] + hfl * j;
+      q.rk_a = float(kLserkA[st]);
+      q.rk_b = float(kLserkB[st]);
+      e = launch_stage_simt(ctx->N, MODE_LSERK_STORE, q, st_);
     }
     const size_t jn = size_t(n - n0 + 1) * 5;
-    return jn < size_t(5) * C ? US + fl * jn : nxt;
+    return jn < size_t(5) * C ? USb[b] + fl * jn : nxt_;
   };
 
   // ---- forward sweep: checkpoints at the segment starts, the last segment
@@ -804,7 +854,7 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
     }
     const float *after = u;
     if (n >= n0_last) {
-      after = stored_step(n, n0_last, nseg - 1);
+      after = stored_step(n, n0_last, nseg - 1, (nseg - 1) % 2, s, res, nxt);
     } else {
       sa.res = res;
       for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
@@ -830,11 +880,26 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   aa.grad = grad;
   aa.dt = float(dt);
   float pending = 1.f; // a of the stage reversed last, applied to lr by the next lift
+  // with two segment buffers, segment seg lives in buffer seg % 2, and the
+  // segment before it is recomputed on the second stream while seg is reversed
+  if (overlap && e == cudaSuccess) e = cudaEventRecord(ws.ev_fwd, s);
+  if (overlap && e == cudaSuccess) e = cudaStreamWaitEvent(ws.s2, ws.ev_fwd, 0);
   for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
     const int n0 = seg_start(seg), n1 = seg + 1 < nseg ? seg_start(seg + 1) : nsteps;
-    // recompute the segment from its checkpoint (the last one is already stored)
-    if (seg < nseg - 1)
-      for (int n = n0; n < n1 && e == cudaSuccess; ++n) stored_step(n, n0, seg);
+    const int b = seg % 2;
+    if (overlap) {
+      // segment seg - 1 into the buffer that the reverse sweep of seg + 1 has released
+      if (seg >= 1) {
+        if (seg + 1 < nseg) e = cudaStreamWaitEvent(ws.s2, ws.ev_rev[(seg + 1) % 2], 0);
+        const int p0 = seg_start(seg - 1);
+        for (int n = p0; n < n0 && e == cudaSuccess; ++n) stored_step(n, p0, seg - 1, (seg - 1) % 2, ws.s2, res2, nxt2);
+        if (e == cudaSuccess) e = cudaEventRecord(ws.ev_rec[(seg - 1) % 2], ws.s2);
+      }
+      if (seg < nseg - 1 && e == cudaSuccess) e = cudaStreamWaitEvent(s, ws.ev_rec[b], 0);
+    } else if (seg < nseg - 1) {
+      // recompute the segment from its checkpoint (the last one is already stored)
+      for (int n = n0; n < n1 && e == cudaSuccess; ++n) stored_step(n, n0, seg, b, s, res, nxt);
+    }
     for (int n = n1 - 1; n >= n0 && e == cudaSuccess; --n) {
       k_recv_source<<<rb, 256, 0, s>>>(lu, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, resid + int64_t(n) * 3 * R);
       e = cudaGetLastError();
@@ -849,12 +914,19 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
         if (e != cudaSuccess) break;
         aa.lr_out = nullptr;
         aa.lu_out = lu;
-        aa.u_s = j == 0 ? ck + fl * seg : US + fl * j;
-        aa.rhs_s = RS + hfl * j;
+        aa.u_s = j == 0 ? ck + fl * seg : USb[b] + fl * j;
+        aa.rhs_s = RSb[b] + hfl * j;
         e = launch_adj(ctx->N, 1, aa, s); // lu += dt A^T lr; grad
         pending = float(kLserkA[st]);
       }
     }
+    if (overlap && e == cudaSuccess) e = cudaEventRecord(ws.ev_rev[b], s);
+  }
+  // the second stream's work is all ordered before the last reverse sweep;
+  // after an error it may still run, so it is drained before returning
+  if (overlap) {
+    const cudaError_t e2 = cudaStreamSynchronize(ws.s2);
+    if (e == cudaSuccess) e = e2;
   }
   double Jh = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&Jh, Jd, sizeof(double), cudaMemcpyDeviceToHost, s);

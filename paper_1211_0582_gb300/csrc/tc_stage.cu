@@ -196,6 +196,27 @@ struct EnsLaunch {
   GridBarrier *gb;
 };
 
+// Optional phase timestamps of the single-tile kernel below (build with
+// -DDGMX_STAGE_TIMING; off in the library): thread 0's SM clock, in cycles
+// since the block passed its setup, at the phase boundaries of each tile
+// (slots 0-9 and 12), and the times at which the first and the last warp
+// finished their fluxes (slots 11, 10); per block and tile of a single-stage
+// launch, read back with dgmx_tc_trace(). paper_1211_0582_gb300/stage_timing.py
+// builds that library and prints the breakdown.
+constexpr int kTraceTiles = 32, kTraceEvents = 32, kTraceBlocks = 160, kTcEvents = 16;
+#ifdef DGMX_STAGE_TIMING
+__device__ uint32_t g_tc_trace[kTraceBlocks * kTraceTiles * kTcEvents];
+#define TC_MARK(ev)                                                                                                 \
+  do {                                                                                                              \
+    if (!ENS && tid == 0 && itn < kTraceTiles && blockIdx.x < kTraceBlocks)                                         \
+      g_tc_trace[(blockIdx.x * kTraceTiles + itn) * kTcEvents + (ev)] = uint32_t(clock64() - tc_t0);                \
+  } while (0)
+#else
+#define TC_MARK(ev) \
+  do {              \
+  } while (0)
+#endif
+
 // ENS = false: one stage (MODE_RHS or MODE_LSERK) over all tiles. ENS = true:
 // 5 * nsteps LSERK stages in one cooperative launch, a grid barrier after each
 // stage (a stage reads the neighbours' states the previous one wrote), field
@@ -275,6 +296,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   // stage after stage: the setup above may overlap the end of the previous
   // stage, nothing it wrote is read before this point
   if constexpr (!ENS) pdl_wait();
+#ifdef DGMX_STAGE_TIMING
+  const long long tc_t0 = clock64();
+  __shared__ uint32_t s_fend[2]; // last and first warp done with its fluxes
+  if (tid == 0) s_fend[0] = 0u, s_fend[1] = 0xffffffffu;
+#endif
 
   // field split: warp w writes the TMEM lanes of its quarter w % 4 (lane =
   // operand row) and K values 16 (w / 4) .. +15 of A1 (warps past K1 idle); an
@@ -338,6 +364,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       stage_tile(blockIdx.x, int(phase));
     }
     for (int tile = blockIdx.x; tile < tm.ntiles; tile += gridDim.x) {
+#ifdef DGMX_STAGE_TIMING
+      const int itn = (tile - int(blockIdx.x)) / int(gridDim.x);
+#endif
+      TC_MARK(0);
       if (!ENS && tile + int(gridDim.x) >= tm.ntiles) pdl_launch_next(); // this block's last tile
       const int64_t k0 = tm.start(tile);
       const int ne = tm.size(tile, a.K);
@@ -379,6 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         failed = true;
         break;
       }
+      TC_MARK(1);
       if (read_res && rloader) {
         umma::mbar_arrive_expect_tx(barR, 6u * rowbytes);
         for (int f = 0; f < 6; ++f) umma::bulk_g2s(s_res + f * FS, a.res + f * KN + k0 * NPP, rowbytes, barR);
@@ -411,6 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       umma::fence_before_sync();
       __syncthreads();
       if (!BF16 && tid < 128) s_rowmx[tid] = 0u;
+      TC_MARK(2);
 
       // ---- 3. local differentiation on the tensor cores (asynchronous)
       if (issuer) {
@@ -516,6 +548,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+#ifdef DGMX_STAGE_TIMING
+      if (lane == 0) {
+        const uint32_t tf = uint32_t(clock64() - tc_t0);
+        atomicMax(&s_fend[0], tf);
+        atomicMin(&s_fend[1], tf);
+      }
+#endif
+      TC_MARK(3);
       // the next tile's fields and face data: into the other slot during the
       // flux phase (N <= 4), or over this tile's once every thread is done
       // with them (N = 5)
@@ -529,6 +569,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       // the previous tile's bulk stores must have read the A2 bytes
       if (storer) umma::bulk_wait_read_all();
       __syncthreads();
+      TC_MARK(4);
+#ifdef DGMX_STAGE_TIMING
+      if (!ENS && tid == 0 && itn < kTraceTiles && blockIdx.x < kTraceBlocks) {
+        g_tc_trace[(blockIdx.x * kTraceTiles + itn) * kTcEvents + 10] = s_fend[0];
+        g_tc_trace[(blockIdx.x * kTraceTiles + itn) * kTcEvents + 11] = s_fend[1];
+      }
+      __syncthreads();
+      if (tid == 0) s_fend[0] = 0u, s_fend[1] = 0xffffffffu;
+#endif
       if (!T::PINGPONG && stager) {
         const bool more = tile + int(gridDim.x) < tm.ntiles;
         if (more) stage_tile(tile + gridDim.x, slot ^ 1);
@@ -568,6 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       umma::fence_proxy_async();
       __syncthreads();
+      TC_MARK(5);
 
       // ---- 6. flux lifting on the tensor cores; meanwhile the volume terms
       // from GEMM1: chain rule (eq. dg-reference-matrices) and curls
@@ -596,6 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         row_scale(__uint_as_float(s_ex2[lane_used ? 2 * e_loc + fld / 3 : 0] << 23), sc, inv2);
       }
       ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
+      TC_MARK(6);
       umma::fence_after_sync();
       float vol[CPP][8];
 #pragma unroll
@@ -620,8 +671,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
         }
       }
+      TC_MARK(7);
       ok = umma::mbar_wait_bounded(bar2, phase, wlim) && ok;
       if (read_res) ok = umma::mbar_wait_bounded(barR, rphase, wlim) && ok;
+      TC_MARK(12);
       // this slot's face and element data are rewritten by the staging after next
       umma::fence_proxy_async();
       if (__syncthreads_or(!ok)) {
@@ -636,6 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         failed = true;
         break;
       }
+      TC_MARK(8);
       umma::fence_after_sync();
 
       // ---- 7. epilogue: lifted flux, material scale, update; results go to the
@@ -684,6 +738,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       umma::fence_proxy_async();
       umma::fence_before_sync();
       __syncthreads();
+      TC_MARK(9);
       // ---- 8. write the tile back with asynchronous bulk stores; clear the
       // flux maxima for the next tile
       if (storer) {
@@ -757,11 +812,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #endif
 constexpr int kWsE = 8, kWsF = DGMX_WS_FLUX_WARPS;
 
-// Optional per-role timestamps (build with -DDGMX_WS_TIMING; off in the
+// Optional per-role timestamps (build with -DDGMX_STAGE_TIMING; off in the
 // library): SM clock cycles since the block's start at fixed points of each
 // role, per block and tile, read back with dgmx_ws_trace().
-constexpr int kTraceTiles = 32, kTraceEvents = 32, kTraceBlocks = 160;
-#ifdef DGMX_WS_TIMING
+#ifdef DGMX_STAGE_TIMING
 __device__ uint32_t g_ws_trace[kTraceBlocks * kTraceTiles * kTraceEvents];
 #define WS_MARK(t, ev)                                                                                              \
   do {                                                                                                              \
@@ -856,7 +910,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
   pdl_wait(); // nothing the previous stage writes is read before this point
-#ifdef DGMX_WS_TIMING
+#ifdef DGMX_STAGE_TIMING
   const long long ws_t0 = clock64();
 #endif
 
@@ -1479,7 +1533,10 @@ cudaError_t launch_tc_order(int mode, bool bf16, const StageArgs &a, const TcSta
 
 } // namespace
 
-#ifdef DGMX_WS_TIMING
+#ifdef DGMX_STAGE_TIMING
+extern "C" int dgmx_tc_trace(uint32_t *host) {
+  return int(cudaMemcpyFromSymbol(host, g_tc_trace, sizeof(g_tc_trace)));
+}
 extern "C" int dgmx_ws_trace(uint32_t *host) {
   return int(cudaMemcpyFromSymbol(host, g_ws_trace, sizeof(g_ws_trace)));
 }
