@@ -78,6 +78,21 @@ int dg_create(dg_ctx **out, int N, int precision, void *cuda_stream);
 /* Release the context and everything it owns. NULL is accepted. */
 int dg_destroy(dg_ctx *ctx);
 
+/* Interpolation nodes (Section 2: the warp & blend nodes of the paper's node
+ * reference, which names no blend parameter). dg_create builds the operators
+ * on the plain construction (alpha = 0); this rebuilds them, on the host, on
+ * the nodes whose face warps along edge (P, Q) are scaled by
+ * (1 + (alpha * l_R)^2), l_R the barycentric of the face's third vertex.
+ * alpha in [0, 10]. Only before a mesh is uploaded: with a mesh on ctx it
+ * fails and changes nothing. Needs no GPU.
+ * Errors: DG_ERR_ARG (alpha out of range, a mesh present). */
+int dg_set_node_alpha(dg_ctx *ctx, double alpha);
+
+/* Blend parameter of least Lebesgue constant for order N in 1..9, from a
+ * built-in table (a search over alpha in [0, 3] on equidistant lattices of the
+ * tetrahedron; 0 where no alpha lowers the constant, N <= 4); -1 outside 1..9. */
+double dg_optimised_node_alpha(int N);
+
 /* Message of the last failure on ctx ("" if none); valid until the next call.
  * ctx may be NULL (then the last failure of dg_create is reported). */
 const char *dg_last_error(const dg_ctx *ctx);

@@ -67,13 +67,19 @@ def lib():
             L.or_nfp.argtypes = [C.c_int]
             L.or_lgl.argtypes = [C.c_int, _dp]
             L.or_nodes.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.or_nodes_alpha.argtypes = [C.c_int, C.c_double, _dp, _dp, _dp]
+            L.or_lebesgue.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)]
             L.or_operators.argtypes = [C.c_int] + [C.c_void_p] * 8
+            L.or_operators_alpha.argtypes = [C.c_int, C.c_double] + [C.c_void_p] * 8
             L.or_basis.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.or_mesh_create.restype = C.c_void_p
             L.or_mesh_create.argtypes = [C.c_int, C.c_int64, _dp, _dp, _dp, C.c_int64, _ip32,
                                          C.c_void_p, C.c_void_p]
+            L.or_mesh_create_alpha.restype = C.c_void_p
+            L.or_mesh_create_alpha.argtypes = [C.c_int, C.c_double, C.c_int64, _dp, _dp, _dp, C.c_int64, _ip32,
+                                               C.c_void_p, C.c_void_p]
             L.or_mesh_destroy.argtypes = [C.c_void_p]
             L.or_mesh_K.argtypes = [C.c_void_p]
             L.or_mesh_K.restype = C.c_int64
@@ -122,21 +128,46 @@ def lgl(N: int) -> np.ndarray:
     return x
 
 
-def nodes(N: int):
+def nodes(N: int, alpha: float = 0.0):
+    """Warp & blend nodes of blend parameter alpha (0: the plain construction)."""
     Np = np_count(N)
     r, s, t = np.zeros(Np), np.zeros(Np), np.zeros(Np)
-    _check(lib().or_nodes(N, r, s, t))
+    if alpha == 0.0:
+        _check(lib().or_nodes(N, r, s, t))
+    else:
+        _check(lib().or_nodes_alpha(N, float(alpha), r, s, t))
     return r, s, t
 
 
-def operators(N: int) -> dict:
+def lebesgue(N: int, alpha: float = 0.0, M: int = 30) -> float:
+    """Lebesgue constant of those nodes on the order-M equidistant lattice."""
+    v = C.c_double()
+    _check(lib().or_lebesgue(N, float(alpha), M, C.byref(v)))
+    return v.value
+
+
+def optimal_alpha(N: int) -> float:
+    """Blend parameter of least Lebesgue constant, from the table written by
+    oracle/optimize_node_alpha.py (0 below N = 3, where the warp vanishes or
+    the nodes do not depend on it)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "node_alpha.txt")
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, a = line.split()[:2]
+                if int(n) == N:
+                    return float(a)
+    raise KeyError(f"no optimised blend parameter for N={N}")
+
+
+def operators(N: int, alpha: float = 0.0) -> dict:
     Np, Nfp = np_count(N), nfp_count(N)
     out = dict(V=np.zeros((Np, Np)), Dr=np.zeros((Np, Np)), Ds=np.zeros((Np, Np)),
                Dt=np.zeros((Np, Np)), M=np.zeros((Np, Np)),
                Fmask=np.zeros((4, Nfp), dtype=np.int32), Mf=np.zeros((4, Nfp, Nfp)),
                LIFT=np.zeros((Np, 4 * Nfp)))
-    _check(lib().or_operators(N, *[_ptr(out[k]) for k in
-                                   ("V", "Dr", "Ds", "Dt", "M", "Fmask", "Mf", "LIFT")]))
+    _check(lib().or_operators_alpha(N, float(alpha), *[_ptr(out[k]) for k in
+                                                       ("V", "Dr", "Ds", "Dt", "M", "Fmask", "Mf", "LIFT")]))
     return out
 
 
@@ -163,16 +194,17 @@ def lserk_coeffs():
 class Mesh:
     """Oracle mesh: connectivity, geometry and exterior-node map, all FP64."""
 
-    def __init__(self, N, VX, VY, VZ, EToV, eps=None, mu=None):
+    def __init__(self, N, VX, VY, VZ, EToV, eps=None, mu=None, node_alpha: float = 0.0):
         self.N = N
+        self.node_alpha = float(node_alpha)
         self.Np, self.Nfp = np_count(N), nfp_count(N)
         VX, VY, VZ = (np.ascontiguousarray(v, dtype=np.float64) for v in (VX, VY, VZ))
         EToV = np.ascontiguousarray(EToV, dtype=np.int32)
         self.K = EToV.shape[0]
         self._eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
         self._mu = None if mu is None else np.ascontiguousarray(mu, dtype=np.float64)
-        h = lib().or_mesh_create(N, VX.size, VX, VY, VZ, self.K, EToV,
-                                 _ptr(self._eps), _ptr(self._mu))
+        h = lib().or_mesh_create_alpha(N, self.node_alpha, VX.size, VX, VY, VZ, self.K, EToV,
+                                       _ptr(self._eps), _ptr(self._mu))
         if not h:
             raise RuntimeError("oracle: " + lib().or_error().decode())
         self._h = h

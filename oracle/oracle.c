@@ -165,24 +165,27 @@ static double warp_factor(int N, const double *xlgl, double r) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Warp & blend nodes on the tetrahedron (blend parameter alpha = 0),    */
+/* Warp & blend nodes on the tetrahedron (blend parameter alpha; 0 = plain), */
 /* built in the equilateral tetrahedron and mapped back.               */
 /* ------------------------------------------------------------------ */
 
 /* 2D face shift in the equilateral-triangle frame: edges bottom (left->right),
  * right (right->top), left (top->left), each warped by the 1D warp along the
- * edge and blended by 4 * (product of the edge's two barycentrics). */
-static void face_shift(int N, const double *xlgl, double Lleft, double Lright, double Ltop,
+ * edge and blended by 4 * (product of the edge's two barycentrics) times
+ * (1 + (alpha * barycentric of the vertex opposite the edge)^2), the blend
+ * parameter of the warp & blend construction (Section 2's node reference). */
+static void face_shift(int N, const double *xlgl, double alpha, double Lleft, double Lright, double Ltop,
                        double *dx, double *dy) {
-  double wb = 4.0 * Lleft * Lright * warp_factor(N, xlgl, Lright - Lleft);
-  double wr = 4.0 * Lright * Ltop * warp_factor(N, xlgl, Ltop - Lright);
-  double wl = 4.0 * Ltop * Lleft * warp_factor(N, xlgl, Lleft - Ltop);
+  double wb = 4.0 * Lleft * Lright * warp_factor(N, xlgl, Lright - Lleft) * (1.0 + (alpha * Ltop) * (alpha * Ltop));
+  double wr = 4.0 * Lright * Ltop * warp_factor(N, xlgl, Ltop - Lright) * (1.0 + (alpha * Lleft) * (alpha * Lleft));
+  double wl = 4.0 * Ltop * Lleft * warp_factor(N, xlgl, Lleft - Ltop) * (1.0 + (alpha * Lright) * (alpha * Lright));
   *dx = wb + cos(2.0 * M_PI / 3.0) * wr + cos(4.0 * M_PI / 3.0) * wl;
   *dy = sin(2.0 * M_PI / 3.0) * wr + sin(4.0 * M_PI / 3.0) * wl;
 }
 
-int or_nodes(int N, double *r, double *s, double *t) {
+int or_nodes_alpha(int N, double alpha, double *r, double *s, double *t) {
   if (N < 1 || N > 12) return fail("or_nodes: N out of range");
+  if (!(alpha >= 0.0 && alpha <= 10.0)) return fail("or_nodes: blend parameter outside [0, 10]");
   double xlgl[16];
   or_lgl(N, xlgl);
   /* equilateral vertices for reference vertices a=(-1,-1,-1), b=(1,-1,-1), c=(-1,1,-1), d=(-1,-1,1) */
@@ -217,7 +220,7 @@ int or_nodes(int N, double *r, double *s, double *t) {
             t2[c] /= sqrt(n2);
           }
           double dx, dy;
-          face_shift(N, xlgl, L[pl], L[pr], L[pt], &dx, &dy);
+          face_shift(N, xlgl, alpha, L[pl], L[pr], L[pt], &dx, &dy);
           double blend = L[pl] * L[pr] * L[pt];
           double denom = (L[pl] + 0.5 * L[o]) * (L[pr] + 0.5 * L[o]) * (L[pt] + 0.5 * L[o]);
           if (denom > tol) blend = blend / denom;
@@ -255,6 +258,8 @@ int or_nodes(int N, double *r, double *s, double *t) {
       }
   return 0;
 }
+
+int or_nodes(int N, double *r, double *s, double *t) { return or_nodes_alpha(N, 0.0, r, s, t); }
 
 /* ------------------------------------------------------------------ */
 /* Orthonormal bases                                                   */
@@ -347,12 +352,12 @@ static void ops_free(ref_ops *o) {
   free(o->M); free(o->Minv); free(o->LIFT); free(o->Mf); free(o->Fmask);
 }
 
-static int ops_build(int N, ref_ops *o) {
+static int ops_build(int N, double alpha, ref_ops *o) {
   memset(o, 0, sizeof *o);
   int Np = or_np(N), Nfp = or_nfp(N);
   o->N = N; o->Np = Np; o->Nfp = Nfp;
   o->r = malloc(sizeof(double) * Np); o->s = malloc(sizeof(double) * Np); o->t = malloc(sizeof(double) * Np);
-  if (or_nodes(N, o->r, o->s, o->t)) return -1;
+  if (or_nodes_alpha(N, alpha, o->r, o->s, o->t)) return -1;
   size_t nn = (size_t)Np * Np;
   o->V = malloc(sizeof(double) * nn);
   double *Vr = malloc(sizeof(double) * nn), *Vs = malloc(sizeof(double) * nn), *Vt = malloc(sizeof(double) * nn);
@@ -420,11 +425,11 @@ static int ops_build(int N, ref_ops *o) {
   return 0;
 }
 
-int or_operators(int N, double *V, double *Dr, double *Ds, double *Dt, double *M, int32_t *Fmask,
-                 double *Mf, double *LIFT) {
+int or_operators_alpha(int N, double alpha, double *V, double *Dr, double *Ds, double *Dt, double *M,
+                       int32_t *Fmask, double *Mf, double *LIFT) {
   ref_ops o;
   if (N < 1 || N > 10) return fail("or_operators: N out of range");
-  if (ops_build(N, &o)) { ops_free(&o); return -1; }
+  if (ops_build(N, alpha, &o)) { ops_free(&o); return -1; }
   size_t nn = (size_t)o.Np * o.Np;
   if (V) memcpy(V, o.V, sizeof(double) * nn);
   if (Dr) memcpy(Dr, o.Dr, sizeof(double) * nn);
@@ -435,6 +440,44 @@ int or_operators(int N, double *V, double *Dr, double *Ds, double *Dt, double *M
   if (Mf) memcpy(Mf, o.Mf, sizeof(double) * 4 * o.Nfp * o.Nfp);
   if (LIFT) memcpy(LIFT, o.LIFT, sizeof(double) * o.Np * 4 * o.Nfp);
   ops_free(&o);
+  return 0;
+}
+
+int or_operators(int N, double *V, double *Dr, double *Ds, double *Dt, double *M, int32_t *Fmask, double *Mf,
+                 double *LIFT) {
+  return or_operators_alpha(N, 0.0, V, Dr, Ds, Dt, M, Fmask, Mf, LIFT);
+}
+
+/* Lebesgue constant of the warp & blend nodes with blend parameter alpha,
+ * estimated as the largest sum over the nodal basis of |l_i(x)| over the
+ * points x of the order-M equidistant lattice of the tetrahedron. l_i(x) =
+ * sum_m phi_m(x) (V^-1)_{m i}, with V the orthonormal-basis Vandermonde at the
+ * nodes (the definition of the Lagrange basis through the modal one). */
+int or_lebesgue(int N, double alpha, int M, double *lambda) {
+  if (M < 1 || M > 200) return fail("or_lebesgue: lattice order out of range");
+  ref_ops o;
+  if (N < 1 || N > 10) return fail("or_lebesgue: N out of range");
+  if (ops_build(N, alpha, &o)) { ops_free(&o); return -1; }
+  const int Np = o.Np;
+  double *Vinv = malloc(sizeof(double) * Np * Np), *phi = malloc(sizeof(double) * Np);
+  if (mat_inverse(Np, o.V, Vinv)) { free(Vinv); free(phi); ops_free(&o); return fail("singular Vandermonde"); }
+  double best = 0.0;
+  for (int k = 0; k <= M; ++k)
+    for (int j = 0; j <= M - k; ++j)
+      for (int i = 0; i <= M - k - j; ++i) {
+        const double r = -1.0 + 2.0 * i / M, s = -1.0 + 2.0 * j / M, t = -1.0 + 2.0 * k / M;
+        double d0, d1, d2;
+        for (int m = 0; m < Np; ++m) or_basis(N, m, r, s, t, &phi[m], &d0, &d1, &d2);
+        double sum = 0.0;
+        for (int q = 0; q < Np; ++q) {
+          double l = 0.0;
+          for (int m = 0; m < Np; ++m) l += phi[m] * Vinv[m * Np + q];
+          sum += fabs(l);
+        }
+        if (sum > best) best = sum;
+      }
+  *lambda = best;
+  free(Vinv); free(phi); ops_free(&o);
   return 0;
 }
 
@@ -479,11 +522,11 @@ void or_mesh_destroy(or_mesh *m) {
 
 int64_t or_mesh_K(const or_mesh *m) { return m->K; }
 
-or_mesh *or_mesh_create(int N, int64_t Nv, const double *VX, const double *VY, const double *VZ, int64_t K,
-                        const int32_t *EToV, const double *eps, const double *mu) {
+or_mesh *or_mesh_create_alpha(int N, double alpha, int64_t Nv, const double *VX, const double *VY, const double *VZ,
+                              int64_t K, const int32_t *EToV, const double *eps, const double *mu) {
   if (K < 1 || Nv < 4) { fail("or_mesh_create: empty mesh"); return NULL; }
   or_mesh *m = calloc(1, sizeof(or_mesh));
-  if (ops_build(N, &m->o)) { or_mesh_destroy(m); return NULL; }
+  if (ops_build(N, alpha, &m->o)) { or_mesh_destroy(m); return NULL; }
   int Np = m->o.Np, Nfp = m->o.Nfp;
   m->K = K;
   m->x = malloc(sizeof(double) * K * Np); m->y = malloc(sizeof(double) * K * Np); m->z = malloc(sizeof(double) * K * Np);
@@ -593,6 +636,11 @@ or_mesh *or_mesh_create(int N, int64_t Nv, const double *VX, const double *VY, c
       }
     }
   return m;
+}
+
+or_mesh *or_mesh_create(int N, int64_t Nv, const double *VX, const double *VY, const double *VZ, int64_t K,
+                        const int32_t *EToV, const double *eps, const double *mu) {
+  return or_mesh_create_alpha(N, 0.0, Nv, VX, VY, VZ, K, EToV, eps, mu);
 }
 
 int or_mesh_coords(const or_mesh *m, double *x, double *y, double *z) {

@@ -32,12 +32,20 @@ int or_lgl(int N, double *x);
  * (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1); equidistant lattice order
  * (t outer, s middle, r inner). */
 int or_nodes(int N, double *r, double *s, double *t);
+/* The same with blend parameter alpha in [0, 10]: every edge warp of a face is
+ * scaled by (1 + (alpha * barycentric of the face vertex opposite the edge)^2). */
+int or_nodes_alpha(int N, double alpha, double *r, double *s, double *t);
+/* Lebesgue constant of those nodes, estimated on the order-M equidistant lattice. */
+int or_lebesgue(int N, double alpha, int M, double *lambda);
 
 /* Reference operators (Section 2, eq. dg-global-matrices, Fig. lifting-matrix):
  * V (Np x Np), Dr/Ds/Dt (Np x Np), M (Np x Np), Fmask (4 x Nfp, int32),
  * Mf (4 x Nfp x Nfp face mass matrices), LIFT (Np x 4Nfp). Any pointer may be NULL. */
 int or_operators(int N, double *V, double *Dr, double *Ds, double *Dt, double *M,
                  int32_t *Fmask, double *Mf, double *LIFT);
+/* The same on the nodes of blend parameter alpha. */
+int or_operators_alpha(int N, double alpha, double *V, double *Dr, double *Ds, double *Dt, double *M,
+                       int32_t *Fmask, double *Mf, double *LIFT);
 
 /* Orthonormal PKD basis function m (i outer, j, k inner ordering) and its
  * gradient at (r,s,t). */
@@ -49,6 +57,10 @@ int or_basis(int N, int m, double r, double s, double t, double *val, double *dr
 or_mesh *or_mesh_create(int N, int64_t Nv, const double *VX, const double *VY,
                         const double *VZ, int64_t K, const int32_t *EToV,
                         const double *eps, const double *mu);
+/* The same on the nodes of blend parameter alpha. */
+or_mesh *or_mesh_create_alpha(int N, double alpha, int64_t Nv, const double *VX, const double *VY,
+                              const double *VZ, int64_t K, const int32_t *EToV,
+                              const double *eps, const double *mu);
 void or_mesh_destroy(or_mesh *m);
 int64_t or_mesh_K(const or_mesh *m);
 

@@ -51,6 +51,9 @@ def lib():
             L.dg_mesh_upload.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp]
             L.dg_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
             L.dg_operators.argtypes = [vp] + [vp] * 9
+            L.dg_set_node_alpha.argtypes = [vp, dbl]
+            L.dg_optimised_node_alpha.argtypes = [i32]
+            L.dg_optimised_node_alpha.restype = dbl
             L.dg_node_coords.argtypes = [vp, vp]
             L.dg_set_eps.argtypes = [vp, vp]
             L.dg_rhs.argtypes = [vp, vp, vp, flt]
@@ -82,10 +85,21 @@ def _t_ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def optimised_node_alpha(N: int) -> float:
+    """Blend parameter of least Lebesgue constant for order N (the library's table)."""
+    a = lib().dg_optimised_node_alpha(N)
+    if a < 0:
+        raise ValueError(f"no blend parameter for N={N}")
+    return a
+
+
 class Solver:
     """One mesh, one polynomial order, one arithmetic, one CUDA stream."""
 
-    def __init__(self, N: int, precision: str = "fp32", stream=None):
+    def __init__(self, N: int, precision: str = "fp32", stream=None, node_alpha=0.0):
+        """node_alpha: blend parameter of the warp & blend nodes, a number in
+        [0, 10] or "optimised" (the built-in value of least Lebesgue constant
+        for N); 0 is the plain construction."""
         import torch
         self.N = N
         self.precision = precision
@@ -99,6 +113,13 @@ class Solver:
             raise DGError(rc, lib().dg_last_error(None).decode())
         self._h = handle
         self.K = 0
+        if isinstance(node_alpha, str):
+            if node_alpha != "optimised":
+                raise ValueError(f"unknown node_alpha {node_alpha!r}")
+            node_alpha = optimised_node_alpha(N)
+        self.node_alpha = float(node_alpha)
+        if self.node_alpha != 0.0:
+            self._check(lib().dg_set_node_alpha(self._h, self.node_alpha))
         Np, Npad, K = C.c_int(), C.c_int(), C.c_int64()
         lib().dg_layout(self._h, C.byref(Np), C.byref(Npad), C.byref(K))
         self.Np, self.Npad = Np.value, Npad.value

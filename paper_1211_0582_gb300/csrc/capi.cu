@@ -124,6 +124,19 @@ int dg_create(dg_ctx **out, int N, int precision, void *cuda_stream) {
   return DG_OK;
 }
 
+int dg_set_node_alpha(dg_ctx *ctx, double alpha) {
+  if (!ctx) return DG_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->K > 0) return set_err(ctx, DG_ERR_ARG, "dg_set_node_alpha: the context already holds a mesh");
+  RefOps o;
+  std::string err;
+  if (!build_refops(ctx->N, o, err, alpha)) return set_err(ctx, DG_ERR_ARG, "dg_set_node_alpha: " + err);
+  ctx->ops = std::move(o);
+  return DG_OK;
+}
+
+double dg_optimised_node_alpha(int N) { return optimised_alpha(N); }
+
 int dg_destroy(dg_ctx *ctx) {
   if (!ctx) return DG_OK;
   free_mesh(ctx);

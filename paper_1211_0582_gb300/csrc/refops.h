@@ -20,6 +20,7 @@ constexpr int kBoundaryConn = 0xFFFF;
 
 struct RefOps {
   int N = 0, Np = 0, Nfp = 0, Npad = 0;
+  double alpha = 0.0;             // blend parameter of the warp & blend nodes
   std::vector<double> r, s, t;   // nodes on the reference tetrahedron
   std::vector<double> Dr, Ds, Dt; // Np x Np, row-major (output node, input node)
   std::vector<double> M;          // mass matrix, Np x Np
@@ -32,9 +33,15 @@ struct RefOps {
   std::vector<uint8_t> nbr_fnode; // kConnKinds x Nfp
 };
 
-// Builds every reference operator for order N (1..kMaxOrder). Returns false
-// and sets err on failure.
-bool build_refops(int N, RefOps &out, std::string &err);
+// Builds every reference operator for order N (1..kMaxOrder) on the warp &
+// blend nodes of blend parameter alpha (0: the plain construction). Returns
+// false and sets err on failure.
+bool build_refops(int N, RefOps &out, std::string &err, double alpha = 0.0);
+
+// Blend parameter of least Lebesgue constant for order N (0 where it does not
+// lower the constant), from a search over [0, 3] on equidistant lattices of the
+// tetrahedron; -1 for N outside 1..kMaxOrder.
+double optimised_alpha(int N);
 
 // Local vertices of reference face f: t=-1 (0,1,2), s=-1 (0,1,3),
 // r+s+t=-1 (1,2,3), r=-1 (0,2,3).

@@ -53,6 +53,38 @@ def test_host_operators_match_oracle(N):
     np.testing.assert_array_equal(ops["Fmask"], ref["Fmask"])
 
 
+@pytest.mark.parametrize("N", [5, 7, 9])
+def test_host_operators_on_blended_nodes_match_oracle(N):
+    # the library's table of blend parameters equals the oracle's, and the
+    # operators built on those nodes match the oracle's
+    alpha = dg.optimised_node_alpha(N)
+    assert alpha == O.optimal_alpha(N)
+    s = dg.Solver(N, stream=None, node_alpha="optimised")
+    ops = s.operators()
+    for got, ref in zip((ops["r"], ops["s"], ops["t"]), O.nodes(N, alpha)):
+        np.testing.assert_allclose(got, ref, atol=1e-14)
+    ref = O.operators(N, alpha)
+    scale = max(1.0, N * N)
+    for key in ("Dr", "Ds", "Dt"):
+        np.testing.assert_allclose(ops[key], ref[key], atol=1e-12 * scale)
+    np.testing.assert_allclose(ops["M"], ref["M"], atol=1e-13)
+    np.testing.assert_allclose(ops["LIFT"], ref["LIFT"], atol=1e-11 * scale)
+    np.testing.assert_array_equal(ops["Fmask"], ref["Fmask"])
+
+
+def test_node_alpha_table_and_limits():
+    assert [dg.optimised_node_alpha(N) for N in range(1, 10)] == [O.optimal_alpha(N) for N in range(1, 10)]
+    L = dg.lib()
+    assert L.dg_optimised_node_alpha(0) == -1.0 and L.dg_optimised_node_alpha(10) == -1.0
+    s = dg.Solver(4, stream=None)
+    assert L.dg_set_node_alpha(s._h, -0.5) == -1
+    assert L.dg_set_node_alpha(s._h, 11.0) == -1
+    assert L.dg_set_node_alpha(s._h, 0.7) == 0
+    r = np.zeros(s.Np)
+    assert L.dg_operators(s._h, r.ctypes.data, None, None, None, None, None, None, None, None) == 0
+    np.testing.assert_allclose(r, O.nodes(4, 0.7)[0], atol=1e-14)
+
+
 def test_create_rejects_bad_arguments():
     L = dg.lib()
     h = C.c_void_p()

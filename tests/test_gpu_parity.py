@@ -44,6 +44,35 @@ def test_rhs_parity(N, n, alpha):
     assert rel_l2(got, ref) < TOL_FP32
 
 
+@pytest.mark.parametrize("N,n,precision,tol", [(5, 3, "fp32", TOL_FP32), (6, 2, "fp32", TOL_FP32),
+                                               (8, 2, "fp32", TOL_FP32), (9, 2, "fp32", TOL_FP32),
+                                               (5, 3, "fp16x3", 1e-5), (6, 2, "fp16x3", 1e-5),
+                                               (7, 2, "bf16x3", 2e-4)])
+def test_rhs_and_step_parity_on_blended_nodes(N, n, precision, tol):
+    # the operators and node coordinates of the alpha-optimised warp & blend
+    # nodes, against the oracle built on the same blend parameter
+    alpha = O.optimal_alpha(N)
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    eps = W.element_eps(EToV.shape[0], seed=2)
+    s = dg.Solver(N, precision=precision, node_alpha="optimised")
+    assert s.node_alpha == alpha > 0
+    s.upload(VX, VY, VZ, EToV, eps=eps)
+    m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps.astype(np.float64), node_alpha=alpha)
+    for a, b in zip(s.node_coords(), m.coords()):
+        np.testing.assert_allclose(a, b, atol=1e-13)
+    u = random_fields(m.shape)
+    assert rel_l2(s.from_device(s.rhs(s.to_device(u))), m.rhs(u)) < tol
+    dt = 0.5 / n / N ** 2
+    ref, _ = m.lserk(u, dt, 2)
+    ud, rd = s.to_device(u), s.zeros()
+    s.step(ud, rd, dt, 2)
+    assert rel_l2(s.from_device(ud), ref) < tol
+    # the nodes cannot change under a mesh
+    L = dg.lib()
+    assert L.dg_set_node_alpha(s._h, 0.0) == -1
+    assert b"already holds a mesh" in L.dg_last_error(s._h)
+
+
 def test_node_coordinates_match_oracle():
     s, m = setup_pair(4, 3)
     x, y, z = s.node_coords()

@@ -58,6 +58,86 @@ def test_nodes_symmetric_and_edge_lgl(N):
     assert L.min() > -1e-13
 
 
+# ---------------------------------------------------------------- blend parameter of the nodes
+# The warp & blend construction with blend parameter alpha scales each face's
+# edge warp by (1 + (alpha l_R)^2), l_R the barycentric of the face's third
+# vertex. The table oracle/node_alpha.txt holds, per N, the alpha of least
+# Lebesgue constant found by oracle/optimize_node_alpha.py.
+
+def test_blend_parameter_zero_is_the_plain_construction():
+    for N in (3, 6, 9):
+        np.testing.assert_array_equal(np.stack(O.nodes(N, 1e-300)), np.stack(O.nodes(N)))
+
+
+@pytest.mark.parametrize("N", [5, 6, 7, 8, 9])
+def test_blended_nodes_symmetric_edge_lgl_and_moved(N):
+    # the factor depends on the vertex opposite each edge within the face; any
+    # other choice (an end of the edge, the tetrahedron's fourth vertex) breaks
+    # the symmetry under the 24 vertex permutations checked here
+    alpha = O.optimal_alpha(N)
+    assert alpha > 0
+    L = _bary(*O.nodes(N, alpha))
+    L0 = _bary(*O.nodes(N))
+    key = lambda A: np.array(sorted(map(tuple, np.round(A, 12))))
+    base = key(L)
+    for p in itertools.permutations(range(4)):
+        np.testing.assert_allclose(key(L[:, p]), base, atol=1e-12)
+    # edge nodes stay at the 1D LGL points (l_R = 0 on an edge), others move
+    on_edge = (np.sort(L, axis=1)[:, :2] < 1e-12).all(axis=1)
+    np.testing.assert_allclose(L[on_edge], L0[on_edge], atol=1e-14)
+    assert np.abs(L[~on_edge] - L0[~on_edge]).max() > 1e-3
+    assert L.min() > -1e-13
+
+
+@pytest.mark.parametrize("N", [6, 9])
+def test_blended_nodes_give_exact_operators(N):
+    alpha = O.optimal_alpha(N)
+    ops = O.operators(N, alpha)
+    r, s, t = O.nodes(N, alpha)
+    err = 0.0
+    for a, b, c in [(N, 0, 0), (0, N, 0), (0, 0, N), (1, 2, N - 3), (2, 2, N - 4), (N - 1, 1, 0)]:
+        f = r ** a * s ** b * t ** c
+        for D, g in ((ops["Dr"], a * r ** max(a - 1, 0) * s ** b * t ** c),
+                     (ops["Ds"], b * r ** a * s ** max(b - 1, 0) * t ** c),
+                     (ops["Dt"], c * r ** a * s ** b * t ** max(c - 1, 0))):
+            err = max(err, np.abs(D @ f - g).max())
+    assert err < 1e-11 * N ** 2
+    L = _bary(r, s, t)
+    f, g = L[:, 1] ** N, L[:, 2] ** N
+    assert abs(f @ ops["M"] @ g - _dirichlet((0, N, N, 0), 3)) < 1e-12
+
+
+def _lebesgue_monomial(N, alpha, M):
+    """Lebesgue constant on the order-M lattice with the Lagrange basis built
+    from monomials r^a s^b t^c (not the oracle's orthonormal basis)."""
+    r, s, t = O.nodes(N, alpha)
+    pw = [(a, b, c) for a in range(N + 1) for b in range(N + 1 - a) for c in range(N + 1 - a - b)]
+    mono = lambda x, y, z: np.stack([x ** a * y ** b * z ** c for a, b, c in pw], axis=1)
+    lat = np.array([(-1 + 2 * i / M, -1 + 2 * j / M, -1 + 2 * k / M)
+                    for k in range(M + 1) for j in range(M + 1 - k) for i in range(M + 1 - k - j)])
+    ell = mono(*lat.T) @ np.linalg.inv(mono(r, s, t))
+    return np.abs(ell).sum(axis=1).max()
+
+
+def test_lebesgue_constant_closed_form_and_independent_basis():
+    # N = 1: the barycentric basis is non-negative and sums to 1
+    assert abs(O.lebesgue(1, 0.0, 12) - 1.0) < 1e-13
+    for N, alpha in [(3, 0.0), (4, 0.7), (5, O.optimal_alpha(5))]:
+        assert abs(O.lebesgue(N, alpha, 16) - _lebesgue_monomial(N, alpha, 16)) < 1e-9
+
+
+def test_optimised_blend_parameter_lowers_the_lebesgue_constant():
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(O.__file__), "node_alpha.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert [int(r[0]) for r in rows] == list(range(1, 10))
+    for N in range(5, 10):
+        a = O.optimal_alpha(N)
+        # on a lattice the search did not use
+        assert O.lebesgue(N, a, 45) < O.lebesgue(N, 0.0, 45)
+    # N = 3: the one face-interior node is the face centroid for every alpha
+    assert O.lebesgue(3, 1.3, 30) == pytest.approx(O.lebesgue(3, 0.0, 30), abs=1e-13)
+
+
 # ---------------------------------------------------------------- operators
 def _dirichlet(powers, dim):
     """Integral of prod(lambda_i^a_i) over the reference simplex (|T| = 4/3 or 2)."""
