@@ -86,6 +86,24 @@ struct TS {
   static_assert(SMEM <= 232448, "tile does not fit in shared memory");
 };
 
+// Optional phase timestamps (build with -DDGMX_STAGE_TIMING; off in the
+// library): thread 0's SM clock (the MMA thread's for slot 13: all of GEMM1
+// issued; slot 14: all of GEMM2 issued), in cycles since the block passed its
+// setup, per block and tile, read back with dgmx_tcs_trace().
+constexpr int kTsTraceTiles = 32, kTsTraceBlocks = 160, kTsEvents = 16;
+#ifdef DGMX_STAGE_TIMING
+__device__ uint32_t g_tcs_trace[kTsTraceBlocks * kTsTraceTiles * kTsEvents];
+#define TS_MARK(who, ev)                                                                                            \
+  do {                                                                                                              \
+    if ((who) && itn < kTsTraceTiles && blockIdx.x < kTsTraceBlocks)                                                \
+      g_tcs_trace[(blockIdx.x * kTsTraceTiles + itn) * kTsEvents + (ev)] = uint32_t(clock64() - ts_t0);             \
+  } while (0)
+#else
+#define TS_MARK(who, ev) \
+  do {                   \
+  } while (0)
+#endif
+
 // Byte offset of stream step st (0 .. PER-1) in the operator stream.
 template <int N>
 __host__ __device__ constexpr uint32_t slice_offset(int st) {
@@ -140,6 +158,9 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   // stage after stage: the setup above may overlap the end of the previous
   // stage, nothing it wrote is read before this point
   pdl_wait();
+#ifdef DGMX_STAGE_TIMING
+  const long long ts_t0 = clock64();
+#endif
 
   // operator stream (issuer only): step j of the periodic slice sequence
   // goes to slot j % kSlots
@@ -234,6 +255,10 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+#ifdef DGMX_STAGE_TIMING
+    const int itn = (tile - int(blockIdx.x)) / int(gridDim.x);
+#endif
+    TS_MARK(tid == 0, 0);
     if (tile + int(gridDim.x) >= ntiles) pdl_launch_next(); // this block's last tile
     const int64_t k0 = int64_t(tile) * kTileS;
     const int ne = int(a.K - k0 < kTileS ? a.K - k0 : kTileS);
@@ -259,6 +284,9 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       }
       if constexpr (!BF16) mx = absmax4(mx, v[s]);
     }
+#ifdef DGMX_STAGE_TIMING
+    if (tid == 0 && mx >= 0.f) TS_MARK(true, 10); // after thread 0's field loads have landed (FP16)
+#endif
     if (tid < kTileS * 4) {
       float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 1.f, 1.f);
       int2 cn = make_int2(0, kBoundaryConn);
@@ -272,8 +300,11 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       s_face[tid * 3 + 1] = g1;
       s_face[tid * 3 + 2] = make_float4(__int_as_float(cn.x), __int_as_float(cn.y), 0.f, 0.f);
     }
+    TS_MARK(tid == 0, 12);
     if (issuer) umma::bulk_wait_read_all();
+    TS_MARK(issuer, 11);
     __syncthreads();
+    TS_MARK(tid == 0, 1);
     {
       float sc1 = 1.f, inv1r = 1.f;
       if constexpr (!BF16) {
@@ -300,6 +331,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     }
     umma::fence_proxy_async();
     __syncthreads();
+    TS_MARK(tid == 0, 2);
 
     // ---- 3. local differentiation, streamed operator slices
     if (issuer) {
@@ -324,6 +356,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         }) && ok;
       }
       umma::commit(bar1);
+      TS_MARK(true, 13);
     }
 
     // ---- 4. neighbour traces and upwind flux (overlaps GEMM1), in registers
@@ -423,9 +456,11 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         }
       }
     }
+    TS_MARK(tid == 0, 3);
     // A2 overwrites A1: GEMM1 must have completed
     ok = umma::mbar_wait_bounded(bar1, phase, wlim) && ok;
     __syncthreads();
+    TS_MARK(tid == 0, 4);
 
     // ---- 5. split the face fluxes into the A2 operand
     if (warp < kFluxWarps) {
@@ -460,6 +495,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     }
     umma::fence_proxy_async();
     __syncthreads();
+    TS_MARK(tid == 0, 5);
 
     // ---- 6. flux lifting (streamed slices); meanwhile the residual rows are read
     if (issuer) {
@@ -484,6 +520,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         }) && ok;
       }
       umma::commit(bar2);
+      TS_MARK(true, 14);
     }
     const bool live = lane_used && e_loc < ne;
     const int64_t k = k0 + e_loc;
@@ -513,7 +550,9 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     };
     float4 rn0, rn1;
     load_res(ch0, rn0, rn1);
+    TS_MARK(tid == 0, 6);
     ok = umma::mbar_wait_bounded(bar2, phase, wlim) && ok;
+    TS_MARK(tid == 0, 7);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicExch(err_flag, 1);
       // the matrix operations issued for this tile complete before tensor
@@ -521,6 +560,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       if (issuer) umma::mbar_wait_bounded(bar2, phase);
       break;
     }
+    TS_MARK(tid == 0, 8);
     umma::fence_after_sync();
 
     // ---- 7. epilogue: chain rule (eq. dg-reference-matrices), curls, lifted
@@ -581,6 +621,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
+    TS_MARK(tid == 0, 9);
     if (issuer) {
       const uint32_t rowbytes = uint32_t(ne * NPP * 4);
       for (int f = 0; f < 6; ++f) {
@@ -683,4 +724,10 @@ cudaError_t launch_tc_streamed(int N, int mode, bool bf16, const StageArgs &a, c
 }
 
 } // namespace tcc
+
+#ifdef DGMX_STAGE_TIMING
+extern "C" int dgmx_tcs_trace(uint32_t *host) {
+  return int(cudaMemcpyFromSymbol(host, g_tcs_trace, sizeof(g_tcs_trace)));
+}
+#endif
 } // namespace dgmx

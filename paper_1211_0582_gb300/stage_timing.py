@@ -14,9 +14,19 @@ of the last single-stage launch (dgmx_tc_trace) and prints, per phase, thread
   8 -> 9   epilogue (lifted flux, update) into the output buffer
   9 -> 0'  bulk stores issued, next tile
 
+At N = 6, 7 (the kernel that streams its operators from L2, dgmx_tcs_trace):
+
+  0 -> 1   fields from L2 into registers, face table
+  1 -> 2   field split into the GEMM1 operand in shared memory
+  2 -> 3   neighbour gathers and upwind fluxes (warp 0); 2 -> 13: GEMM1 issued
+  3 -> 4   GEMM1 wait and barrier
+  4 -> 5   flux split; 5 -> 14: GEMM2 issued
+  5 -> 6   geometry and first residual chunk; 6 -> 7 GEMM2 wait
+  8 -> 9   epilogue
+
 Usage (on a GPU): python -m paper_1211_0582_gb300.stage_timing [precision N n] ...
-e.g. `fp16x3 5 24 bf16x3 5 24`. Only orders that run the single-tile kernel
-(N <= 5, the default form) are timed.
+e.g. `fp16x3 5 24 bf16x3 5 24 fp16x3 7 16`. N <= 5 times the default
+(single-tile) form.
 """
 from __future__ import annotations
 
@@ -32,6 +42,11 @@ TILES, EVENTS, BLOCKS = 32, 16, 160
 PHASES = [(0, 1, "fields in registers"), (1, 2, "field split, GEMM1 issued"), (2, 3, "fluxes (warp 0)"),
           (3, 4, "flux barrier"), (4, 5, "flux split"), (5, 6, "GEMM1 wait"), (6, 7, "volume terms"),
           (7, 12, "GEMM2 + residual wait"), (12, 8, "barrier"), (8, 9, "epilogue")]
+PHASES_STREAMED = [(0, 10, "thread 0's field loads landed (FP16)"), (0, 12, "thread 0's face table written"),
+                   (0, 11, "previous tile's stores read (MMA thread)"), (0, 1, "fields and face table"), (1, 2, "field split"), (2, 3, "fluxes (warp 0)"),
+                   (2, 13, "GEMM1 issued (MMA thread)"), (3, 4, "GEMM1 wait, barrier"), (4, 5, "flux split"),
+                   (5, 14, "GEMM2 issued (MMA thread)"), (5, 6, "geometry, first residual"),
+                   (6, 7, "GEMM2 wait"), (7, 8, "barrier"), (8, 9, "epilogue")]
 
 
 def timing_library() -> str:
@@ -53,7 +68,9 @@ def breakdown(prec: str, N: int, n: int, order: str = "hilbert") -> dict:
     s.step(u, r, 0.5 / n / N ** 2, 3)
     s.sync()
     buf = np.zeros(BLOCKS * TILES * EVENTS, dtype=np.uint32)
-    rc = dg.lib().dgmx_tc_trace(buf.ctypes.data_as(C.c_void_p))
+    streamed = N >= 6
+    reader = dg.lib().dgmx_tcs_trace if streamed else dg.lib().dgmx_tc_trace
+    rc = reader(buf.ctypes.data_as(C.c_void_p))
     torch.cuda.synchronize()
     if rc != 0:
         raise RuntimeError(f"dgmx_tc_trace failed ({rc})")
@@ -64,11 +81,12 @@ def breakdown(prec: str, N: int, n: int, order: str = "hilbert") -> dict:
         raise ValueError("the mesh gives fewer than 4 tiles per block")
     cur, nxt = T[:, 1:nt - 1], T[:, 2:nt]
     out = {"period": float((nxt[:, :, 0] - cur[:, :, 0]).mean())}
-    for a, b, name in PHASES:
+    for a, b, name in (PHASES_STREAMED if streamed else PHASES):
         out[name] = float((cur[:, :, b] - cur[:, :, a]).mean())
     out["stores, next tile"] = float((nxt[:, :, 0] - cur[:, :, 9]).mean())
-    out["first warp done with fluxes (after 2)"] = float((cur[:, :, 11] - cur[:, :, 2]).mean())
-    out["last warp done with fluxes (after 2)"] = float((cur[:, :, 10] - cur[:, :, 2]).mean())
+    if not streamed:
+        out["first warp done with fluxes (after 2)"] = float((cur[:, :, 11] - cur[:, :, 2]).mean())
+        out["last warp done with fluxes (after 2)"] = float((cur[:, :, 10] - cur[:, :, 2]).mean())
     return out
 
 
@@ -82,7 +100,8 @@ def main(argv) -> None:
         b = breakdown(prec, N, n)
         print(f"{prec} N={N} {n}^3x6 tets (Hilbert order): cycles per tile, thread 0")
         for k, v in b.items():
-            pct = "" if k == "period" or k.startswith(("first", "last")) else f"  {100 * v / b['period']:5.1f}%"
+            pct = "" if k == "period" or k.startswith(("first", "last", "thread 0", "previous")) or "issued" in k \
+                else f"  {100 * v / b['period']:5.1f}%"
             print(f"  {k:<40} {v:8.0f}{pct}")
 
 
