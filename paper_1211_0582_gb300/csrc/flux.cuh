@@ -45,4 +45,54 @@ __device__ __forceinline__ void maxwell_flux_w(float4 nf, const float *qm, const
   out[5] = w.y * (nx * vy - ny * vx);
 }
 
+// Packed FP32 pairs (two face nodes at once): per-element IEEE fp32 add, sub,
+// mul and fma with round-to-nearest, in one instruction each (PTX .f32x2).
+#define DGMX_F2OP(name, op)                                                                                          \
+  __device__ __forceinline__ float2 name(float2 a, float2 b) {                                                       \
+    float2 d;                                                                                                        \
+    asm("{\n .reg .b64 A, B, D;\n mov.b64 A, {%2, %3};\n mov.b64 B, {%4, %5};\n " op                            \
+        " D, A, B;\n mov.b64 {%0, %1}, D;\n}"                                                                        \
+        : "=f"(d.x), "=f"(d.y)                                                                                       \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                                   \
+    return d;                                                                                                        \
+  }
+DGMX_F2OP(f2add, "add.rn.f32x2")
+DGMX_F2OP(f2sub, "sub.rn.f32x2")
+DGMX_F2OP(f2mul, "mul.rn.f32x2")
+#undef DGMX_F2OP
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 A, B, C, D;\n mov.b64 A, {%2, %3};\n mov.b64 B, {%4, %5};\n mov.b64 C, {%6, %7};\n"
+      " fma.rn.f32x2 D, A, B, C;\n mov.b64 {%0, %1}, D;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// maxwell_flux_w at two face nodes of one face (same normal and weights),
+// each value a pair (node 0, node 1).
+__device__ __forceinline__ void maxwell_flux_w2(float4 nf, const float2 *qm, const float2 *qp, float4 w,
+                                                float alpha, float2 *out) {
+  const float2 nx = f2(nf.x), ny = f2(nf.y), nz = f2(nf.z);
+  const float2 mnx = f2(-nf.x), mny = f2(-nf.y), mnz = f2(-nf.z);
+  const float2 dEx = f2sub(qp[0], qm[0]), dEy = f2sub(qp[1], qm[1]), dEz = f2sub(qp[2], qm[2]);
+  const float2 dHx = f2sub(qp[3], qm[3]), dHy = f2sub(qp[4], qm[4]), dHz = f2sub(qp[5], qm[5]);
+  const float2 cEx = f2fma(ny, dEz, f2mul(mnz, dEy)), cEy = f2fma(nz, dEx, f2mul(mnx, dEz)),
+               cEz = f2fma(nx, dEy, f2mul(mny, dEx));
+  const float2 cHx = f2fma(ny, dHz, f2mul(mnz, dHy)), cHy = f2fma(nz, dHx, f2mul(mnx, dHz)),
+               cHz = f2fma(nx, dHy, f2mul(mny, dHx));
+  const float2 ma = f2(-alpha), pa = f2(alpha), wz = f2(w.z), ww = f2(w.w), wx = f2(w.x), wy = f2(w.y);
+  float2 vx = f2fma(wz, dHx, f2mul(ma, cEx)), vy = f2fma(wz, dHy, f2mul(ma, cEy)), vz = f2fma(wz, dHz, f2mul(ma, cEz));
+  out[0] = f2mul(wx, f2fma(ny, vz, f2mul(mnz, vy)));
+  out[1] = f2mul(wx, f2fma(nz, vx, f2mul(mnx, vz)));
+  out[2] = f2mul(wx, f2fma(nx, vy, f2mul(mny, vx)));
+  vx = f2fma(ww, dEx, f2mul(pa, cHx));
+  vy = f2fma(ww, dEy, f2mul(pa, cHy));
+  vz = f2fma(ww, dEz, f2mul(pa, cHz));
+  out[3] = f2mul(wy, f2fma(ny, vz, f2mul(mnz, vy)));
+  out[4] = f2mul(wy, f2fma(nz, vx, f2mul(mnx, vz)));
+  out[5] = f2mul(wy, f2fma(nx, vy, f2mul(mny, vx)));
+}
+
 } // namespace dgmx

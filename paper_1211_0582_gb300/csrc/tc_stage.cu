@@ -503,23 +503,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (blk < NBLK && f < 4 && e < ne) {
           const float4 g0 = s_fgeo[e * 4 + f], w1 = s_fmat[e * 4 + f];
           const bool wall = s_fconn[e * 4 + f].y == kBoundaryConn;
+          {
+            // both nodes of the pair at once (the second may be past the face's last node)
+            const bool two = mm + 1 < NFP;
+            const int vm0 = s_fm[f * NFP + mm], vm1 = s_fm[f * NFP + mm + (two ? 1 : 0)];
+            float2 qm[6], q[6], o[6];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (mm + h < NFP) {
-              const int vm = s_fm[f * NFP + mm + h];
-              float qm[6], q[6];
+            for (int c = 0; c < 6; ++c) qm[c] = make_float2(s_u[c * FS + e * NPP + vm0], s_u[c * FS + e * NPP + vm1]);
 #pragma unroll
-              for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
+            for (int c = 0; c < 6; ++c)
+              q[c] = make_float2(lidx[s][0] >= 0 ? s_u[c * FS + lidx[s][0]] : qp[s][0][c],
+                                 lidx[s][1] >= 0 ? s_u[c * FS + lidx[s][1]] : qp[s][1][c]);
+            if (wall) {
 #pragma unroll
-              for (int c = 0; c < 6; ++c) q[c] = lidx[s][h] >= 0 ? s_u[c * FS + lidx[s][h]] : qp[s][h][c];
-              if (wall) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                  q[c] = -qm[c];
-                  q[c + 3] = qm[c + 3];
-                }
+              for (int c = 0; c < 3; ++c) {
+                q[c] = make_float2(-qm[c].x, -qm[c].y);
+                q[c + 3] = qm[c + 3];
               }
-              maxwell_flux_w(g0, qm, q, w1, a.alpha, fl[s][h]);
+            }
+            maxwell_flux_w2(g0, qm, q, w1, a.alpha, o);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              fl[s][0][c] = o[c].x;
+              fl[s][1][c] = two ? o[c].y : 0.f;
             }
           }
         }

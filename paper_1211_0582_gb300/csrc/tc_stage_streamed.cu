@@ -413,22 +413,29 @@ __global__ void __launch_bounds__(kThreadsS, 1)
             const int f = fm / NFP;
             const float4 g0 = s_face[(e * 4 + f) * 3 + 0], w1 = s_face[(e * 4 + f) * 3 + 1];
             const bool wall = __float_as_int(s_face[(e * 4 + f) * 3 + 2].y) == kBoundaryConn;
+            {
+              // both nodes of the pair at once (Nfp is even: both are face nodes)
+              const int vm0 = s_fm[fm], vm1 = s_fm[fm + 1];
+              float2 qm[6], q[6], o[6];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int vm = s_fm[fm + h];
-              float qm[6], q[6];
+              for (int c = 0; c < 6; ++c) qm[c] = make_float2(s_u[c * FS + e * NPP + vm0], s_u[c * FS + e * NPP + vm1]);
 #pragma unroll
-              for (int c = 0; c < 6; ++c) qm[c] = s_u[c * FS + e * NPP + vm];
-#pragma unroll
-              for (int c = 0; c < 6; ++c) q[c] = lidx[b][h] >= 0 ? s_u[c * FS + lidx[b][h]] : qp[b][h][c];
+              for (int c = 0; c < 6; ++c)
+                q[c] = make_float2(lidx[b][0] >= 0 ? s_u[c * FS + lidx[b][0]] : qp[b][0][c],
+                                   lidx[b][1] >= 0 ? s_u[c * FS + lidx[b][1]] : qp[b][1][c]);
               if (wall) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                  q[c] = -qm[c];
+                  q[c] = make_float2(-qm[c].x, -qm[c].y);
                   q[c + 3] = qm[c + 3];
                 }
               }
-              maxwell_flux_w(g0, qm, q, w1, a.alpha, fl[s][h]);
+              maxwell_flux_w2(g0, qm, q, w1, a.alpha, o);
+#pragma unroll
+              for (int c = 0; c < 6; ++c) {
+                fl[s][0][c] = o[c].x;
+                fl[s][1][c] = o[c].y;
+              }
             }
           }
           if constexpr (!BF16) {
