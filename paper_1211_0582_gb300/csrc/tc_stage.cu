@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int fld = lane_used ? lane % 6 : 5;
   const int comp = fld % 3;
   const bool isE = fld < 3;
+  const float sgn = isE ? 1.f : -1.f;
   const int src1 = ep * 6 + (isE ? 3 : 0) + (comp + 2) % 3;
   const int src2 = ep * 6 + (isE ? 3 : 0) + (comp + 1) % 3;
   const int dl1 = (comp + 2) % 3, dl2 = (comp + 1) % 3;
@@ -668,13 +669,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma::reg_fence8(ur);
         umma::reg_fence8(us);
         umma::reg_fence8(ut);
+        // two nodes at a time in packed FP32 pairs; the sign of the curl
+        // (E rows take v1 - v2, H rows v2 - v1) is applied in the epilogue
 #pragma unroll
-        for (int n = 0; n < 8; ++n) {
-          const float p1 = g1r * ur[n] + g1s * us[n] + g1t * ut[n];
-          const float p2 = g2r * ur[n] + g2s * us[n] + g2t * ut[n];
-          const float v1 = __shfl_sync(0xffffffffu, p1, src1);
-          const float v2 = __shfl_sync(0xffffffffu, p2, src2);
-          vol[c][n] = isE ? (v1 - v2) : (v2 - v1);
+        for (int n = 0; n < 8; n += 2) {
+          const float2 r2 = make_float2(ur[n], ur[n + 1]), s2 = make_float2(us[n], us[n + 1]),
+                       t2 = make_float2(ut[n], ut[n + 1]);
+          const float2 p1 = f2fma(f2(g1t), t2, f2fma(f2(g1s), s2, f2mul(f2(g1r), r2)));
+          const float2 p2 = f2fma(f2(g2t), t2, f2fma(f2(g2s), s2, f2mul(f2(g2r), r2)));
+          const float2 v1 = make_float2(__shfl_sync(0xffffffffu, p1.x, src1), __shfl_sync(0xffffffffu, p1.y, src1));
+          const float2 v2 = make_float2(__shfl_sync(0xffffffffu, p2.x, src2), __shfl_sync(0xffffffffu, p2.y, src2));
+          const float2 d = f2sub(v1, v2);
+          vol[c][n] = d.x;
+          vol[c][n + 1] = d.y;
         }
       }
       TC_MARK(7);
@@ -716,26 +723,34 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int h = 0; h < 2; ++h) {
             const int i = i0 + 4 * h;
             if (i < NPP) {
-              float r4[4];
+              // packed FP32 pairs: r = (sign (v1 - v2) + lift inv2) w, then the update
+              float2 r2[2];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? (vol[c][4 * h + q] + lf[4 * h + q] * inv2) * w : 0.f;
+              for (int q = 0; q < 2; ++q) {
+                const int j = 4 * h + 2 * q;
+                const float2 d = f2mul(f2(sgn), make_float2(vol[c][j], vol[c][j + 1]));
+                r2[q] = f2mul(f2fma(make_float2(lf[j], lf[j + 1]), f2(inv2), d), f2(w));
+                if (i + 2 * q >= NP) r2[q].x = 0.f;
+                if (i + 2 * q + 1 >= NP) r2[q].y = 0.f;
+              }
               float4 *op = reinterpret_cast<float4 *>(s_out + soff + i);
               if (MODE == MODE_RHS) {
-                *op = make_float4(r4[0], r4[1], r4[2], r4[3]);
+                *op = make_float4(r2[0].x, r2[0].y, r2[1].x, r2[1].y);
               } else {
                 const float4 rs = read_res ? *reinterpret_cast<const float4 *>(s_res + soff + i)
                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float rsv[4] = {rs.x, rs.y, rs.z, rs.w};
-                const float uov[4] = {uold[4 * h], uold[4 * h + 1], uold[4 * h + 2], uold[4 * h + 3]};
-                float nr[4], nu[4];
+                const float2 rsv[2] = {make_float2(rs.x, rs.y), make_float2(rs.z, rs.w)};
+                float2 nr[2], nu[2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const bool pad = i + q >= NP;
-                  nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[q], dtk * r4[q]);
-                  nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
+                for (int q = 0; q < 2; ++q) {
+                  const int j = 4 * h + 2 * q;
+                  nr[q] = f2fma(f2(a.rk_a), rsv[q], f2mul(f2(dtk), r2[q]));
+                  nu[q] = f2fma(f2(a.rk_b), nr[q], make_float2(uold[j], uold[j + 1]));
+                  if (i + 2 * q >= NP) nr[q].x = nu[q].x = 0.f;
+                  if (i + 2 * q + 1 >= NP) nr[q].y = nu[q].y = 0.f;
                 }
-                op[0] = make_float4(nr[0], nr[1], nr[2], nr[3]);
-                op[6 * FS / 4] = make_float4(nu[0], nu[1], nu[2], nu[3]);
+                op[0] = make_float4(nr[0].x, nr[0].y, nr[1].x, nr[1].y);
+                op[6 * FS / 4] = make_float4(nu[0].x, nu[0].y, nu[1].x, nu[1].y);
               }
             }
           }

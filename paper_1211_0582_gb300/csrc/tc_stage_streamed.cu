@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
   const int fld = lane < 30 ? lane % 6 : 5;
   const int comp = fld % 3;
   const bool isE = fld < 3;
+  const float sgn = isE ? 1.f : -1.f;
   const int src1 = ep * 6 + (isE ? 3 : 0) + (comp + 2) % 3;
   const int src2 = ep * 6 + (isE ? 3 : 0) + (comp + 1) % 3;
   const int dl1 = (comp + 2) % 3, dl2 = (comp + 1) % 3;
@@ -589,37 +590,51 @@ __global__ void __launch_bounds__(kThreadsS, 1)
       umma::reg_fence8(us);
       umma::reg_fence8(ut);
       umma::reg_fence8(lf);
+      // two nodes at a time in packed FP32 pairs; vol = sign (v1 - v2), with
+      // sign +1 on E rows and -1 on H rows
 #pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        const float p1 = g1r * ur[n] + g1s * us[n] + g1t * ut[n];
-        const float p2 = g2r * ur[n] + g2s * us[n] + g2t * ut[n];
-        const float v1 = __shfl_sync(0xffffffffu, p1, src1);
-        const float v2 = __shfl_sync(0xffffffffu, p2, src2);
-        vol[n] = isE ? (v1 - v2) : (v2 - v1);
+      for (int n = 0; n < 8; n += 2) {
+        const float2 r2 = make_float2(ur[n], ur[n + 1]), s2 = make_float2(us[n], us[n + 1]),
+                     t2 = make_float2(ut[n], ut[n + 1]);
+        const float2 p1 = f2fma(f2(g1t), t2, f2fma(f2(g1s), s2, f2mul(f2(g1r), r2)));
+        const float2 p2 = f2fma(f2(g2t), t2, f2fma(f2(g2s), s2, f2mul(f2(g2r), r2)));
+        const float2 v1 = make_float2(__shfl_sync(0xffffffffu, p1.x, src1), __shfl_sync(0xffffffffu, p1.y, src1));
+        const float2 v2 = make_float2(__shfl_sync(0xffffffffu, p2.x, src2), __shfl_sync(0xffffffffu, p2.y, src2));
+        const float2 d = f2mul(f2(sgn), f2sub(v1, v2));
+        vol[n] = d.x;
+        vol[n + 1] = d.y;
       }
       if (live) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int i = i0 + 4 * h;
           if (i < NPP) {
-            float r4[4];
+            // packed FP32 pairs: r = (vol + lift inv2) w, then the update
+            float2 r2[2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) r4[q] = (i + q < NP) ? (vol[4 * h + q] + lf[4 * h + q] * inv2) * w : 0.f;
+            for (int q = 0; q < 2; ++q) {
+              const int j = 4 * h + 2 * q;
+              r2[q] = f2mul(f2fma(make_float2(lf[j], lf[j + 1]), f2(inv2), make_float2(vol[j], vol[j + 1])), f2(w));
+              if (i + 2 * q >= NP) r2[q].x = 0.f;
+              if (i + 2 * q + 1 >= NP) r2[q].y = 0.f;
+            }
             if (MODE == MODE_RHS) {
-              *reinterpret_cast<float4 *>(s_out + soff + i) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+              *reinterpret_cast<float4 *>(s_out + soff + i) = make_float4(r2[0].x, r2[0].y, r2[1].x, r2[1].y);
             } else {
               float4 *up = reinterpret_cast<float4 *>(s_u + soff + i);
               const float4 uo = *up;
-              const float uov[4] = {uo.x, uo.y, uo.z, uo.w};
-              float nr[4], nu[4];
+              const float2 uov[2] = {make_float2(uo.x, uo.y), make_float2(uo.z, uo.w)};
+              float2 nr[2], nu[2];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const bool pad = i + q >= NP;
-                nr[q] = pad ? 0.f : fmaf(a.rk_a, rsv[4 * h + q], a.dt * r4[q]);
-                nu[q] = pad ? 0.f : fmaf(a.rk_b, nr[q], uov[q]);
+              for (int q = 0; q < 2; ++q) {
+                const int j = 4 * h + 2 * q;
+                nr[q] = f2fma(f2(a.rk_a), make_float2(rsv[j], rsv[j + 1]), f2mul(f2(a.dt), r2[q]));
+                nu[q] = f2fma(f2(a.rk_b), nr[q], uov[q]);
+                if (i + 2 * q >= NP) nr[q].x = nu[q].x = 0.f;
+                if (i + 2 * q + 1 >= NP) nr[q].y = nu[q].y = 0.f;
               }
-              *reinterpret_cast<float4 *>(s_out + soff + i) = make_float4(nr[0], nr[1], nr[2], nr[3]);
-              *up = make_float4(nu[0], nu[1], nu[2], nu[3]);
+              *reinterpret_cast<float4 *>(s_out + soff + i) = make_float4(nr[0].x, nr[0].y, nr[1].x, nr[1].y);
+              *up = make_float4(nu[0].x, nu[0].y, nu[1].x, nu[1].y);
             }
           }
         }
