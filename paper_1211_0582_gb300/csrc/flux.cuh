@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "f32x2.cuh"
+
 namespace dgmx {
 
 template <int N>
@@ -44,31 +46,6 @@ __device__ __forceinline__ void maxwell_flux_w(float4 nf, const float *qm, const
   out[4] = w.y * (nz * vx - nx * vz);
   out[5] = w.y * (nx * vy - ny * vx);
 }
-
-// Packed FP32 pairs (two face nodes at once): per-element IEEE fp32 add, sub,
-// mul and fma with round-to-nearest, in one instruction each (PTX .f32x2).
-#define DGMX_F2OP(name, op)                                                                                          \
-  __device__ __forceinline__ float2 name(float2 a, float2 b) {                                                       \
-    float2 d;                                                                                                        \
-    asm("{\n .reg .b64 A, B, D;\n mov.b64 A, {%2, %3};\n mov.b64 B, {%4, %5};\n " op                            \
-        " D, A, B;\n mov.b64 {%0, %1}, D;\n}"                                                                        \
-        : "=f"(d.x), "=f"(d.y)                                                                                       \
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                                   \
-    return d;                                                                                                        \
-  }
-DGMX_F2OP(f2add, "add.rn.f32x2")
-DGMX_F2OP(f2sub, "sub.rn.f32x2")
-DGMX_F2OP(f2mul, "mul.rn.f32x2")
-#undef DGMX_F2OP
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n .reg .b64 A, B, C, D;\n mov.b64 A, {%2, %3};\n mov.b64 B, {%4, %5};\n mov.b64 C, {%6, %7};\n"
-      " fma.rn.f32x2 D, A, B, C;\n mov.b64 {%0, %1}, D;\n}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
 // maxwell_flux_w at two face nodes of one face (same normal and weights),
 // each value a pair (node 0, node 1).

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 
 namespace dgmx {
 namespace tcc {
@@ -34,13 +35,13 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_
   if constexpr (BF16) {
     const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
     hi = *reinterpret_cast<const uint32_t *>(&hh);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
-    const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - h0, x1 - h1);
+    const float2 r = f2sub(make_float2(x0, x1), make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xFFFF0000u)));
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(r.x, r.y);
     lo = *reinterpret_cast<const uint32_t *>(&ll);
   } else {
     const __half2 hh = __floats2half2_rn(x0, x1);
-    const float2 hf = __half22float2(hh);
-    const __half2 ll = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    const float2 r = f2sub(make_float2(x0, x1), __half22float2(hh));
+    const __half2 ll = __floats2half2_rn(r.x, r.y);
     hi = *reinterpret_cast<const uint32_t *>(&hh);
     lo = *reinterpret_cast<const uint32_t *>(&ll);
   }

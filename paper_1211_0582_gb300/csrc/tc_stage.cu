@@ -429,7 +429,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           raw[4 * j] = __float_as_uint(v[j].x), raw[4 * j + 1] = __float_as_uint(v[j].y);
           raw[4 * j + 2] = __float_as_uint(v[j].z), raw[4 * j + 3] = __float_as_uint(v[j].w);
           float4 w = v[j];
-          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+          if constexpr (!BF16) {
+            const float2 a01 = f2mul(make_float2(w.x, w.y), f2(sc1)), a23 = f2mul(make_float2(w.z, w.w), f2(sc1));
+            w = make_float4(a01.x, a01.y, a23.x, a23.y);
+          }
           split2<BF16>(w.x, w.y, hi[2 * j], lo[2 * j]);
           split2<BF16>(w.z, w.w, hi[2 * j + 1], lo[2 * j + 1]);
         }
@@ -614,7 +617,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
               uint32_t hi, lo;
-              split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
+              const float2 x = f2mul(make_float2(fl[s][0][c], fl[s][1][c]), f2(sc2[c]));
+              split2<BF16>(x.x, x.y, hi, lo);
               const uint32_t o = T::a2_offset(r0 + uint32_t(c), uint32_t(fm));
               *reinterpret_cast<uint32_t *>(smem + T::OFF_A2H + o) = hi;
               *reinterpret_cast<uint32_t *>(smem + T::OFF_A2L + o) = lo;
@@ -1001,7 +1005,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           float4 w = load4(kb1 + 8 * c + 4 * j);
-          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+          if constexpr (!BF16) {
+            const float2 a01 = f2mul(make_float2(w.x, w.y), f2(sc1)), a23 = f2mul(make_float2(w.z, w.w), f2(sc1));
+            w = make_float4(a01.x, a01.y, a23.x, a23.y);
+          }
           split2<BF16>(w.x, w.y, hi[2 * j], lo[2 * j]);
           split2<BF16>(w.z, w.w, hi[2 * j + 1], lo[2 * j + 1]);
         }

@@ -320,7 +320,10 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         if (cr1 >= 0 && k < T::K1) {
           if (k < NPP) *reinterpret_cast<float4 *>(s_u + f1 * FS + e1 * NPP + k) = v[s];
           float4 w = v[s];
-          if constexpr (!BF16) w.x *= sc1, w.y *= sc1, w.z *= sc1, w.w *= sc1;
+          if constexpr (!BF16) {
+            const float2 a01 = f2mul(make_float2(w.x, w.y), f2(sc1)), a23 = f2mul(make_float2(w.z, w.w), f2(sc1));
+            w = make_float4(a01.x, a01.y, a23.x, a23.y);
+          }
           uint2 hi, lo;
           split2<BF16>(w.x, w.y, hi.x, lo.x);
           split2<BF16>(w.z, w.w, hi.y, lo.y);
@@ -493,7 +496,8 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
             uint32_t hi, lo;
-            split2<BF16>(fl[s][0][c] * sc2[c], fl[s][1][c] * sc2[c], hi, lo);
+            const float2 x = f2mul(make_float2(fl[s][0][c], fl[s][1][c]), f2(sc2[c]));
+            split2<BF16>(x.x, x.y, hi, lo);
             const uint32_t o = T::a2_offset(r0 + uint32_t(c), uint32_t(fm));
             *reinterpret_cast<uint32_t *>(smem + o) = hi;
             *reinterpret_cast<uint32_t *>(smem + T::A2B + o) = lo;
