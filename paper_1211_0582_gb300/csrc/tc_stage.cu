@@ -448,15 +448,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!BF16 && tid < 128) s_rowmx[tid] = 0u;
       TC_MARK(2);
 
-      // ---- 3. local differentiation on the tensor cores (asynchronous)
-      if (issuer) {
-        umma::fence_after_sync();
-        issue_split_gemm_ta<BF16, T::K1, T::N1>(tmem, a1_hi, a1_lo, sbase + T::OFF_B1H, sbase + T::OFF_B1L);
-        umma::commit(bar1);
-      }
       bool ok = true;
 
-      // ---- 4. upwind flux (overlaps GEMM1), in registers: the neighbour traces
+      // ---- 3. upwind flux, in registers: the neighbour traces
       // outside the tile are requested from L2 first (all of a lane's loads in
       // flight together); neighbours inside the tile are read from the staged
       // fields
@@ -594,6 +588,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         *s_staged = more ? 1 : 0;
       }
 
+      // ---- 4. local differentiation on the tensor cores (asynchronous,
+      // overlapping the flux split): issued after the flux phase, whose
+      // shared-memory loads would otherwise queue behind its operand reads
+      if (issuer) {
+        umma::fence_after_sync();
+        issue_split_gemm_ta<BF16, T::K1, T::N1>(tmem, a1_hi, a1_lo, sbase + T::OFF_B1H, sbase + T::OFF_B1L);
+        umma::commit(bar1);
+      }
       // ---- 5. split the face fluxes into the A2 operand
       {
 #pragma unroll

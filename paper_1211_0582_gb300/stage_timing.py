@@ -7,9 +7,9 @@ of the last single-stage launch (dgmx_tc_trace) and prints, per phase, thread
 0's cycles averaged over all blocks and over the tiles 1 .. 30 of each block:
 
   0 -> 1   wait for the tile's staged fields, load them, FP16 row maxima
-  1 -> 2   field split into the GEMM1 operand in tensor memory (GEMM1 issued at 2)
+  1 -> 2   field split into the GEMM1 operand in tensor memory
   2 -> 3   neighbour gathers and upwind fluxes (warp 0), then the flux barrier
-  4 -> 5   flux split into the GEMM2 operand (GEMM2 issued at 5)
+  4 -> 5   flux split into the GEMM2 operand (GEMM1 issued at 4, GEMM2 at 5)
   5 -> 6   GEMM1 wait; 6 -> 7 volume terms; 7 -> 12 GEMM2 and residual waits
   8 -> 9   epilogue (lifted flux, update) into the output buffer
   9 -> 0'  bulk stores issued, next tile
@@ -39,8 +39,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 TILES, EVENTS, BLOCKS = 32, 16, 160
-PHASES = [(0, 1, "fields in registers"), (1, 2, "field split, GEMM1 issued"), (2, 3, "fluxes (warp 0)"),
-          (3, 4, "flux barrier"), (4, 5, "flux split"), (5, 6, "GEMM1 wait"), (6, 7, "volume terms"),
+PHASES = [(0, 1, "fields in registers"), (1, 2, "field split"), (2, 3, "fluxes (warp 0)"),
+          (3, 4, "flux barrier"), (4, 5, "flux split, GEMM1 issued"), (5, 6, "GEMM1 wait"), (6, 7, "volume terms"),
           (7, 12, "GEMM2 + residual wait"), (12, 8, "barrier"), (8, 9, "epilogue")]
 PHASES_STREAMED = [(0, 10, "thread 0's field loads landed (FP16)"), (0, 12, "thread 0's face table written"),
                    (0, 11, "previous tile's stores read (MMA thread)"), (0, 1, "fields and face table"), (1, 2, "field split"), (2, 3, "fluxes (warp 0)"),
