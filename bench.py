@@ -68,9 +68,9 @@ def bytes_per_element(N: int, Npad: int) -> float:
 # capture of the current kernel exists. The N=7 32^3 entries are the 16^3
 # captures scaled by the element count (x8).
 NCU_TRAFFIC = {
-    ("fp16x3", 5, 24, "hilbert"): 391.87e6, ("fp16x3", 5, 24, "lexicographic"): 387.582e6,
-    ("fp16x3", 7, 16, "hilbert"): 219.45e6, ("fp16x3", 7, 16, "lexicographic"): 218.986e6,
-    ("fp16x3", 7, 32, "hilbert"): 8 * 219.45e6, ("fp16x3", 7, 32, "lexicographic"): 8 * 218.986e6,
+    ("fp16x3", 5, 24, "hilbert"): 391.75e6, ("bf16x3", 5, 24, "hilbert"): 391.77e6,
+    ("fp16x3", 7, 16, "hilbert"): 220.30e6, ("bf16x3", 7, 16, "hilbert"): 219.38e6,
+    ("fp16x3", 7, 32, "hilbert"): 8 * 220.30e6, ("bf16x3", 7, 32, "hilbert"): 8 * 219.38e6,
 }
 
 
