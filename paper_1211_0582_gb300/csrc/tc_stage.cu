@@ -323,6 +323,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int NBLK = (kTileElems / 4) * KGF;
   constexpr int R2 = (NBLK + 15) / 16;
   const int eo = lane >> 3, kp = lane & 7;
+  // this lane's own face-node traces in the tile buffer (element row offset
+  // plus volume node; the pair's second node falls back to the first past the
+  // face's last node), the same for every tile: two 16-bit offsets per block
+  int own_off[R2];
+#pragma unroll
+  for (int s = 0; s < R2; ++s) {
+    const int blk = warp + 16 * s;
+    const int e = 4 * (blk / KGF) + eo, fm = 16 * (blk % KGF) + 2 * kp;
+    const int f = fm / NFPE, mm = fm - f * NFPE;
+    own_off[s] = 0;
+    if (blk < NBLK && f < 4 && e < kTileElems) {
+      const int vm0 = s_fm[f * NFP + mm], vm1 = s_fm[f * NFP + mm + (mm + 1 < NFP ? 1 : 0)];
+      own_off[s] = (e * NPP + vm0) | ((e * NPP + vm1) << 16);
+    }
+  }
 
   // epilogue: one thread per (element, field) row of the accumulators
   const int quarter = warp & 3, part = warp >> 2;
@@ -504,10 +519,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           {
             // both nodes of the pair at once (the second may be past the face's last node)
             const bool two = mm + 1 < NFP;
-            const int vm0 = s_fm[f * NFP + mm], vm1 = s_fm[f * NFP + mm + (two ? 1 : 0)];
+            const int o0 = own_off[s] & 0xFFFF, o1 = own_off[s] >> 16;
             float2 qm[6], q[6], o[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) qm[c] = make_float2(s_u[c * FS + e * NPP + vm0], s_u[c * FS + e * NPP + vm1]);
+            for (int c = 0; c < 6; ++c) qm[c] = make_float2(s_u[c * FS + o0], s_u[c * FS + o1]);
 #pragma unroll
             for (int c = 0; c < 6; ++c)
               q[c] = make_float2(lidx[s][0] >= 0 ? s_u[c * FS + lidx[s][0]] : qp[s][0][c],
