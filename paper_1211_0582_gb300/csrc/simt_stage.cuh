@@ -109,10 +109,15 @@ __device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, 
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         float uj = su[c * EB * NPP + j];
+        // packed FP32 pairs: two output nodes per instruction
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int n = 0; n < 4; ++n) acc[d][c][n] = fmaf(dv[d][n], uj, acc[d][c][n]);
+          for (int n = 0; n < 4; n += 2) {
+            const float2 r = f2fma(make_float2(dv[d][n], dv[d][n + 1]), f2(uj), make_float2(acc[d][c][n], acc[d][c][n + 1]));
+            acc[d][c][n] = r.x;
+            acc[d][c][n + 1] = r.y;
+          }
       }
     }
     const float *g = a.geo + (live ? k : 0) * G_STRIDE;
@@ -179,10 +184,9 @@ __device__ __forceinline__ void simt_stage_tile(const StageArgs &a, int64_t k0, 
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         float gv = sf[c * EB * NFF + fm];
-        vol[c][0] = fmaf(L.x, gv, vol[c][0]);
-        vol[c][1] = fmaf(L.y, gv, vol[c][1]);
-        vol[c][2] = fmaf(L.z, gv, vol[c][2]);
-        vol[c][3] = fmaf(L.w, gv, vol[c][3]);
+        const float2 v01 = f2fma(make_float2(L.x, L.y), f2(gv), make_float2(vol[c][0], vol[c][1]));
+        const float2 v23 = f2fma(make_float2(L.z, L.w), f2(gv), make_float2(vol[c][2], vol[c][3]));
+        vol[c][0] = v01.x, vol[c][1] = v01.y, vol[c][2] = v23.x, vol[c][3] = v23.y;
       }
     }
   }
