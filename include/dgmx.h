@@ -266,9 +266,13 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * right-hand side of one segment are held at a time. The forward sweep saves a
  * checkpoint at each segment start and stores the last segment directly, so
  * only the earlier segments are recomputed (nsteps - ckpt_every forward steps
- * in all). ckpt_every = 0 picks the longest segment that fits in half of the
- * device memory that is free or already held by these buffers (one segment,
- * no recomputation, when the whole run fits); dg_adjoint_segment_steps reports
+ * in all). With more than one segment, the recomputation of a segment runs on
+ * a second stream owned by the context while the reverse sweep of the next
+ * one runs on the context's stream (two segment buffers; events order them).
+ * ckpt_every = 0 picks the longest segment that fits in half of the device
+ * memory that is free or already held by these buffers (then halved when
+ * more than one segment is needed, for the two buffers; one segment, no
+ * recomputation, when the whole run fits); dg_adjoint_segment_steps reports
  * the choice. Inputs (DEVICE): u0 [6][K][Np_pad], eps (K, or NULL = current),
  * recv (R), Eref [nsteps][3][R] FP32. Outputs: *J (HOST double), dJ_deps
  * (DEVICE, K doubles, reduced in FP64; may be NULL), dJ_du0 (DEVICE field
@@ -276,7 +280,8 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * and the misfit are computed (no checkpoints, no reverse sweep; segment
  * length reported as 0). FP32 CUDA-core kernels regardless of the context's
  * precision. Device memory: about (nsteps/ckpt_every + 7.5 ckpt_every + 8)
- * field vectors. Synchronises. Errors: DG_ERR_ARG (also ckpt_every < 0),
+ * field vectors in one segment, (nsteps/ckpt_every + 15 ckpt_every + 10) with
+ * several. Synchronises. Errors: DG_ERR_ARG (also ckpt_every < 0),
  * DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE. */
 int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, int ckpt_every,
                     float alpha, const int64_t *recv, int64_t R, const float *Eref, double *J, double *dJ_deps,
