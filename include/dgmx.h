@@ -59,9 +59,11 @@ typedef enum {
 typedef enum {
   DG_FP32 = 0,   /* FP32 arithmetic on the CUDA cores */
   DG_BF16X3 = 1, /* D and LIFT contractions on tensor cores, BF16 hi+lo split, FP32 accumulate */
-  DG_FP16X3 = 2  /* same with FP16 hi+lo split, FP32 accumulate; power-of-two scaled per
+  DG_FP16X3 = 2, /* same with FP16 hi+lo split, FP32 accumulate; power-of-two scaled per
                     (element, field) row of the field operand and per element and field
                     type (E, H) of the flux operand (FP16 range) */
+  DG_FP32_TC = 3  /* FP32-level accuracy on the tensor cores: the split whose error matches
+                     the FP32 path (FP16X3; the context then reports and behaves as FP16X3) */
 } dg_precision;
 /* The FP32 precision covers N = 1..9. The tensor-core precisions cover
  * N = 1..7 (DG_ERR_UNSUPPORTED at mesh upload for N = 8, 9): up to N = 5 the split operators

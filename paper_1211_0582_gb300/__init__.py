@@ -21,7 +21,7 @@ _lib = None
 DG_OK = 0
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_CUDA", -4: "DG_ERR_NONFINITE",
           -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_UNSUPPORTED", -7: "DG_ERR_OOM"}
-PRECISION = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
+PRECISION = {"fp32": 0, "bf16x3": 1, "fp16x3": 2, "fp32_tc": 3}
 
 
 class DGError(RuntimeError):

@@ -108,8 +108,9 @@ int dg_create(dg_ctx **out, int N, int precision, void *cuda_stream) {
   if (!out) return set_err(nullptr, DG_ERR_ARG, "dg_create: out is NULL");
   *out = nullptr;
   if (N < 1 || N > kMaxOrder) return set_err(nullptr, DG_ERR_ARG, "dg_create: N must be in 1..9");
-  if (precision != DG_FP32 && precision != DG_BF16X3 && precision != DG_FP16X3)
+  if (precision != DG_FP32 && precision != DG_BF16X3 && precision != DG_FP16X3 && precision != DG_FP32_TC)
     return set_err(nullptr, DG_ERR_ARG, "dg_create: unknown precision");
+  if (precision == DG_FP32_TC) precision = DG_FP16X3; // the split that reaches FP32 error
   dg_ctx *c = new (std::nothrow) dg_ctx();
   if (!c) return set_err(nullptr, DG_ERR_OOM, "dg_create: out of host memory");
   c->N = N;

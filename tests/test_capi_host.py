@@ -92,6 +92,9 @@ def test_create_rejects_bad_arguments():
     assert L.dg_create(C.byref(h), 10, 0, None) == -1
     assert L.dg_create(C.byref(h), 3, 9, None) == -1
     assert b"precision" in L.dg_last_error(None)
+    assert L.dg_create(C.byref(h), 3, 4, None) == -1
+    assert L.dg_create(C.byref(h), 3, 3, None) == 0  # DG_FP32_TC
+    assert L.dg_destroy(h) == 0
     assert L.dg_create(None, 3, 0, None) == -1
 
 

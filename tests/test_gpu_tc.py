@@ -44,6 +44,18 @@ def test_tc_rhs_parity(precision, N, n):
     s.sync()
 
 
+@pytest.mark.parametrize("N,n", [(5, 4), (7, 3)])
+def test_fp32_tc_precision_is_the_fp32_accurate_split(N, n):
+    # DG_FP32_TC asks for FP32-level accuracy on the tensor cores: the FP16x3
+    # split, bit for bit, within the FP32 tolerance of the oracle
+    s, m = pair(N, n, "fp32_tc")
+    s16, _ = pair(N, n, "fp16x3")
+    u = np.random.default_rng(12).standard_normal(m.shape)
+    got = s.from_device(s.rhs(s.to_device(u)))
+    np.testing.assert_array_equal(got, s16.from_device(s16.rhs(s16.to_device(u))))
+    assert rel_l2(got, m.rhs(u)) < 1e-5
+
+
 @pytest.mark.parametrize("N,precision", [(3, "fp32"), (6, "fp32"), (4, "fp16x3"), (5, "bf16x3"), (7, "fp16x3"),
                                          (6, "bf16x3")])
 def test_step_ignores_entry_residual(N, precision):
