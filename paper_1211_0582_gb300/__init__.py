@@ -281,6 +281,44 @@ class Solver:
         return E.value
 
 
+class MaxwellSolve:
+    """torch.autograd.Function: the receiver traces E(recv) after each of
+    nsteps LSERK4 steps from u0 with per-element permittivity eps, shape
+    [nsteps][3][R] (dg_receiver_traces). backward(G), G = dL/dtraces, runs the
+    library's hand-written adjoint (dg_adjoint_step) against the reference
+    traces E_ref = traces - G / 2: the gradient of that misfit,
+    sum_n 2 (P u_n - E_ref,n) . d(P u_n), is sum_n G_n . d traces_n, the
+    vector-Jacobian product. The residuals P u_n - E_ref,n are formed in FP32
+    from the same traces, so G is carried to about one FP32 ulp of the traces."""
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _Solve(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, u0, eps, solver, recv, dt, nsteps, ckpt_every, alpha):
+                u0c, epsc = u0.detach().contiguous(), eps.detach().contiguous()
+                traces = solver.receiver_traces(u0c, recv, dt, nsteps, eps=epsc, alpha=alpha)
+                ctx.save_for_backward(u0c, epsc, recv, traces)
+                ctx.args = (solver, dt, nsteps, ckpt_every, alpha)
+                return traces
+
+            @staticmethod
+            def backward(ctx, G):
+                u0c, epsc, recv, traces = ctx.saved_tensors
+                solver, dt, nsteps, ckpt_every, alpha = ctx.args
+                Eref = (traces - 0.5 * G.to(traces.dtype)).contiguous()
+                _, g_eps, g_u0 = solver.adjoint(u0c, recv, Eref, dt, nsteps, ckpt_every, eps=epsc, alpha=alpha)
+                return g_u0, g_eps.to(torch.float32), None, None, None, None, None, None
+
+        return _Solve
+
+    @classmethod
+    def apply(cls, u0, eps, solver, recv, dt, nsteps, ckpt_every=20, alpha=1.0):
+        return cls._fn().apply(u0, eps, solver, recv, dt, nsteps, ckpt_every, alpha)
+
+
 class ReceiverMisfit:
     """torch.autograd.Function: J(u0, eps) = sum over steps and receivers of
     |E - E_ref|^2 for an LSERK4 run. When u0 or eps requires a gradient the

@@ -111,6 +111,36 @@ def test_receiver_misfit_autograd_function():
     assert abs(float(J1) - Jo) < 1e-5 * Jo
 
 
+def test_maxwell_solve_autograd_function():
+    # traces out; backward = the vector-Jacobian product through the adjoint,
+    # against the oracle's discrete adjoint of the misfit whose residuals are
+    # G / 2 (E_ref = traces - G / 2), and against ReceiverMisfit for
+    # L = |traces - E_ref|^2 (G = 2 (traces - E_ref))
+    N, n, steps, ck = 4, 6, 12, 5
+    s, m, eps, eps_t, u0, u0d, recv, rd, Eref, dt = _misfit_problem(N, n, steps)
+    epsd = torch.as_tensor(eps, device="cuda")
+    u_in = u0d.clone().requires_grad_(True)
+    e_in = epsd.clone().requires_grad_(True)
+    tr = dg.MaxwellSolve.apply(u_in, e_in, s, rd, dt, steps, ck)
+    assert tr.shape == (steps, 3, rd.numel()) and tr.requires_grad
+    ref = m.receiver_traces(u0, dt, steps, recv, eps=eps.astype(np.float64))
+    assert rel(tr.detach().double().cpu().numpy(), ref) < 1e-5
+    w = torch.as_tensor(np.random.default_rng(5).standard_normal(tuple(tr.shape)), dtype=torch.float32,
+                        device="cuda") * tr.detach().abs().max()
+    (w * tr).sum().backward()
+    Eo = ref - 0.5 * w.double().cpu().numpy()
+    _, go_eps, go_u0 = m.misfit_gradient(u0, dt, steps, recv, Eo, eps=eps.astype(np.float64))
+    assert rel(e_in.grad.double().cpu().numpy(), go_eps) < 1e-4
+    assert rel(s.from_device(u_in.grad), go_u0) < 1e-4
+    # L = misfit: the same gradients as ReceiverMisfit
+    u2 = u0d.clone().requires_grad_(True)
+    e2 = epsd.clone().requires_grad_(True)
+    ((dg.MaxwellSolve.apply(u2, e2, s, rd, dt, steps, ck) - Eref) ** 2).sum().backward()
+    _, ge_ref, gu_ref = s.adjoint(u0d, rd, Eref, dt, steps, ck, eps=epsd)
+    assert rel(e2.grad.double().cpu().numpy(), ge_ref.cpu().numpy()) < 1e-5
+    assert rel(s.from_device(u2.grad), s.from_device(gu_ref)) < 1e-5
+
+
 def test_adjoint_segmentations_agree():
     # 4^3 x 6 tets at N=4, 12 steps: one-step segments (everything recomputed),
     # segments of 5 aligned to the end (2 + 5 + 5, the last one stored by the
