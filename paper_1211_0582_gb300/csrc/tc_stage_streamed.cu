@@ -246,6 +246,9 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     if (tu < ntiles) {
       const int64_t kb = int64_t(tu) * kTileS, nb = a.K - kb < kTileS ? a.K - kb : kTileS;
       for (int f = 0; f < 6; ++f) umma::prefetch_l2(a.u + f * KN + kb * NPP, uint32_t(nb * NPP * 4));
+      umma::prefetch_l2(a.fconn + kb * 4, uint32_t(nb * 32));
+      umma::prefetch_l2(a.fgeo + kb * 4, uint32_t(nb * 64));
+      umma::prefetch_l2(a.fmat + kb * 4, uint32_t(nb * 64));
     }
     if (MODE == MODE_LSERK && a.rk_a != 0.f && tr < ntiles) {
       const int64_t kb = int64_t(tr) * kTileS, nb = a.K - kb < kTileS ? a.K - kb : kTileS;
@@ -268,6 +271,15 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 
     // ---- 1. fields and face table of the tile into registers; once the
     // previous tile's bulk stores have read shared memory, the staging and A1
+    // the face table first, so that its loads are in flight with the fields'
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 1.f, 1.f);
+    int2 cn = make_int2(0, kBoundaryConn);
+    if (tid < kTileS * 4 && (tid >> 2) < ne) {
+      const int64_t q = (k0 + (tid >> 2)) * 4 + (tid & 3);
+      cn = __ldg(a.fconn + q);
+      g0 = __ldg(a.fgeo + q);
+      g1 = __ldg(a.fmat + q);
+    }
     float4 v[R1];
     float mx = 0.f;
 #pragma unroll
@@ -289,14 +301,6 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     if (tid == 0 && mx >= 0.f) TS_MARK(true, 10); // after thread 0's field loads have landed (FP16)
 #endif
     if (tid < kTileS * 4) {
-      float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 1.f, 1.f);
-      int2 cn = make_int2(0, kBoundaryConn);
-      if ((tid >> 2) < ne) {
-        const int64_t q = (k0 + (tid >> 2)) * 4 + (tid & 3);
-        cn = __ldg(a.fconn + q);
-        g0 = __ldg(a.fgeo + q);
-        g1 = __ldg(a.fmat + q);
-      }
       s_face[tid * 3 + 0] = g0;
       s_face[tid * 3 + 1] = g1;
       s_face[tid * 3 + 2] = make_float4(__int_as_float(cn.x), __int_as_float(cn.y), 0.f, 0.f);
