@@ -69,8 +69,11 @@ def bytes_per_element(N: int, Npad: int) -> float:
 # captures scaled by the element count (x8).
 NCU_TRAFFIC = {
     ("fp16x3", 5, 24, "hilbert"): 391.75e6, ("bf16x3", 5, 24, "hilbert"): 391.77e6,
-    ("fp16x3", 7, 16, "hilbert"): 220.30e6, ("bf16x3", 7, 16, "hilbert"): 219.38e6,
-    ("fp16x3", 7, 32, "hilbert"): 8 * 220.30e6, ("bf16x3", 7, 32, "hilbert"): 8 * 219.38e6,
+    ("fp32", 5, 24, "hilbert"): 394.45e6,
+    ("fp16x3", 7, 16, "hilbert"): 220.23e6, ("bf16x3", 7, 16, "hilbert"): 219.47e6,
+    ("fp32", 7, 16, "hilbert"): 221.75e6,
+    ("fp16x3", 7, 32, "hilbert"): 8 * 220.23e6, ("bf16x3", 7, 32, "hilbert"): 8 * 219.47e6,
+    ("fp32", 7, 32, "hilbert"): 8 * 221.75e6,
 }
 
 
