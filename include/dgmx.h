@@ -270,7 +270,9 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * only the earlier segments are recomputed (nsteps - ckpt_every forward steps
  * in all). With more than one segment, the recomputation of a segment runs on
  * a second stream owned by the context while the reverse sweep of the next
- * one runs on the context's stream (two segment buffers; events order them).
+ * one runs on the context's stream (two segment buffers; events order them),
+ * and the forward sweep fills both buffers: the last two segments are stored
+ * directly (nsteps - 2 ckpt_every steps recomputed).
  * ckpt_every = 0 picks the longest segment that fits in half of the device
  * memory that is free or already held by these buffers (then halved when
  * more than one segment is needed, for the two buffers; one segment, no
@@ -281,7 +283,9 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * vector; may be NULL). With both gradient outputs NULL only the forward run
  * and the misfit are computed (no checkpoints, no reverse sweep; segment
  * length reported as 0). FP32 CUDA-core kernels regardless of the context's
- * precision. Device memory: about (nsteps/ckpt_every + 7.5 ckpt_every + 8)
+ * precision; each reverse stage is one volume kernel that also runs the next
+ * stage's lift (one separate lift per step, after the receiver source).
+ * Device memory: about (nsteps/ckpt_every + 7.5 ckpt_every + 8)
  * field vectors in one segment, (nsteps/ckpt_every + 15 ckpt_every + 10) with
  * several. Synchronises. Errors: DG_ERR_ARG (also ckpt_every < 0),
  * DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE. */

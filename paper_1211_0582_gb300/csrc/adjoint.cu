@@ -31,11 +31,14 @@ namespace dgmx {
 
 struct AdjArgs {
   const float *lr_in;  // lambda_r (read)
-  float *lr_out;       // k_adj_lift: lr_scale lr + b lu (may alias lr_in, may be null); k_adj_vol: a * lr (may be null)
+  float *lr_out;       // k_adj_lift: lr_scale lr + b lu (may alias lr_in, may be null); k_adj_vol: a * lr (may be
+                       // null), or with the next lift fused in a * lr + b_next * lu_out (may alias lr_in)
   float lr_scale;      // k_adj_lift: the factor a of the stage reversed before, still to be applied to lr
   const float *lu_in;  // lambda_u (read; null = 0)
   float *lu_out;       // k_adj_vol: lu + dt A^T lr
   float *g;            // face data [6][K][NFF]
+  float *g_next;       // k_adj_vol with the next lift fused in: that lift's face data (not g)
+  float b_next;        // ... and the b of the stage it belongs to
   const float *u_s;    // stage state (eps gradient; null = no gradient)
   const float *rhs_s;  // A u_s at that stage
   double *grad;        // K, FP64 accumulation of dt <lr, dA/deps u_s>
@@ -217,11 +220,15 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT1) k_adj_lift(AdjArgs a) {
 }
 
 // ---- 2. lu <- lu + dt A^T lr; lr <- a lr; grad += dt <lr, dA/deps u_s>
-template <int N, bool GRAD>
+// FUSE: the lift of the stage reversed next runs here too (it is element-local:
+// lr <- a lr + b_next lu and g_next = Fscale * LIFT^T (W lr) need only this
+// element's new lu), which saves the separate pass over lr and lu.
+template <int N, bool GRAD, bool FUSE>
 __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
   using D = Dims<N>;
   using C = AdjCfg<N>;
   constexpr int NP = D::NP, NPP = D::NPP, NQ = D::NQ, NFF = D::NFF, NFP = D::NFP, EB = C::EB2, NT = C::NT2;
+  constexpr int MQ = C::MQ;
   extern __shared__ float4 smem4[];
   // per face of the block's elements: {n, 1/(Z-+Z+)}, {Z-, Z+, Y-, Y+},
   // {1/(Y-+Y+), dZ-/deps, dY-/deps, connection kind}, {neighbour element, wall}
@@ -386,7 +393,9 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
   //    E_c <- -d_{c+2}^T (W lr)_{H_{c+1}} + d_{c+1}^T (W lr)_{H_{c+2}}
   const int e = tid / NQ, q = tid - (tid / NQ) * NQ;
   const int64_t k = k0 + e;
-  if (tid < EB * NQ && k < a.K) {
+  const bool active = tid < EB * NQ && k < a.K;
+  float wl[6][4]; // FUSE: W lr of this lane's nodes after the update, for the fused lift
+  if (active) {
     float G[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) G[t] = __ldg(a.geo + k * G_STRIDE + t);
@@ -430,13 +439,64 @@ __global__ void __launch_bounds__(AdjCfg<N>::NT2) k_adj_vol(AdjArgs a) {
 #pragma unroll
       for (int n = 0; n < 4; ++n) o[n] = (4 * q + n < NP) ? fmaf(a.dt, wv[n], o[n]) : 0.f;
       *reinterpret_cast<float4 *>(a.lu_out + off) = make_float4(o[0], o[1], o[2], o[3]);
-      if (a.lr_out) {
+      if (FUSE) {
+        // the next lift's first half, in the separate lift's order of operations
+        const float4 lr = *reinterpret_cast<const float4 *>(a.lr_in + off);
+        const float lv[4] = {lr.x, lr.y, lr.z, lr.w};
+        float p[4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) p[n] = (4 * q + n < NP) ? fmaf(a.b_next, o[n], lv[n] * a.a) : 0.f;
+        *reinterpret_cast<float4 *>(a.lr_out + off) = make_float4(p[0], p[1], p[2], p[3]);
+        const float w = __ldg(a.geo + k * G_STRIDE + (c < 3 ? G_IEPS : G_IMU));
+#pragma unroll
+        for (int n = 0; n < 4; ++n) wl[c][n] = p[n] * w;
+      } else if (a.lr_out) {
         const float4 lr = *reinterpret_cast<const float4 *>(a.lr_in + off);
         *reinterpret_cast<float4 *>(a.lr_out + off) = make_float4(a.a * lr.x, a.a * lr.y, a.a * lr.z, a.a * lr.w);
       }
     }
   }
   if (GRAD && tid < EB && k0 + tid < a.K) a.grad[k0 + tid] += double(a.dt) * double(s_gr[tid]);
+  if constexpr (FUSE) {
+    // the next lift's second half: g_next = Fscale * LIFT^T (W lr), one
+    // (element, face-node quad) per item, from the new W lr in shared memory
+    __syncthreads(); // every lane has finished reading s_v in the transposed volume term
+    if (tid < EB * NQ)
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        reinterpret_cast<float4 *>(s_v)[(c * EB + e) * NQ + q] =
+            active ? make_float4(wl[c][0], wl[c][1], wl[c][2], wl[c][3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int t = tid; t < EB * MQ; t += NT) {
+      const int el = t / MQ, mq = t - (t / MQ) * MQ;
+      const int64_t kl = k0 + el;
+      if (kl >= a.K) continue;
+      float acc[6][4];
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) acc[c][n] = 0.f;
+#pragma unroll 4
+      for (int i = 0; i < NP; ++i) {
+        const float4 L = ldg4(a.LF + i * NFF + 4 * mq);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const float v = s_v[(c * EB + el) * NPP + i];
+          acc[c][0] = fmaf(L.x, v, acc[c][0]);
+          acc[c][1] = fmaf(L.y, v, acc[c][1]);
+          acc[c][2] = fmaf(L.z, v, acc[c][2]);
+          acc[c][3] = fmaf(L.w, v, acc[c][3]);
+        }
+      }
+      float fs[4];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) fs[n] = __ldg(a.fgeo + kl * 4 + (4 * mq + n) / NFP).w;
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        *reinterpret_cast<float4 *>(a.g_next + (c * a.K + kl) * NFF + 4 * mq) =
+            make_float4(fs[0] * acc[c][0], fs[1] * acc[c][1], fs[2] * acc[c][2], fs[3] * acc[c][3]);
+    }
+  }
 }
 
 template <int N>
@@ -450,15 +510,12 @@ cudaError_t launch_adj_order(int which, const AdjArgs &a, cudaStream_t s) {
     return launch_pdl(k_adj_lift<N>, dim3(unsigned((a.K + C::EB1 - 1) / C::EB1)), dim3(C::NT1), C::SMEM1, s, a);
   } else {
     const unsigned blocks = unsigned((a.K + C::EB2 - 1) / C::EB2);
-    if (a.u_s) {
-      e = cudaFuncSetAttribute(k_adj_vol<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
-      if (e != cudaSuccess) return e;
-      return launch_pdl(k_adj_vol<N, true>, dim3(blocks), dim3(C::NT2), C::SMEM2, s, a);
-    } else {
-      e = cudaFuncSetAttribute(k_adj_vol<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
-      if (e != cudaSuccess) return e;
-      return launch_pdl(k_adj_vol<N, false>, dim3(blocks), dim3(C::NT2), C::SMEM2, s, a);
-    }
+    auto go = [&](auto kern) {
+      cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM2));
+      return r != cudaSuccess ? r : launch_pdl(kern, dim3(blocks), dim3(C::NT2), C::SMEM2, s, a);
+    };
+    if (a.g_next) return a.u_s ? go(k_adj_vol<N, true, true>) : go(k_adj_vol<N, false, true>);
+    return a.u_s ? go(k_adj_vol<N, true, false>) : go(k_adj_vol<N, false, false>);
   }
 }
 
@@ -798,9 +855,10 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   float *resid = ws.get<float>(6, size_t(nsteps) * 3 * R);
   double *Jd = ws.get<double>(7, 1), *grad = ws.get<double>(8, ctx->K);
   float *ck = ws.get<float>(9, fl * nseg);
+  float *g2 = ws.get<float>(16, gfl); // the face data of the lift fused into the volume kernel (two in turn)
   // stage states u_s and the E components of the stage right-hand sides A u_s of one segment
   float *US = ws.get<float>(10, fl * 5 * C), *RS = ws.get<float>(11, hfl * 5 * C);
-  if (!u || !nxt || !res || !lu || !lr || !g || !resid || !Jd || !grad || !ck || !US || !RS)
+  if (!u || !nxt || !res || !lu || !lr || !g || !g2 || !resid || !Jd || !grad || !ck || !US || !RS)
     return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed (checkpoints and one segment of stage "
                                  "states are kept in device memory)");
   // the second segment buffer and the recompute stream's scratch; without
@@ -845,16 +903,22 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   };
 
   // ---- forward sweep: checkpoints at the segment starts, the last segment
-  // stored, and the receiver residuals
-  const int n0_last = seg_start(nseg - 1);
+  // stored (the last two when both segment buffers exist), and the receiver
+  // residuals
+  const int n0_stored = seg_start(overlap && nseg >= 2 ? nseg - 2 : nseg - 1);
   for (int n = 0, sg = 0; n < nsteps && e == cudaSuccess; ++n) {
     if (n == seg_start(sg)) {
       e = cudaMemcpyAsync(ck + fl * sg, u, fl * 4, cudaMemcpyDeviceToDevice, s);
       ++sg;
     }
     const float *after = u;
-    if (n >= n0_last) {
-      after = stored_step(n, n0_last, nseg - 1, (nseg - 1) % 2, s, res, nxt);
+    if (n >= n0_stored) {
+      // step n belongs to segment sg - 1, which starts from its checkpoint copy
+      after = stored_step(n, seg_start(sg - 1), sg - 1, (sg - 1) % 2, s, res, nxt);
+      if (sg < nseg && n + 1 == seg_start(sg)) {
+        // the state after the segment is the next checkpoint's source
+        if (e == cudaSuccess && after != u) e = cudaMemcpyAsync(u, after, fl * 4, cudaMemcpyDeviceToDevice, s);
+      }
     } else {
       sa.res = res;
       for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
@@ -876,10 +940,10 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
 
   // ---- reverse sweep, segment by segment
   AdjArgs aa = adj_base(ctx, alpha);
-  aa.g = g;
   aa.grad = grad;
   aa.dt = float(dt);
-  float pending = 1.f; // a of the stage reversed last, applied to lr by the next lift
+  float pending = 1.f; // a of the stage 1 reversed last, applied to lr by the next separate lift
+  float *gcur = g, *gnext = g2;
   // with two segment buffers, segment seg lives in buffer seg % 2, and the
   // segment before it is recomputed on the second stream while seg is reversed
   if (overlap && e == cudaSuccess) e = cudaEventRecord(ws.ev_fwd, s);
@@ -892,7 +956,9 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
       if (seg >= 1) {
         if (seg + 1 < nseg) e = cudaStreamWaitEvent(ws.s2, ws.ev_rev[(seg + 1) % 2], 0);
         const int p0 = seg_start(seg - 1);
-        for (int n = p0; n < n0 && e == cudaSuccess; ++n) stored_step(n, p0, seg - 1, (seg - 1) % 2, ws.s2, res2, nxt2);
+        // (the segment before the last one was stored by the forward sweep)
+        if (p0 < n0_stored)
+          for (int n = p0; n < n0 && e == cudaSuccess; ++n) stored_step(n, p0, seg - 1, (seg - 1) % 2, ws.s2, res2, nxt2);
         if (e == cudaSuccess) e = cudaEventRecord(ws.ev_rec[(seg - 1) % 2], ws.s2);
       }
       if (seg < nseg - 1 && e == cudaSuccess) e = cudaStreamWaitEvent(s, ws.ev_rec[b], 0);
@@ -906,18 +972,35 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
       for (int st = 4; st >= 0 && e == cudaSuccess; --st) {
         const size_t j = size_t(n - n0) * 5 + st;
         aa.lr_in = lr;
-        aa.lr_out = lr;
         aa.lu_in = lu;
-        aa.b = float(kLserkB[st]);
-        aa.lr_scale = pending;
-        e = launch_adj(ctx->N, 0, aa, s); // lr = pending lr + b lu; g = Fscale LIFT^T W lr
-        if (e != cudaSuccess) break;
-        aa.lr_out = nullptr;
+        if (st == 4) {
+          // the last stage's lift runs on its own: the receiver source has just changed lu
+          aa.lr_out = lr;
+          aa.b = float(kLserkB[st]);
+          aa.lr_scale = pending;
+          aa.g = gcur;
+          aa.g_next = nullptr;
+          e = launch_adj(ctx->N, 0, aa, s); // lr = pending lr + b lu; g = Fscale LIFT^T W lr
+          if (e != cudaSuccess) break;
+        }
         aa.lu_out = lu;
+        aa.g = gcur;
         aa.u_s = j == 0 ? ck + fl * seg : USb[b] + fl * j;
         aa.rhs_s = RSb[b] + hfl * j;
-        e = launch_adj(ctx->N, 1, aa, s); // lu += dt A^T lr; grad
-        pending = float(kLserkA[st]);
+        if (st > 0) {
+          // lu += dt A^T lr; grad; then the lift of stage st - 1: lr = a_st lr + b_{st-1} lu, g_next
+          aa.lr_out = lr;
+          aa.a = float(kLserkA[st]);
+          aa.b_next = float(kLserkB[st - 1]);
+          aa.g_next = gnext;
+          e = launch_adj(ctx->N, 1, aa, s);
+          std::swap(gcur, gnext);
+        } else {
+          aa.lr_out = nullptr;
+          aa.g_next = nullptr;
+          e = launch_adj(ctx->N, 1, aa, s); // lu += dt A^T lr; grad
+          pending = float(kLserkA[st]);
+        }
       }
     }
     if (overlap && e == cudaSuccess) e = cudaEventRecord(ws.ev_rev[b], s);
