@@ -282,16 +282,31 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * (DEVICE, K doubles, reduced in FP64; may be NULL), dJ_du0 (DEVICE field
  * vector; may be NULL). With both gradient outputs NULL only the forward run
  * and the misfit are computed (no checkpoints, no reverse sweep; segment
- * length reported as 0). FP32 CUDA-core kernels regardless of the context's
- * precision; each reverse stage is one volume kernel that also runs the next
- * stage's lift (one separate lift per step, after the receiver source).
+ * length reported as 0). The forward sweeps run the FP32 CUDA-core stage
+ * regardless of the context's precision. Each reverse stage is one volume
+ * kernel that also runs the next stage's lift (one separate lift per step,
+ * after the receiver source); for N <= 5 on a GB300 its two contractions (the
+ * transposed differentiation and lifting matrices) run on the tensor cores in
+ * the FP16x3 split (FP32-level accuracy), unless dg_set_adjoint_form chose
+ * the CUDA-core form.
  * Device memory: about (nsteps/ckpt_every + 7.5 ckpt_every + 8)
  * field vectors in one segment, (nsteps/ckpt_every + 15 ckpt_every + 10) with
  * several. Synchronises. Errors: DG_ERR_ARG (also ckpt_every < 0),
- * DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE. */
+ * DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE, DG_ERR_TIMEOUT (a bounded device
+ * wait of the tensor-core reverse stage ran out; see dg_set_wait_limit). */
 int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, int ckpt_every,
                     float alpha, const int64_t *recv, int64_t R, const float *Eref, double *J, double *dJ_deps,
                     float *dJ_du0);
+
+/* The form of dg_adjoint_step's reverse volume stage: 0 = FP32 CUDA cores,
+ * 1 = tensor cores (FP16x3 split of the transposed differentiation and lifting
+ * contractions; N <= 5 and a GB300, else DG_ERR_UNSUPPORTED). The default is
+ * the tensor-core form where it is supported. No counterpart in the paper
+ * (which has no adjoint); both forms compute the same discrete adjoint. */
+int dg_set_adjoint_form(dg_ctx *ctx, int form);
+
+/* The form the next dg_adjoint_step will use (0 or 1; -1 for a NULL ctx). */
+int dg_adjoint_form(const dg_ctx *ctx);
 
 /* Steps per segment used by the last dg_adjoint_step call on ctx (0 before
  * the first call, or for ctx == NULL). */

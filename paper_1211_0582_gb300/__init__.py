@@ -73,6 +73,8 @@ def lib():
             L.dg_receiver_traces.argtypes = [vp, vp, vp, dbl, i32, flt, vp, i64, vp]
             L.dg_adjoint_step.argtypes = [vp, vp, vp, dbl, i32, i32, flt, vp, i64, vp, C.POINTER(dbl), vp, vp]
             L.dg_adjoint_segment_steps.argtypes = [vp]
+            L.dg_set_adjoint_form.argtypes = [vp, i32]
+            L.dg_adjoint_form.argtypes = [vp]
             _lib = L
     return _lib
 
@@ -221,6 +223,13 @@ class Solver:
     def adjoint_segment_steps(self) -> int:
         """Steps per segment used by the last adjoint call (ckpt_every = 0 chooses it)."""
         return int(lib().dg_adjoint_segment_steps(self._h))
+
+    def set_adjoint_form(self, form: str):
+        """Reverse stage of the adjoint: "tensor" (tcgen05, FP16x3 split; N <= 5) or "cuda" (FP32 CUDA cores)."""
+        self._check(lib().dg_set_adjoint_form(self._h, {"cuda": 0, "tensor": 1}[form]))
+
+    def adjoint_form(self) -> str:
+        return "tensor" if lib().dg_adjoint_form(self._h) == 1 else "cuda"
 
     # ---------------------------------------------------------------- ensembles
     def upload_ensemble(self, meshes, eps=None, dt=None):

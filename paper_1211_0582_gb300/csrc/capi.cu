@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/dgmx.h"
+#include "adj_common.cuh"
 #include "common.cuh"
 #include "tc_api.h"
 
@@ -62,6 +63,7 @@ void free_mesh(dg_ctx *c) {
   tc_free(c);
   ensemble_free(c);
   adjoint_free(c);
+  adj_tc_free(c);
   c->K = 0;
 }
 

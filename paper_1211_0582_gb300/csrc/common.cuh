@@ -151,6 +151,8 @@ struct dg_ctx {
   void *tc = nullptr;          // tensor-core operator buffers (precision != DG_FP32)
   void *ens = nullptr;         // ensemble state (dg_ensemble_upload)
   void *adj = nullptr;         // adjoint / receiver-trace work buffers (grown on demand)
+  void *adj_tc = nullptr;      // operators of the tensor-core reverse stage (built on first use)
+  int adj_form = -1;           // reverse stage: 0 CUDA cores, 1 tensor cores, -1 tensor cores where supported
   int adj_segment = 0;         // steps per segment of the last dg_adjoint_step call
   std::vector<double> host_vert;   // VX, VY, VZ (kept for node coordinates)
   std::vector<int32_t> host_EToV;

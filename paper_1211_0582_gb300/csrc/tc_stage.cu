@@ -168,25 +168,6 @@ __device__ __forceinline__ void issue_split_gemm(uint32_t d_tmem, uint32_t a_hi,
   }
 }
 
-// The same products with the A operand (hi and lo) in tensor memory: one N
-// chunk; a K step of 16 advances the A address by 8 columns.
-template <bool BF16, int KP, int NR>
-__device__ __forceinline__ void issue_split_gemm_ta(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                                    uint32_t b_lo) {
-  constexpr uint32_t sbo = uint32_t(KP) * 16u;
-  static_assert(NR <= 256, "one N chunk");
-  const uint32_t idesc = umma::make_idesc(BF16, 128, uint32_t(NR));
-  const uint64_t dbh = umma::make_desc(b_hi, 128, sbo), dbl = umma::make_desc(b_lo, 128, sbo);
-#pragma unroll
-  for (int kk = 0; kk < KP / 16; ++kk) {
-    const uint64_t ko = uint64_t(kk) * 16u;
-    const uint32_t ac = uint32_t(8 * kk);
-    umma::mma_f16_ta(d_tmem, a_hi + ac, dbh + ko, idesc, kk > 0 ? 1u : 0u);
-    umma::mma_f16_ta(d_tmem, a_hi + ac, dbl + ko, idesc, 1u);
-    umma::mma_f16_ta(d_tmem, a_lo + ac, dbh + ko, idesc, 1u);
-  }
-}
-
 // Multi-step persistent form (ensembles): stage coefficients, the two state
 // buffers the stages alternate between, the step count and the grid barrier.
 struct EnsLaunch {

@@ -1,8 +1,11 @@
-"""GPU checks of the hand-written discrete adjoint (FP32 kernels, FP64 reductions).
+"""GPU checks of the hand-written discrete adjoint (FP32 kernels, the reverse
+stage's contractions on the tensor cores or the CUDA cores, FP64 reductions).
 
 - transpose identity <A u, v> = <u, A^T v> and parity of A^T with the oracle;
 - receiver traces and the misfit gradient against the FP64 oracle's discrete
   adjoint on the 6^3 x 6 version of the adjoint workload (N=4);
+- both forms of the reverse stage against the oracle at N = 1..5, and the
+  tensor-core form's bounded waits (timeout reported, context reusable);
 - the same gradient for every segmentation of the run (recomputed segments,
   segments aligned to the end with the last one stored, one stored segment,
   the automatic choice);
@@ -79,6 +82,51 @@ def test_adjoint_gradient_matches_oracle_discrete_adjoint():
     assert abs(J - Jo) < 1e-5 * Jo
     assert rel(g_eps.cpu().numpy(), go_eps) < 1e-4
     assert rel(s.from_device(g_u0), go_u0) < 1e-4
+
+
+@pytest.mark.parametrize("N,n", [(1, 3), (2, 3), (3, 3), (4, 4), (5, 2)])
+def test_adjoint_forms_agree_with_the_oracle(N, n):
+    # the reverse stage with its contractions on the tensor cores (FP16x3 split
+    # of D^T and LIFT^T) and on the CUDA cores both give the oracle's discrete
+    # adjoint; checkpoints every 3 of 7 steps (recomputed segments, a partial
+    # one, the fused and the separate lifts), partial element tiles
+    steps, ck = 7, 3
+    s, m, eps, eps_t, u0, u0d, recv, rd, Eref, dt = _misfit_problem(N, n, steps)
+    epsd = torch.as_tensor(eps, device="cuda")
+    Jo, go_eps, go_u0 = m.misfit_gradient(u0, dt, steps, recv, Eref.double().cpu().numpy(),
+                                          eps=eps.astype(np.float64))
+    assert s.adjoint_form() == "tensor"  # the default on a GB300 for N <= 5
+    out = {}
+    for form in ("tensor", "cuda"):
+        s.set_adjoint_form(form)
+        assert s.adjoint_form() == form
+        J, g_eps, g_u0 = s.adjoint(u0d, rd, Eref, dt, steps, ck, eps=epsd)
+        assert abs(J - Jo) < 1e-5 * Jo
+        assert rel(g_eps.cpu().numpy(), go_eps) < 1e-4, form
+        assert rel(s.from_device(g_u0), go_u0) < 1e-4, form
+        out[form] = (g_eps.cpu().numpy(), s.from_device(g_u0))
+    assert rel(out["tensor"][0], out["cuda"][0]) < 2e-5
+    assert rel(out["tensor"][1], out["cuda"][1]) < 2e-5
+
+
+def test_adjoint_tensor_form_wait_timeout_and_recovery():
+    # a wait limit of one cycle makes the tensor-core reverse stage's waits run
+    # out: DG_ERR_TIMEOUT, no fault; with the default limit the same context
+    # gives the undisturbed gradient again
+    N, n, steps = 4, 3, 4
+    s, m, eps, eps_t, u0, u0d, recv, rd, Eref, dt = _misfit_problem(N, n, steps)
+    epsd = torch.as_tensor(eps, device="cuda")
+    s.set_adjoint_form("tensor")
+    J0, ge0, gu0 = s.adjoint(u0d, rd, Eref, dt, steps, 2, eps=epsd)
+    s.set_wait_limit(1)
+    with pytest.raises(dg.DGError) as ei:
+        s.adjoint(u0d, rd, Eref, dt, steps, 2, eps=epsd)
+    assert ei.value.code == -5
+    s.set_wait_limit(0)
+    J1, ge1, gu1 = s.adjoint(u0d, rd, Eref, dt, steps, 2, eps=epsd)
+    assert abs(J1 - J0) <= 1e-12 * J0  # the misfit's FP64 atomic sums may reorder
+    assert rel(ge1.cpu().numpy(), ge0.cpu().numpy()) < 1e-6
+    assert rel(s.from_device(gu1), s.from_device(gu0)) < 1e-6
 
 
 def test_receiver_misfit_autograd_function():
