@@ -26,6 +26,7 @@ struct AdjArgs {
   const float *Dn;     // [3][Np][Npad] D_d[i][j]
   const float *LF;     // [Np][NFF] LIFT
   const uint8_t *fmask, *nbrtab, *nbrface;
+  const float4 *fcon;  // tensor-core form: [K][4][4] per-face constants of the transposed flux (launch_adj_face_consts)
   int64_t K;
   float alpha, a, b, dt;
 };
@@ -123,6 +124,11 @@ __device__ __forceinline__ void flux_weight_partials_w(const float *n, const flo
 // cudaErrorNotSupported where it does not apply (order, device).
 bool adj_tc_supported(const dg_ctx *ctx);
 cudaError_t launch_adj_tc(dg_ctx *ctx, const AdjArgs &a, cudaStream_t s);
+// The per-face constants the tensor-core form reads (they depend on eps
+// through the impedances; computed once per adjoint call): out is [K][4][4]
+// float4 {n, 1/(Z-+Z+)}, {Z-, Z+, Y-, Y+}, {1/(Y-+Y+), dZ-/deps, dY-/deps,
+// connection kind}, {neighbour element, wall}.
+cudaError_t launch_adj_face_consts(const dg_ctx *ctx, float4 *out, cudaStream_t s);
 void adj_tc_free(dg_ctx *ctx);
 
 } // namespace dgmx

@@ -752,6 +752,12 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   double *Jd = ws.get<double>(7, 1), *grad = ws.get<double>(8, ctx->K);
   float *ck = ws.get<float>(9, fl * nseg);
   float *g2 = ws.get<float>(16, gfl); // the face data of the lift fused into the volume kernel (two in turn)
+  // the reverse volume stage: its contractions on the tensor cores (FP16x3)
+  // where supported unless the CUDA-core form was asked for; that form reads
+  // per-face constants computed once per call
+  const bool tc_reverse = ctx->adj_form != 0 && adj_tc_supported(ctx);
+  float4 *fcon = tc_reverse ? ws.get<float4>(17, size_t(16) * ctx->K) : nullptr;
+  if (tc_reverse && !fcon) return fail(ctx, DG_ERR_OOM, "dg_adjoint_step: device allocation failed (face constants)");
   // stage states u_s and the E components of the stage right-hand sides A u_s of one segment
   float *US = ws.get<float>(10, fl * 5 * C), *RS = ws.get<float>(11, hfl * 5 * C);
   if (!u || !nxt || !res || !lu || !lr || !g || !g2 || !resid || !Jd || !grad || !ck || !US || !RS)
@@ -838,14 +844,15 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
   AdjArgs aa = adj_base(ctx, alpha);
   aa.grad = grad;
   aa.dt = float(dt);
-  // the reverse volume stage: its contractions on the tensor cores (FP16x3)
-  // where supported unless the CUDA-core form was asked for
-  const bool tc_reverse = ctx->adj_form != 0 && adj_tc_supported(ctx);
-  if (tc_reverse && e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s);
+  if (tc_reverse && e == cudaSuccess) {
+    aa.fcon = fcon;
+    e = launch_adj_face_consts(ctx, fcon, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s);
+  }
   auto reverse_stage = [&](const AdjArgs &x) {
     return tc_reverse ? launch_adj_tc(ctx, x, s) : launch_adj(ctx->N, 1, x, s);
   };
-  float pending = 1.f; // a of the stage 1 reversed last, applied to lr by the next separate lift
+  bool lifted = false; // the lift of the step's last stage already ran in the previous volume kernel
   float *gcur = g, *gnext = g2;
   // with two segment buffers, segment seg lives in buffer seg % 2, and the
   // segment before it is recomputed on the second stream while seg is reversed
@@ -870,39 +877,50 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
       for (int n = n0; n < n1 && e == cudaSuccess; ++n) stored_step(n, n0, seg, b, s, res, nxt);
     }
     for (int n = n1 - 1; n >= n0 && e == cudaSuccess; --n) {
-      k_recv_source<<<rb, 256, 0, s>>>(lu, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, resid + int64_t(n) * 3 * R);
-      e = cudaGetLastError();
+      if (!lifted) {
+        // the run's last step: its receiver source, then its last stage's lift on its own
+        k_recv_source<<<rb, 256, 0, s>>>(lu, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R, resid + int64_t(n) * 3 * R);
+        e = cudaGetLastError();
+        aa.lr_in = lr;
+        aa.lu_in = lu;
+        aa.lr_out = lr;
+        aa.b = float(kLserkB[4]);
+        aa.lr_scale = 1.f; // lr is still zero
+        aa.g = gcur;
+        aa.g_next = nullptr;
+        if (e == cudaSuccess) e = launch_adj(ctx->N, 0, aa, s); // lr = pending lr + b lu; g = Fscale LIFT^T W lr
+      }
       for (int st = 4; st >= 0 && e == cudaSuccess; --st) {
         const size_t j = size_t(n - n0) * 5 + st;
         aa.lr_in = lr;
         aa.lu_in = lu;
-        if (st == 4) {
-          // the last stage's lift runs on its own: the receiver source has just changed lu
-          aa.lr_out = lr;
-          aa.b = float(kLserkB[st]);
-          aa.lr_scale = pending;
-          aa.g = gcur;
-          aa.g_next = nullptr;
-          e = launch_adj(ctx->N, 0, aa, s); // lr = pending lr + b lu; g = Fscale LIFT^T W lr
-          if (e != cudaSuccess) break;
-        }
         aa.lu_out = lu;
         aa.g = gcur;
         aa.u_s = j == 0 ? ck + fl * seg : USb[b] + fl * j;
         aa.rhs_s = RSb[b] + hfl * j;
-        if (st > 0) {
-          // lu += dt A^T lr; grad; then the lift of stage st - 1: lr = a_st lr + b_{st-1} lu, g_next
+        if (st > 0 || n > 0) {
+          // lu += dt A^T lr; grad; then the lift of the stage reversed next,
+          // lr = a_st lr + b_next lu and g_next: stage st - 1, or the last stage
+          // of step n - 1. That step's receiver source goes into lu first: it
+          // and this stage's update both only add to lu
+          if (st == 0) {
+            k_recv_source<<<rb, 256, 0, s>>>(lu, ctx->K, ctx->ops.Np, ctx->ops.Npad, recv, R,
+                                             resid + int64_t(n - 1) * 3 * R);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) break;
+          }
           aa.lr_out = lr;
           aa.a = float(kLserkA[st]);
-          aa.b_next = float(kLserkB[st - 1]);
+          aa.b_next = float(kLserkB[st > 0 ? st - 1 : 4]);
           aa.g_next = gnext;
           e = reverse_stage(aa);
           std::swap(gcur, gnext);
+          lifted = st == 0;
         } else {
+          // the run's first stage: nothing to lift after it
           aa.lr_out = nullptr;
           aa.g_next = nullptr;
           e = reverse_stage(aa); // lu += dt A^T lr; grad
-          pending = float(kLserkA[st]);
         }
       }
     }

@@ -86,17 +86,36 @@ struct AT {
   static constexpr int OFF_LR = rup(OPS, 128); // fp32 [6][FS] lambda_r of the tile
   static constexpr int OFF_LU = OFF_LR + TB;   // fp32 [6][FS] lambda_u of the tile
   static constexpr int OFF_W = OFF_LU + TB;    // fp32 [6][FS] transposed-flux contributions
-  static constexpr int OFF_FACE = OFF_W + TB;  // float4 [80][4] per-face constants
+  static constexpr int OFF_RS = OFF_W + TB;    // fp32 [3][FS] E rows of the stage's right-hand side
+  static constexpr int OFF_FACE = OFF_RS + rup(3 * FS * 4, 128); // float4 [80][4] per-face constants
   static constexpr int OFF_FG = OFF_FACE + kAdjTile * 4 * 64; // float4 [80] {n, Fscale}
-  static constexpr int OFF_FC = OFF_FG + kAdjTile * 4 * 16;   // int2 [80] {neighbour, connection kind}
-  static constexpr int OFF_GEO = OFF_FC + kAdjTile * 4 * 8;   // float [20][G_STRIDE]
+  static constexpr int OFF_GEO = OFF_FG + kAdjTile * 4 * 16;  // float [20][G_STRIDE]
   static constexpr int OFF_TAB = OFF_GEO + kAdjTile * G_STRIDE * 4;
   // u32 [128] row maxima, float [128] inverse row scales, float [20] gradient partials
   static constexpr int OFF_MX = OFF_TAB + rup(NFF + 2 * kConnKinds * NFP, 16);
-  static constexpr int OFF_BAR = OFF_MX + 2 * 128 * 4 + rup(kAdjTile, 4) * 4; // barS, barD, barL; TMEM slot
-  static constexpr int SMEM = OFF_BAR + 32;
+  static constexpr int OFF_BAR = OFF_MX + 2 * 128 * 4 + rup(kAdjTile, 4) * 4; // barS, barF, barD, barL; TMEM slot
+  static constexpr int SMEM = OFF_BAR + 48;
   static_assert(SMEM <= 232448, "the reverse tile does not fit in shared memory");
 };
+
+// Optional phase timestamps (build with -DDGMX_STAGE_TIMING; off in the
+// library): thread 0's SM clock in cycles since the block passed its setup, at
+// the phase boundaries of each tile (slots 0-9), per block and tile, of the
+// last launch with a fused lift, read back with dgmx_adj_trace()
+// (stage_timing.py prints the breakdown).
+constexpr int kAdjTraceTiles = 16, kAdjTraceBlocks = 320, kAdjEvents = 12;
+#ifdef DGMX_STAGE_TIMING
+__device__ uint32_t g_adj_trace[kAdjTraceBlocks * kAdjTraceTiles * kAdjEvents];
+#define AT_MARK(ev)                                                                                                 \
+  do {                                                                                                              \
+    if (fuse && tid == 0 && itn < kAdjTraceTiles && blockIdx.x < kAdjTraceBlocks)                                   \
+      g_adj_trace[(blockIdx.x * kAdjTraceTiles + itn) * kAdjEvents + (ev)] = uint32_t(clock64() - at_t0);           \
+  } while (0)
+#else
+#define AT_MARK(ev) \
+  do {              \
+  } while (0)
+#endif
 
 template <int N>
 __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
@@ -108,18 +127,19 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
   float *s_lr = reinterpret_cast<float *>(smem + T::OFF_LR);
   float *s_lu = reinterpret_cast<float *>(smem + T::OFF_LU);
   float *s_w = reinterpret_cast<float *>(smem + T::OFF_W);
+  float *s_rs = reinterpret_cast<float *>(smem + T::OFF_RS);
   float4 *s_face = reinterpret_cast<float4 *>(smem + T::OFF_FACE);
   const float4 *s_fg = reinterpret_cast<const float4 *>(smem + T::OFF_FG);
-  const int2 *s_fc = reinterpret_cast<const int2 *>(smem + T::OFF_FC);
   const float *s_geo = reinterpret_cast<const float *>(smem + T::OFF_GEO);
   uint8_t *s_fm = smem + T::OFF_TAB;
   uint8_t *s_nb = s_fm + NFF, *s_nf = s_nb + kConnKinds * NFP;
   uint32_t *s_rmx = reinterpret_cast<uint32_t *>(smem + T::OFF_MX); // row maxima (float bits)
   float *s_inv = reinterpret_cast<float *>(s_rmx + 128);            // inverse row scales (compact rows)
   float *s_gr = s_inv + 128;                                         // eps-gradient partial per element
-  uint64_t *barS = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR);  // tile staged
-  uint64_t *barD = barS + 1, *barL = barS + 2;                       // GEMM-D, GEMM-L done
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 24);
+  uint64_t *barS = reinterpret_cast<uint64_t *>(smem + T::OFF_BAR);  // the tile's lambda rows staged
+  uint64_t *barF = barS + 1;                                         // its face and element data staged
+  uint64_t *barD = barS + 2, *barL = barS + 3;                       // GEMM-D, GEMM-L done
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + T::OFF_BAR + 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = tid == NT - 32;
@@ -137,6 +157,7 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
   for (int i = tid; i < kAdjTile; i += NT) s_gr[i] = 0.f;
   if (tid == 0) {
     umma::mbar_init(barS, 1);
+    umma::mbar_init(barF, 1);
     umma::mbar_init(barD, 1);
     umma::mbar_init(barL, 1);
     umma::fence_mbar_init();
@@ -171,53 +192,66 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
   const int ch0 = part * CPP, ch1 = (part + 1) * CPP < NCH ? (part + 1) * CPP : NCH;
   const int gc0 = part * GPP, gc1 = (part + 1) * GPP < GCH ? (part + 1) * GPP : GCH;
 
+  // the bulk copies of tile t (one thread): lambda_r and lambda_u rows on
+  // barS, face and element data on barF; the next tile's rows are requested as
+  // soon as the epilogue has read this tile's, its face data at the tile's end
+  auto stage_rows = [&](int t) {
+    const int64_t kb = int64_t(t) * kAdjTile;
+    const uint32_t nb = uint32_t(a.K - kb < kAdjTile ? a.K - kb : kAdjTile), bytes = nb * NPP * 4u;
+    umma::mbar_arrive_expect_tx(barS, (grad ? 15u : 12u) * bytes);
+    for (int f = 0; f < 6; ++f) {
+      umma::bulk_g2s(s_lr + f * FS, a.lr_in + f * KN + kb * NPP, bytes, barS);
+      umma::bulk_g2s(s_lu + f * FS, a.lu_in + f * KN + kb * NPP, bytes, barS);
+    }
+    if (grad)
+      for (int f = 0; f < 3; ++f) umma::bulk_g2s(s_rs + f * FS, a.rhs_s + f * KN + kb * NPP, bytes, barS);
+  };
+  auto stage_faces = [&](int t) {
+    const int64_t kb = int64_t(t) * kAdjTile;
+    const uint32_t nb = uint32_t(a.K - kb < kAdjTile ? a.K - kb : kAdjTile);
+    umma::mbar_arrive_expect_tx(barF, nb * (64u + G_STRIDE * 4u + 256u));
+    umma::bulk_g2s(smem + T::OFF_FG, a.fgeo + kb * 4, nb * 64u, barF);
+    umma::bulk_g2s(smem + T::OFF_GEO, a.geo + kb * G_STRIDE, nb * G_STRIDE * 4u, barF);
+    umma::bulk_g2s(s_face, a.fcon + kb * 16, nb * 256u, barF);
+  };
+  if (tid == 0 && int(blockIdx.x) < ntiles) {
+    stage_rows(blockIdx.x);
+    stage_faces(blockIdx.x);
+  }
+
   uint32_t phase = 0;
   bool failed = false;
+#ifdef DGMX_STAGE_TIMING
+  const long long at_t0 = clock64();
+#endif
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+#ifdef DGMX_STAGE_TIMING
+    const int itn = (tile - int(blockIdx.x)) / int(gridDim.x);
+#endif
+    AT_MARK(0);
     if (tile + int(gridDim.x) >= ntiles) pdl_launch_next(); // this block's last tile
     const int64_t k0 = int64_t(tile) * kAdjTile;
     const int ne = int(a.K - k0 < kAdjTile ? a.K - k0 : kAdjTile);
-    const uint32_t rb = uint32_t(ne * NPP * 4);
     const bool live = lane_used && e_loc < ne;
 
-    // ---- A. the tile's lambda_r, lambda_u, face and element data by bulk copies
-    if (tid == 0) {
-      umma::mbar_arrive_expect_tx(barS, 12u * rb + uint32_t(ne) * (64u + 32u + G_STRIDE * 4u));
-      for (int f = 0; f < 6; ++f) {
-        umma::bulk_g2s(s_lr + f * FS, a.lr_in + f * KN + k0 * NPP, rb, barS);
-        umma::bulk_g2s(s_lu + f * FS, a.lu_in + f * KN + k0 * NPP, rb, barS);
-      }
-      umma::bulk_g2s(smem + T::OFF_FG, a.fgeo + k0 * 4, uint32_t(ne) * 64u, barS);
-      umma::bulk_g2s(smem + T::OFF_FC, a.fconn + k0 * 4, uint32_t(ne) * 32u, barS);
-      umma::bulk_g2s(smem + T::OFF_GEO, a.geo + k0 * G_STRIDE, uint32_t(ne) * G_STRIDE * 4u, barS);
-    }
-    const bool okS = umma::mbar_wait_bounded(barS, phase, wlim);
+    const bool more = tile + int(gridDim.x) < ntiles;
+    // ---- A. the tile's lambda_r, lambda_u, face and element data (bulk copies
+    // requested during the previous tile)
+    const bool okS = umma::mbar_wait_bounded(barS, phase, wlim) && umma::mbar_wait_bounded(barF, phase, wlim);
     if (__syncthreads_or(!okS)) {
       if (tid == 0) {
         atomicExch(err_flag, 1);
-        umma::mbar_wait_bounded(barS, phase); // the copies in flight land before the block leaves
+        // the copies in flight land before the block leaves
+        umma::mbar_wait_bounded(barS, phase);
+        umma::mbar_wait_bounded(barF, phase);
       }
       failed = true;
       break;
     }
+    AT_MARK(1);
 
-    // ---- B. per-face constants of the transposed flux; W lr split into
-    // GEMM-D's A operand; the 1/eps term of the gradient, -<W lr_E, rhs_E>
-    for (int t = tid; t < ne * 4; t += NT) {
-      const int e = t >> 2;
-      const int2 cn = s_fc[t];
-      const float4 nf = s_fg[t];
-      const float *ge = s_geo + e * G_STRIDE;
-      const float Zk = ge[G_Z], Yk = ge[G_Y];
-      const bool wall = cn.y == kBoundaryConn;
-      const int64_t k2 = wall ? k0 + e : cn.x;
-      const float Z2 = wall ? Zk : __ldg(a.geo + k2 * G_STRIDE + G_Z), Y2 = wall ? Yk : __ldg(a.geo + k2 * G_STRIDE + G_Y);
-      const float ek = 1.f / ge[G_IEPS];
-      s_face[t * 4 + 0] = make_float4(nf.x, nf.y, nf.z, 1.f / (Zk + Z2));
-      s_face[t * 4 + 1] = make_float4(Zk, Z2, Yk, Y2);
-      s_face[t * 4 + 2] = make_float4(1.f / (Yk + Y2), -Zk / (2.f * ek), Yk / (2.f * ek), __int_as_float(cn.y));
-      s_face[t * 4 + 3] = make_float4(__int_as_float(int(k2)), __int_as_float(wall ? 1 : 0), 0.f, 0.f);
-    }
+    // ---- B. W lr split into GEMM-D's A operand; the 1/eps term of the
+    // gradient, -<W lr_E, rhs_E>
     float vv[16];
     {
       const float w = live ? s_geo[e_loc * G_STRIDE + (isE ? G_IEPS : G_IMU)] : 0.f;
@@ -234,7 +268,7 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
 #pragma unroll
           for (int j = 0; j < 16; j += 4) {
             if (kb + j < NPP) {
-              const float4 rs = __ldg(reinterpret_cast<const float4 *>(a.rhs_s + fld * KN + (k0 + e_loc) * NPP + kb + j));
+              const float4 rs = *reinterpret_cast<const float4 *>(s_rs + soff + kb + j);
               gpart -= vv[j] * rs.x + vv[j + 1] * rs.y + vv[j + 2] * rs.z + vv[j + 3] * rs.w;
             }
           }
@@ -260,6 +294,7 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
     umma::fence_before_sync();
     __syncthreads();
     if (tid < 128) s_rmx[tid] = 0u; // read above; the epilogue's maxima come after the face loop's barrier
+    AT_MARK(2);
 
     // ---- C. GEMM-D on the tensor cores (asynchronous, overlapping the face loop)
     if (issuer) {
@@ -286,9 +321,22 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
         const int cny = __float_as_int(r2.w);
         const int64_t k2 = __float_as_int(r3.x);
         const bool wall = __float_as_int(r3.y) != 0;
-        float gk[6];
+        const int vm = s_fm[fm];
+        const int fm2 = wall ? 0 : s_nf[cny * NFP + m] + (cny / 6 % 4) * NFP;
+        const int vn = wall ? 0 : s_nb[cny * NFP + m];
+        // every global load of the item first, all in flight together: the
+        // own and the neighbour's face data, the stage's own and exterior traces
+        float gk[6], g2[6], qm[6], qp[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) gk[c] = a.g[(c * a.K + k) * NFF + fm];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) g2[c] = wall ? 0.f : a.g[(c * a.K + k2) * NFF + fm2];
+        if (grad) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qm[c] = __ldg(a.u_s + c * KN + k * NPP + vm);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qp[c] = wall ? 0.f : __ldg(a.u_s + c * KN + k2 * NPP + vn);
+        }
         float ep3[3], hp3[3], acc[6];
         flux_transpose_w(n, gk, Z2, Y2, zs, ys, a.alpha, ep3, hp3);
 #pragma unroll
@@ -296,8 +344,6 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
           acc[c] = -ep3[c];
           acc[c + 3] = -hp3[c];
         }
-        const int fm2 = wall ? 0 : s_nf[cny * NFP + m] + (cny / 6 % 4) * NFP;
-        float g2[6];
         if (wall) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -305,8 +351,6 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
             acc[c + 3] += hp3[c];
           }
         } else {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) g2[c] = a.g[(c * a.K + k2) * NFF + fm2];
           const float n2[3] = {-n[0], -n[1], -n[2]};
           float ep2[3], hp2[3];
           flux_transpose_w(n2, g2, Zk, Yk, zs, ys, a.alpha, ep2, hp2);
@@ -316,24 +360,14 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
             acc[c + 3] += hp2[c];
           }
         }
-        const int vm = s_fm[fm];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) atomicAdd(&s_w[c * FS + e * NPP + vm], acc[c]);
         if (grad) {
           const float dZ = r2.y, dY = r2.z;
-          float qm[6], qp[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) qm[c] = __ldg(a.u_s + c * KN + k * NPP + vm);
           if (wall) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               qp[c] = -qm[c];
               qp[c + 3] = qm[c + 3];
             }
-          } else {
-            const int vn = s_nb[cny * NFP + m];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) qp[c] = __ldg(a.u_s + c * KN + k2 * NPP + vn);
           }
           float sZm, sZp, sYm, sYp;
           flux_weight_partials_w(n, qm, qp, Z2, Y2, zs, ys, a.alpha, gk, sZm, sZp, sYm, sYp);
@@ -347,10 +381,13 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
             contrib += tZp * dZ + tYp * dY;
           }
         }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) atomicAdd(&s_w[c * FS + e * NPP + vm], acc[c]);
       }
       if (grad) add_by_element(s_gr, e, contrib);
     }
     __syncthreads();
+    AT_MARK(3);
 
     // ---- E. epilogue: transposed curl from T (the row's FP16 scale undone
     // through the metric factors), plus the transposed flux; lambda_u updated;
@@ -373,6 +410,7 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
       failed = true;
       break;
     }
+    AT_MARK(4);
     umma::fence_after_sync();
     float wl[CPP][8];
     float mx2 = 0.f;
@@ -411,6 +449,8 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
           const int i = i0 + 4 * h;
           if (i < NPP) {
             const float4 sw4 = *reinterpret_cast<const float4 *>(s_w + soff + i);
+            // read once: cleared here for the next tile (entries no live row reads are never written)
+            *reinterpret_cast<float4 *>(s_w + soff + i) = make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 lu4 = *reinterpret_cast<const float4 *>(s_lu + soff + i);
             const float4 lr4 = *reinterpret_cast<const float4 *>(s_lr + soff + i);
             const float swv[4] = {sw4.x, sw4.y, sw4.z, sw4.w}, luv[4] = {lu4.x, lu4.y, lu4.z, lu4.w},
@@ -432,8 +472,11 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
       }
     }
     if (fuse && live) atomicMax(s_rmx + r, __float_as_uint(mx2));
+    umma::fence_proxy_async(); // the lambda rows were read: the next tile's copies may overwrite them
     umma::fence_before_sync();
     __syncthreads(); // T has been read; the row maxima of W lambda_r are complete
+    AT_MARK(5);
+    if (tid == 0 && more) stage_rows(tile + gridDim.x);
 
     // ---- F. the fused lift: W lambda_r split over T's columns, GEMM-L, and
     // g_next = Fscale * G
@@ -466,6 +509,7 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
       umma::tmem_wait_st();
       umma::fence_before_sync();
       __syncthreads();
+      AT_MARK(6);
       if (issuer) {
         umma::fence_after_sync();
         issue_split_gemm_ta<false, K1, T::NL>(tmem + uint32_t(T::CG), tmem + uint32_t(T::CAL),
@@ -478,10 +522,12 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
         if (tid == 0) {
           atomicExch(err_flag, 1);
           umma::mbar_wait_bounded(barL, phase);
+          if (more) umma::mbar_wait_bounded(barS, phase ^ 1u); // the next tile's rows in flight
         }
         failed = true;
         break;
       }
+      AT_MARK(7);
       umma::fence_after_sync();
       for (int gc = gc0; gc < gc1; ++gc) { // warp-uniform bounds
         float gv[8];
@@ -504,25 +550,49 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
       }
     }
 
-    // ---- G. the tile's gradient partials; buffers cleared for the next tile
+    AT_MARK(8);
+    // ---- G. the tile's gradient partials; buffers cleared for the next tile;
+    // the next tile's face data requested (this tile's have been read)
+    umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
+    if (tid == 0 && more) stage_faces(tile + gridDim.x);
     if (tid < kAdjTile) {
       const float gsum = s_gr[tid];
       s_gr[tid] = 0.f;
-      if (grad && tid < ne) a.grad[k0 + tid] += double(a.dt) * double(gsum);
+      // one block per element and launch: the sum is that of a plain update,
+      // issued without waiting for the old value
+      if (grad && tid < ne) atomicAdd(a.grad + k0 + tid, double(a.dt) * double(gsum));
     }
     if (tid < 128) s_rmx[tid] = 0u;
-    for (int i = tid; i < 6 * FS; i += NT) s_w[i] = 0.f;
-    // the next tile's bulk copies overwrite what was read here
-    umma::fence_proxy_async();
     __syncthreads();
+    AT_MARK(9);
     phase ^= 1u;
   }
   (void)failed;
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, T::TCOLS);
+}
+
+// Per-face constants of the transposed flux, one thread per face (see
+// launch_adj_face_consts).
+__global__ void k_adj_face_consts(int64_t K, const float *__restrict__ geo, const float4 *__restrict__ fgeo,
+                                  const int2 *__restrict__ fconn, float4 *__restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= 4 * K) return;
+  const int64_t k = t >> 2;
+  const int2 cn = fconn[t];
+  const float4 nf = fgeo[t];
+  const float Zk = geo[k * G_STRIDE + G_Z], Yk = geo[k * G_STRIDE + G_Y];
+  const bool wall = cn.y == kBoundaryConn;
+  const int64_t k2 = wall ? k : cn.x;
+  const float Z2 = wall ? Zk : geo[k2 * G_STRIDE + G_Z], Y2 = wall ? Yk : geo[k2 * G_STRIDE + G_Y];
+  const float ek = 1.f / geo[k * G_STRIDE + G_IEPS];
+  out[t * 4 + 0] = make_float4(nf.x, nf.y, nf.z, 1.f / (Zk + Z2));
+  out[t * 4 + 1] = make_float4(Zk, Z2, Yk, Y2);
+  out[t * 4 + 2] = make_float4(1.f / (Yk + Y2), -Zk / (2.f * ek), Yk / (2.f * ek), __int_as_float(cn.y));
+  out[t * 4 + 3] = make_float4(__int_as_float(int(k2)), __int_as_float(wall ? 1 : 0), 0.f, 0.f);
 }
 
 // Host: D^T and LIFT^T in the canonical K-major operand layout (FP16 hi, then
@@ -584,6 +654,12 @@ cudaError_t launch_adj_tc_order(const AdjArgs &a, const AdjTcState &st, long lon
 
 } // namespace
 
+#ifdef DGMX_STAGE_TIMING
+extern "C" int dgmx_adj_trace(uint32_t *host) {
+  return int(cudaMemcpyFromSymbol(host, g_adj_trace, sizeof(g_adj_trace)));
+}
+#endif
+
 bool adj_tc_supported(const dg_ctx *ctx) {
   if (!ctx || ctx->N < 1 || ctx->N > 5) return false;
   int dev = 0, major = 0, minor = 0;
@@ -633,6 +709,12 @@ cudaError_t launch_adj_tc(dg_ctx *ctx, const AdjArgs &a, cudaStream_t s) {
   case 4: return launch_adj_tc_order<4>(a, *st, ctx->wait_limit, flag, s);
   default: return launch_adj_tc_order<5>(a, *st, ctx->wait_limit, flag, s);
   }
+}
+
+cudaError_t launch_adj_face_consts(const dg_ctx *ctx, float4 *out, cudaStream_t s) {
+  const int64_t n = 4 * ctx->K;
+  k_adj_face_consts<<<unsigned((n + 255) / 256), 256, 0, s>>>(ctx->K, ctx->d_geo, ctx->d_fgeo, ctx->d_fconn, out);
+  return cudaGetLastError();
 }
 
 void adj_tc_free(dg_ctx *ctx) {

@@ -24,9 +24,19 @@ At N = 6, 7 (the kernel that streams its operators from L2, dgmx_tcs_trace):
   5 -> 6   geometry and first residual chunk; 6 -> 7 GEMM2 wait
   8 -> 9   epilogue
 
+The adjoint's tensor-core reverse stage (dgmx_adj_trace; case `adjoint N n`,
+a few steps of the adjoint workload's problem on the n^3 x 6 mesh):
+
+  0 -> 1   the tile's lambda_r, lambda_u and face data staged
+  1 -> 2   face constants, W lambda_r split into GEMM-D's operand (GEMM-D issued at 2)
+  2 -> 3   face loop: transposed flux, gradient weight terms
+  3 -> 4   GEMM-D wait; 4 -> 5 epilogue (transposed curl, lambda updates)
+  5 -> 6   W lambda_r split for GEMM-L; 6 -> 7 GEMM-L wait; 7 -> 8 face data stored
+  8 -> 9   gradient partials, buffers cleared
+
 Usage (on a GPU): python -m paper_1211_0582_gb300.stage_timing [precision N n] ...
-e.g. `fp16x3 5 24 bf16x3 5 24 fp16x3 7 16`. N <= 5 times the default
-(single-tile) form.
+e.g. `fp16x3 5 24 bf16x3 5 24 fp16x3 7 16 adjoint 4 20`. N <= 5 times the
+default (single-tile) form.
 """
 from __future__ import annotations
 
@@ -90,6 +100,48 @@ def breakdown(prec: str, N: int, n: int, order: str = "hilbert") -> dict:
     return out
 
 
+ADJ_TILES, ADJ_EVENTS, ADJ_BLOCKS = 16, 12, 320
+ADJ_PHASES = [(0, 1, "tile staged"), (1, 2, "face constants, split, GEMM-D issued"), (2, 3, "face loop"),
+              (3, 4, "GEMM-D wait"), (4, 5, "epilogue"), (5, 6, "split for GEMM-L"), (6, 7, "GEMM-L wait"),
+              (7, 8, "face data stored"), (8, 9, "gradient partials, clear")]
+
+
+def adjoint_breakdown(N: int, n: int, steps: int = 3) -> dict:
+    import torch
+
+    import paper_1211_0582_gb300 as dg
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import workloads as W
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    eps = W.element_eps(K, seed=2)
+    s = dg.Solver(N).upload(VX, VY, VZ, EToV, eps=eps)
+    s.set_adjoint_form("tensor")
+    x, y, z = s.node_coords()
+    u0 = s.to_device(W.gaussian_pulse(x, y, z, seed=7))
+    recv = torch.as_tensor(W.receivers(K, s.Np, 256, seed=4), device="cuda")
+    dt = 0.5 / n / N ** 2
+    Eref = s.receiver_traces(u0, recv, dt, steps, eps=torch.as_tensor(W.element_eps(K, seed=6), device="cuda"))
+    s.adjoint(u0, recv, Eref, dt, steps, 0, eps=torch.as_tensor(eps, device="cuda"))
+    buf = np.zeros(ADJ_BLOCKS * ADJ_TILES * ADJ_EVENTS, dtype=np.uint32)
+    rc = dg.lib().dgmx_adj_trace(buf.ctypes.data_as(C.c_void_p))
+    torch.cuda.synchronize()
+    if rc != 0:
+        raise RuntimeError(f"dgmx_adj_trace failed ({rc})")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nb = min(ADJ_BLOCKS, 2 * sms)
+    T = buf.reshape(ADJ_BLOCKS, ADJ_TILES, ADJ_EVENTS).astype(np.float64)[:nb]
+    nt = min(ADJ_TILES, K // 20 // nb)
+    if nt < 4:
+        raise ValueError("the mesh gives fewer than 4 tiles per block")
+    cur, nxt = T[:, 1:nt - 1], T[:, 2:nt]
+    out = {"period": float((nxt[:, :, 0] - cur[:, :, 0]).mean())}
+    for a, b, name in ADJ_PHASES:
+        out[name] = float((cur[:, :, b] - cur[:, :, a]).mean())
+    return out
+
+
 def main(argv) -> None:
     import paper_1211_0582_gb300 as dg
     dg._LIB_PATH = timing_library()
@@ -97,8 +149,12 @@ def main(argv) -> None:
     cases = [(argv[i], int(argv[i + 1]), int(argv[i + 2])) for i in range(0, len(argv) - 2, 3)] or \
         [("fp16x3", 5, 24), ("bf16x3", 5, 24), ("fp16x3", 4, 28)]
     for prec, N, n in cases:
-        b = breakdown(prec, N, n)
-        print(f"{prec} N={N} {n}^3x6 tets (Hilbert order): cycles per tile, thread 0")
+        if prec == "adjoint":
+            b = adjoint_breakdown(N, n)
+            print(f"adjoint reverse stage (tensor cores) N={N} {n}^3x6 tets: cycles per tile, thread 0 (last launch)")
+        else:
+            b = breakdown(prec, N, n)
+            print(f"{prec} N={N} {n}^3x6 tets (Hilbert order): cycles per tile, thread 0")
         for k, v in b.items():
             pct = "" if k == "period" or k.startswith(("first", "last", "thread 0", "previous")) or "issued" in k \
                 else f"  {100 * v / b['period']:5.1f}%"
