@@ -78,6 +78,11 @@ struct AT {
   static constexpr int CPP = (NCH + PARTS - 1) / PARTS;        // chunks per part
   static constexpr int GCH = NL / 8;                            // 8-column chunks of G
   static constexpr int GPP = (GCH + PARTS - 1) / PARTS;
+  // elements per tile: at most the 20 rows' worth, fewer where that makes the
+  // face loop (4 Nfp items per element over NT threads) one round shorter
+  static constexpr int R20 = (kAdjTile * NFF + NT - 1) / NT;
+  static constexpr int TE_FIT = R20 > 1 ? (R20 - 1) * NT / NFF : kAdjTile;
+  static constexpr int TE = TE_FIT >= 17 && TE_FIT < kAdjTile ? TE_FIT : kAdjTile;
   static constexpr int FS = kAdjTile * NPP + 4; // padded field-block stride of the staged tiles
   static constexpr int B1B = N1 * K1 * 2, B2B = NL * K1 * 2;
   static constexpr int OPS = 2 * B1B + 2 * B2B; // D^T blocks hi, lo, then LIFT^T blocks hi, lo
@@ -196,8 +201,8 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
   // barS, face and element data on barF; the next tile's rows are requested as
   // soon as the epilogue has read this tile's, its face data at the tile's end
   auto stage_rows = [&](int t) {
-    const int64_t kb = int64_t(t) * kAdjTile;
-    const uint32_t nb = uint32_t(a.K - kb < kAdjTile ? a.K - kb : kAdjTile), bytes = nb * NPP * 4u;
+    const int64_t kb = int64_t(t) * T::TE;
+    const uint32_t nb = uint32_t(a.K - kb < T::TE ? a.K - kb : T::TE), bytes = nb * NPP * 4u;
     umma::mbar_arrive_expect_tx(barS, (grad ? 15u : 12u) * bytes);
     for (int f = 0; f < 6; ++f) {
       umma::bulk_g2s(s_lr + f * FS, a.lr_in + f * KN + kb * NPP, bytes, barS);
@@ -207,8 +212,8 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
       for (int f = 0; f < 3; ++f) umma::bulk_g2s(s_rs + f * FS, a.rhs_s + f * KN + kb * NPP, bytes, barS);
   };
   auto stage_faces = [&](int t) {
-    const int64_t kb = int64_t(t) * kAdjTile;
-    const uint32_t nb = uint32_t(a.K - kb < kAdjTile ? a.K - kb : kAdjTile);
+    const int64_t kb = int64_t(t) * T::TE;
+    const uint32_t nb = uint32_t(a.K - kb < T::TE ? a.K - kb : T::TE);
     umma::mbar_arrive_expect_tx(barF, nb * (64u + G_STRIDE * 4u + 256u));
     umma::bulk_g2s(smem + T::OFF_FG, a.fgeo + kb * 4, nb * 64u, barF);
     umma::bulk_g2s(smem + T::OFF_GEO, a.geo + kb * G_STRIDE, nb * G_STRIDE * 4u, barF);
@@ -230,8 +235,8 @@ __global__ void __launch_bounds__(AT<N>::NT, AT<N>::MINB)
 #endif
     AT_MARK(0);
     if (tile + int(gridDim.x) >= ntiles) pdl_launch_next(); // this block's last tile
-    const int64_t k0 = int64_t(tile) * kAdjTile;
-    const int ne = int(a.K - k0 < kAdjTile ? a.K - k0 : kAdjTile);
+    const int64_t k0 = int64_t(tile) * T::TE;
+    const int ne = int(a.K - k0 < T::TE ? a.K - k0 : T::TE);
     const bool live = lane_used && e_loc < ne;
 
     const bool more = tile + int(gridDim.x) < ntiles;
@@ -645,7 +650,7 @@ cudaError_t launch_adj_tc_order(const AdjArgs &a, const AdjTcState &st, long lon
   const int tmem_fit = 512 / T::TCOLS;
   if (per_sm > tmem_fit) per_sm = tmem_fit;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int ntiles = int((a.K + kAdjTile - 1) / kAdjTile);
+  const int ntiles = int((a.K + T::TE - 1) / T::TE);
   const int cap = per_sm * st.sms;
   const int grid = ntiles < cap ? ntiles : cap;
   return launch_pdl(kern, dim3(unsigned(grid)), dim3(T::NT), size_t(T::SMEM), s, a,
