@@ -629,6 +629,13 @@ def adjoint_leg(stream, steps: int = 400, fd_dirs: int = 16) -> dict:
     # stored by the forward sweep, the other 360 of 400 steps recomputed)
     s.adjoint(u0, recv, Eref, dt, steps, 20, eps=epsd)
     adj20_ms = _timed(lambda: s.adjoint(u0, recv, Eref, dt, steps, 20, eps=epsd), stream)
+    form = s.adjoint_form()
+    # the same with the reverse stage's contractions on the CUDA cores
+    s.set_adjoint_form("cuda")
+    s.adjoint(u0, recv, Eref, dt, steps, 20, eps=epsd)
+    adj20c_ms = _timed(lambda: s.adjoint(u0, recv, Eref, dt, steps, 20, eps=epsd), stream)
+    if form == "tensor":
+        s.set_adjoint_form("tensor")
     h = 1e-3
     dirs = 2.0 * W.uniform(5, 16 * K).reshape(16, K)[:fd_dirs] - 1.0
     rels = []
@@ -643,8 +650,11 @@ def adjoint_leg(stream, steps: int = 400, fd_dirs: int = 16) -> dict:
     return {"workload": f"adjoint, 20^3x6 jittered tets, N=4, FP32, 256 receivers, {steps} steps",
             "K": K, "dof": dof, "steps": steps, "forward_ms": fwd_ms,
             "forward_gdof_s": STAGES * dof * steps / (fwd_ms * 1e-3) / 1e9, "J": J,
+            "reverse_stage": form + (" cores: FP16x3 tcgen05 transposed contractions, face loop on the CUDA cores"
+                                     if form == "tensor" else " cores"),
             "checkpoints_every_20": {"adjoint_ms": adj20_ms, "ratio": adj20_ms / fwd_ms,
-                                     "recomputed_steps": max(0, steps - 40)},
+                                     "recomputed_steps": max(0, steps - 40),
+                                     "cuda_core_reverse": {"adjoint_ms": adj20c_ms, "ratio": adj20c_ms / fwd_ms}},
             "automatic_segments": {"adjoint_ms": adj_ms, "ratio": adj_ms / fwd_ms, "segment_steps": seg,
                                    "recomputed_steps": steps - seg,
                                    "segment_bytes": int(seg * 5 * 1.5 * 6 * K * ((s.Np + 3) // 4 * 4) * 4)},
