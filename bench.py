@@ -552,6 +552,7 @@ def run_ensemble(args):
     u_init = u.clone()
     ens.ensemble_tune(force=True)
     best, ebs, tms = ens.ensemble_tuning()
+    gbest, geb, gbps, gms = ens.ensemble_tuning_grid()
     steps, warm = args.steps, max(3, args.warmup)
     ens.ensemble_step(u, res, warm)
     ms = _timed(lambda: ens.ensemble_step(u, res, steps), stream)
@@ -587,7 +588,9 @@ def run_ensemble(args):
                                  "launches_per_call": 1},
             "per_mesh_launches": {"gdof_s": STAGES * dof * steps / (ms2 * 1e-3) / 1e9, "ms_per_step": ms2 / steps,
                                   "launches_per_step": 5 * len(meshes)},
-            "autotune": {"elements_per_block": ebs, "ms_per_step": tms, "chosen": best},
+            "autotune": {"elements_per_block": ebs, "ms_per_step": tms, "chosen": best,
+                         "grid": {"elements_per_block": geb, "blocks_per_sm": gbps, "ms_per_step": gms,
+                                  "chosen_candidate": gbest}},
             "fp16x3_persistent": {"gdof_s": STAGES * dof * steps / (ms16 * 1e-3) / 1e9, "ms_per_step": ms16 / steps,
                                   "graph_replay": ens16.ensemble_graph_used(), "tile_elements": 20,
                                   "rel_l2_vs_fp32_after_10_steps": diff16}}

@@ -210,17 +210,29 @@ int dg_ensemble_layout(const dg_ctx *ctx, int *M, int64_t *offsets);
  * (in/out; the entry value of res is not read). */
 int dg_ensemble_step(dg_ctx *ctx, float *u, float *res, int nsteps, float alpha);
 
-/* Autotuner: time every elements-per-block candidate of the persistent
- * launch on the uploaded ensemble (2 steps, best of 3) and keep the fastest;
+/* Autotuner: time every candidate of the persistent launch on the uploaded
+ * ensemble (2 steps, best of 3) and keep the fastest. The candidates form a
+ * two-axis grid: 4 elements-per-block values x 2 occupancy levels (as many
+ * blocks per SM as fit, or half as many: fewer blocks take part in each grid
+ * barrier and each loops over more tiles); the second level is timed only
+ * where it launches fewer blocks;
  * the choice is cached in a text file (environment DGMX_TUNE_CACHE, default
  * $HOME/.cache/dgmx_ensemble_tune.txt) keyed by GPU name, N and total element
  * count, and reused unless force is nonzero. Synchronises the stream. */
 int dg_ensemble_tune(dg_ctx *ctx, int force);
 
-/* Tuning log: the chosen elements per block, and for each of the 4 candidates
- * its elements per block and measured ms per step (0 = not timed; the
- * tensor-core form has one candidate, 20). HOST outputs. */
+/* Tuning log: the chosen elements per block, and for each of the 4
+ * elements-per-block candidates its value and its measured ms per step at the
+ * better of its occupancy levels (0 = not timed; the tensor-core form has one
+ * candidate, 20). HOST outputs. */
 int dg_ensemble_tuning(const dg_ctx *ctx, int *best_eb, int *eb, float *ms_per_step);
+
+/* The whole tuning grid: *best = the chosen candidate (0..7, -1 before
+ * tuning); for each of the 8 candidates (elements-per-block value c % 4,
+ * occupancy level c / 4) its elements per block, the blocks per SM it was
+ * launched with and its ms per step (0 = not timed). HOST outputs, may be
+ * NULL. The tensor-core form has one candidate (20, one block per SM). */
+int dg_ensemble_tuning_grid(const dg_ctx *ctx, int *best, int *eb, int *blocks_per_sm, float *ms_per_step);
 
 /* 1 if the last dg_ensemble_step was replayed from a captured CUDA graph. */
 int dg_ensemble_graph_used(const dg_ctx *ctx);

@@ -69,6 +69,7 @@ def lib():
             L.dg_ensemble_step.argtypes = [vp, vp, vp, i32, flt]
             L.dg_ensemble_tune.argtypes = [vp, i32]
             L.dg_ensemble_tuning.argtypes = [vp, C.POINTER(i32), vp, vp]
+            L.dg_ensemble_tuning_grid.argtypes = [vp, C.POINTER(i32), vp, vp, vp]
             L.dg_ensemble_graph_used.argtypes = [vp]
             L.dg_receiver_traces.argtypes = [vp, vp, vp, dbl, i32, flt, vp, i64, vp]
             L.dg_adjoint_step.argtypes = [vp, vp, vp, dbl, i32, i32, flt, vp, i64, vp, C.POINTER(dbl), vp, vp]
@@ -269,6 +270,15 @@ class Solver:
         ms = np.zeros(4, dtype=np.float32)
         self._check(lib().dg_ensemble_tuning(self._h, C.byref(best), _np_ptr(eb), _np_ptr(ms)))
         return best.value, eb.tolist(), ms.tolist()
+
+    def ensemble_tuning_grid(self):
+        """(chosen candidate, [elements per block], [blocks per SM], [ms per step]) over the 8 candidates."""
+        best = C.c_int()
+        eb = np.zeros(8, dtype=np.int32)
+        bps = np.zeros(8, dtype=np.int32)
+        ms = np.zeros(8, dtype=np.float32)
+        self._check(lib().dg_ensemble_tuning_grid(self._h, C.byref(best), _np_ptr(eb), _np_ptr(bps), _np_ptr(ms)))
+        return best.value, eb.tolist(), bps.tolist(), ms.tolist()
 
     def ensemble_graph_used(self) -> bool:
         return bool(lib().dg_ensemble_graph_used(self._h))

@@ -34,22 +34,24 @@ int ensemble_candidate_eb_n7(int);
 int ensemble_candidate_eb_n8(int);
 int ensemble_candidate_eb_n9(int);
 
-extern template cudaError_t launch_ensemble_order<1>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<2>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<3>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<4>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<5>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<6>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<7>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<8>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
-extern template cudaError_t launch_ensemble_order<9>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int);
+extern template cudaError_t launch_ensemble_order<1>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<2>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<3>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<4>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<5>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<6>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<7>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<8>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
+extern template cudaError_t launch_ensemble_order<9>(int, const StageArgs &, const StageCoeffs &, float *, float *, int, GridBarrier *, int *, cudaStream_t, int, int *);
 
 namespace {
 
-constexpr int kCandidates = 4;
+constexpr int kEbCandidates = 4;                   // elements per block
+constexpr int kCandidates = 2 * kEbCandidates;     // x occupancy levels (all resident blocks, half)
 constexpr int kTcTileElems = 20; // elements per tile of the tensor-core form
 
-int candidate_eb(int N, int i) {
+int candidate_eb(int N, int cand) {
+  const int i = cand % kEbCandidates;
   switch (N) {
   case 1: return ensemble_candidate_eb_n1(i);
   case 2: return ensemble_candidate_eb_n2(i);
@@ -64,17 +66,17 @@ int candidate_eb(int N, int i) {
 }
 
 cudaError_t launch_ensemble(int N, int cand, const StageArgs &a, const StageCoeffs &rk, float *ua, float *ub,
-                            int nsteps, GridBarrier *gb, int *flag, cudaStream_t s, int sms) {
+                            int nsteps, GridBarrier *gb, int *flag, cudaStream_t s, int sms, int *used) {
   switch (N) {
-  case 1: return launch_ensemble_order<1>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 2: return launch_ensemble_order<2>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 3: return launch_ensemble_order<3>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 4: return launch_ensemble_order<4>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 5: return launch_ensemble_order<5>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 6: return launch_ensemble_order<6>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 7: return launch_ensemble_order<7>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 8: return launch_ensemble_order<8>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  default: return launch_ensemble_order<9>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  case 1: return launch_ensemble_order<1>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  case 2: return launch_ensemble_order<2>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  case 3: return launch_ensemble_order<3>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  case 4: return launch_ensemble_order<4>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  case 5: return launch_ensemble_order<5>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  case 6: return launch_ensemble_order<6>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  case 7: return launch_ensemble_order<7>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  case 8: return launch_ensemble_order<8>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
+  default: return launch_ensemble_order<9>(cand, a, rk, ua, ub, nsteps, gb, flag, s, sms, used);
   }
 }
 
@@ -84,7 +86,8 @@ struct EnsembleState {
   GridBarrier *gb = nullptr;
   int sms = 0;
   int best = -1;                // chosen candidate
-  float ms[kCandidates] = {0, 0, 0, 0};
+  float ms[kCandidates] = {};
+  int bps[kCandidates] = {}; // blocks per SM each candidate launched with
   std::string gpu;
   // captured graph of one call (rebuilt when its arguments change)
   cudaGraphExec_t exec = nullptr;
@@ -170,7 +173,7 @@ cudaError_t enqueue(dg_ctx *c, EnsembleState &st, int cand, float *u, float *res
   cudaError_t e = tc_ensemble_supported(c)
                       ? launch_tc_ensemble(c, a, coeffs(), u, c->d_scratch, nsteps, st.gb, s)
                       : launch_ensemble(c->N, cand, a, coeffs(), u, c->d_scratch, nsteps, st.gb, c->d_flag + 1, s,
-                                        st.sms);
+                                        st.sms, &st.bps[cand]);
   if (e == cudaSuccess && (5 * nsteps) % 2 == 1)
     e = cudaMemcpyAsync(u, c->d_scratch, size_t(6) * c->K * c->ops.Npad * sizeof(float), cudaMemcpyDeviceToDevice, s);
   return e;
@@ -303,7 +306,10 @@ int dg_ensemble_tune(dg_ctx *ctx, int force) {
   for (int cand = 0; cand < kCandidates && e == cudaSuccess; ++cand) {
     st.ms[cand] = 0.f;
     if (tc && cand > 0) continue;
-    if (cand > 0 && candidate_eb(ctx->N, cand) == candidate_eb(ctx->N, cand - 1)) continue;
+    const int i = cand % kEbCandidates;
+    if (i > 0 && candidate_eb(ctx->N, cand) == candidate_eb(ctx->N, cand - 1)) continue;
+    // the second occupancy level only where it launches fewer blocks than the first
+    if (cand >= kEbCandidates && (st.ms[i] == 0.f || st.bps[i] <= 1)) continue;
     float t_min = 1e30f;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
       e = cudaEventRecord(e0, s);
@@ -336,10 +342,25 @@ int dg_ensemble_tuning(const dg_ctx *ctx, int *best_eb, int *eb, float *ms_per_s
   const EnsembleState *st = static_cast<const EnsembleState *>(ctx->ens);
   const bool tc = tc_ensemble_supported(ctx);
   auto eb_of = [&](int i) { return tc ? (i == 0 ? kTcTileElems : 0) : candidate_eb(ctx->N, i); };
-  if (best_eb) *best_eb = st->best >= 0 ? eb_of(st->best) : 0;
-  for (int i = 0; i < kCandidates; ++i) {
+  if (best_eb) *best_eb = st->best >= 0 ? eb_of(st->best % kEbCandidates) : 0;
+  for (int i = 0; i < kEbCandidates; ++i) {
     if (eb) eb[i] = eb_of(i);
-    if (ms_per_step) ms_per_step[i] = st->ms[i];
+    // the better of the elements-per-block candidate's occupancy levels
+    const float a = st->ms[i], b = st->ms[i + kEbCandidates];
+    if (ms_per_step) ms_per_step[i] = (b > 0.f && (a == 0.f || b < a)) ? b : a;
+  }
+  return DG_OK;
+}
+
+int dg_ensemble_tuning_grid(const dg_ctx *ctx, int *best, int *eb, int *blocks_per_sm, float *ms_per_step) {
+  if (!ctx || !ctx->ens) return DG_ERR_ARG;
+  const EnsembleState *st = static_cast<const EnsembleState *>(ctx->ens);
+  const bool tc = tc_ensemble_supported(ctx);
+  if (best) *best = st->best;
+  for (int c = 0; c < kCandidates; ++c) {
+    if (eb) eb[c] = tc ? (c == 0 ? kTcTileElems : 0) : candidate_eb(ctx->N, c);
+    if (blocks_per_sm) blocks_per_sm[c] = st->ms[c] > 0.f ? (tc ? 1 : st->bps[c]) : 0;
+    if (ms_per_step) ms_per_step[c] = st->ms[c];
   }
   return DG_OK;
 }

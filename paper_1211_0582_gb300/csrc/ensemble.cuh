@@ -54,9 +54,12 @@ struct EnsembleCandidates {
   }
 };
 
+// occ = 0: as many blocks per SM as fit; occ = 1: half as many (rounded up),
+// a second tuning axis (fewer blocks take part in each grid barrier, more
+// tiles per block); the blocks per SM launched go to *used (may be null)
 template <int N, int EB>
 cudaError_t launch_ensemble_eb(const StageArgs &a, const StageCoeffs &rk, float *ua, float *ub, int nsteps,
-                               GridBarrier *gb, int *flag, cudaStream_t s, int sms) {
+                               GridBarrier *gb, int *flag, cudaStream_t s, int sms, int occ, int *used) {
   using Cfg = SimtCfg<N, EB>;
   auto kern = k_ensemble_persistent<N, EB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::SMEM));
@@ -65,6 +68,8 @@ cudaError_t launch_ensemble_eb(const StageArgs &a, const StageCoeffs &rk, float 
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (occ == 1) per_sm = (per_sm + 1) / 2;
+  if (used) *used = per_sm;
   const int64_t ntiles = (a.K + EB - 1) / EB;
   const int64_t cap = int64_t(per_sm) * sms;
   const unsigned grid = unsigned(ntiles < cap ? ntiles : cap);
@@ -81,15 +86,17 @@ cudaError_t launch_ensemble_eb(const StageArgs &a, const StageCoeffs &rk, float 
   return cudaLaunchKernelEx(&cfg, kern, a, rk, ua, ub, nsteps, gb, flag);
 }
 
+// Candidate cand: elements per block C::c(cand % 4), occupancy level cand / 4.
 template <int N>
 cudaError_t launch_ensemble_order(int cand, const StageArgs &a, const StageCoeffs &rk, float *ua, float *ub,
-                                  int nsteps, GridBarrier *gb, int *flag, cudaStream_t s, int sms) {
+                                  int nsteps, GridBarrier *gb, int *flag, cudaStream_t s, int sms, int *used) {
   using C = EnsembleCandidates<N>;
-  switch (cand) {
-  case 0: return launch_ensemble_eb<N, C::c(0)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 1: return launch_ensemble_eb<N, C::c(1)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  case 2: return launch_ensemble_eb<N, C::c(2)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
-  default: return launch_ensemble_eb<N, C::c(3)>(a, rk, ua, ub, nsteps, gb, flag, s, sms);
+  const int occ = cand / 4;
+  switch (cand % 4) {
+  case 0: return launch_ensemble_eb<N, C::c(0)>(a, rk, ua, ub, nsteps, gb, flag, s, sms, occ, used);
+  case 1: return launch_ensemble_eb<N, C::c(1)>(a, rk, ua, ub, nsteps, gb, flag, s, sms, occ, used);
+  case 2: return launch_ensemble_eb<N, C::c(2)>(a, rk, ua, ub, nsteps, gb, flag, s, sms, occ, used);
+  default: return launch_ensemble_eb<N, C::c(3)>(a, rk, ua, ub, nsteps, gb, flag, s, sms, occ, used);
   }
 }
 

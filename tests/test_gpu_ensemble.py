@@ -60,6 +60,15 @@ def test_ensemble_matches_separate_runs(steps):
     assert ens.ensemble_graph_used()
     best, eb, ms = ens.ensemble_tuning()
     assert best in eb and max(ms) > 0
+    # the two-axis grid: elements per block x occupancy level; the chosen
+    # candidate was timed, is the fastest, and its half-occupancy twin (when
+    # timed) launched fewer blocks per SM
+    c, eb8, bps, ms8 = ens.ensemble_tuning_grid()
+    assert 0 <= c < 8 and ms8[c] > 0 and eb8[c] == best
+    assert ms8[c] == min(m for m in ms8 if m > 0)
+    for i in range(4):
+        if ms8[i + 4] > 0:
+            assert 0 < bps[i + 4] < bps[i] and eb8[i + 4] == eb8[i]
 
 
 @pytest.mark.parametrize("steps", [3, 2])
