@@ -23,12 +23,15 @@
 // data and stage traces), as in the CUDA-core form, whose device arithmetic
 // (adj_common.cuh) they share.
 //
-// Per tile: the tile's lambda_r, lambda_u and face data arrive by bulk copies;
-// W lr is split into the A operand of GEMM-D in tensor memory; while GEMM-D
-// runs, the face loop scatters the transposed flux into a shared-memory
-// buffer; the epilogue forms lambda_u + dt (curl^T + flux^T), the next
-// stage's lambda_r = a lambda_r + b_next lambda_u and its split W lr' (over
-// the columns of T, which have been read); GEMM-L lifts it, and the face data
+// Per tile (up to 20 elements: 19 at N = 3, 4 and 18 at N = 5, so that the
+// face loop takes whole rounds of the block's threads): the tile's lambda_r,
+// lambda_u, the E rows of the stage's right-hand side, its face data and
+// per-face constants arrive by bulk copies (requested during the previous
+// tile); W lr is split into the A operand of GEMM-D in tensor memory; while
+// GEMM-D runs, the face loop scatters the transposed flux into a shared-memory
+// buffer; the epilogue forms lambda_u + dt (curl^T + flux^T), the next stage's
+// lambda_r = a lambda_r + b_next lambda_u and its split W lr' (over the
+// columns of T, which have been read); GEMM-L lifts it, and the face data
 // g_next = Fscale G go to global memory. Two blocks per SM at N <= 4 overlap
 // each other's phases. Waits are bounded; a wait that runs out sets the
 // context's device flag and the block leaves.
