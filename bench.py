@@ -331,6 +331,10 @@ def run_ours(args):
     e2e_ms = replica_max_ms(e0.elapsed_time(e1), dist, device)
     field_bytes = 6 * K * Npad * 4
     e2e_value = job_gdof_s(world, dof, e2e_steps, e2e_ms)
+    # the host link's own rate on this machine (the end-to-end number is bounded by
+    # max(copy in, copy out, step) per step when the streams overlap them)
+    h2d_ms = _timed(lambda: [ud[0].copy_(u_h, non_blocking=True) for _ in range(5)], streams[0]) / 5
+    d2h_ms = _timed(lambda: [out_h[0].copy_(ud[0], non_blocking=True) for _ in range(5)], streams[0]) / 5
 
     # ---- roofline of the dominant kernel (the fused stage kernel)
     peaks, peak_kind = measured_peaks()
@@ -357,7 +361,8 @@ def run_ours(args):
                 "how": "each step: u from pinned host memory, 1 LSERK4 step, u back to pinned host memory (res is "
                        "scratch: stage 1 overwrites it unread); the steps are independent problems (the same "
                        "state advanced by one step each time, not one time-marching run), alternating over "
-                       f"{ns} contexts/streams so that copies overlap compute"},
+                       f"{ns} contexts/streams so that copies overlap compute",
+                "h2d_gbs": field_bytes / (h2d_ms * 1e-3) / 1e9, "d2h_gbs": field_bytes / (d2h_ms * 1e-3) / 1e9},
         "gpu_launches": launches, "roofline": roof, "clocks": clk,
         "kernel_ms_per_launch": launch_ms, "energy_after": energy,
     }
