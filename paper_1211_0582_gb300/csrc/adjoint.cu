@@ -613,6 +613,7 @@ extern "C" {
 int dg_adjoint_segment_steps(const dg_ctx *ctx) { return ctx ? ctx->adj_segment : 0; }
 
 int dg_rhs_transpose(dg_ctx *ctx, const float *v, float *w, float alpha) {
+  dgmx::NvtxRange nvtx_range("dg_rhs_transpose");
   if (!ctx) return DG_ERR_ARG;
   if (ctx->K <= 0) return fail(ctx, DG_ERR_ARG, "dg_rhs_transpose: no mesh uploaded");
   if (!v || !w || ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(w)) & 15u))
@@ -636,6 +637,7 @@ int dg_rhs_transpose(dg_ctx *ctx, const float *v, float *w, float alpha) {
 
 int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, float alpha,
                        const int64_t *recv, int64_t R, float *out) {
+  dgmx::NvtxRange nvtx_range("dg_receiver_traces");
   int rc = check_common(ctx, u0, dt, nsteps, alpha, recv, R, "dg_receiver_traces");
   if (rc) return rc;
   if (!out) return fail(ctx, DG_ERR_ARG, "dg_receiver_traces: null output");
@@ -672,6 +674,7 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
 int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, int ckpt_every,
                     float alpha, const int64_t *recv, int64_t R, const float *Eref, double *J, double *dJ_deps,
                     float *dJ_du0) {
+  dgmx::NvtxRange nvtx_range("dg_adjoint_step");
   int rc = check_common(ctx, u0, dt, nsteps, alpha, recv, R, "dg_adjoint_step");
   if (rc) return rc;
   if (!Eref) return fail(ctx, DG_ERR_ARG, "dg_adjoint_step: null Eref");

@@ -179,6 +179,7 @@ int dg_operators(const dg_ctx *ctx, double *r, double *s, double *t, double *Dr,
 
 int dg_mesh_upload(dg_ctx *ctx, int64_t Nv, const double *VX, const double *VY, const double *VZ, int64_t K,
                    const int32_t *EToV, const float *eps, const float *mu, const int32_t *bc) {
+  dgmx::NvtxRange nvtx_range("dg_mesh_upload");
   if (!ctx) return DG_ERR_ARG;
   ctx->err.clear();
   if (!VX || !VY || !VZ || !EToV) return set_err(ctx, DG_ERR_ARG, "dg_mesh_upload: null input array");
@@ -347,6 +348,7 @@ int dg_set_eps(dg_ctx *ctx, const float *eps_dev) {
 }
 
 int dg_rhs(dg_ctx *ctx, const float *u, float *rhs, float alpha) {
+  dgmx::NvtxRange nvtx_range("dg_rhs");
   int rc = check_ready(ctx);
   if (rc) return rc;
   if (!u || !rhs) return set_err(ctx, DG_ERR_ARG, "dg_rhs: null field pointer");
@@ -363,6 +365,7 @@ int dg_rhs(dg_ctx *ctx, const float *u, float *rhs, float alpha) {
 }
 
 int dg_step(dg_ctx *ctx, float *u, float *res, double dt, int nsteps, float alpha) {
+  dgmx::NvtxRange nvtx_range("dg_step");
   int rc = check_ready(ctx);
   if (rc) return rc;
   if (!u || !res) return set_err(ctx, DG_ERR_ARG, "dg_step: null field pointer");
@@ -407,6 +410,7 @@ int dg_set_wait_limit(dg_ctx *ctx, long long cycles) {
 }
 
 int dg_energy(dg_ctx *ctx, const float *u, double *E_out) {
+  dgmx::NvtxRange nvtx_range("dg_energy");
   int rc = check_ready(ctx);
   if (rc) return rc;
   if (!u || !E_out) return set_err(ctx, DG_ERR_ARG, "dg_energy: null pointer");

@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of libdgmx.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -105,6 +106,16 @@ __device__ __forceinline__ void pdl_launch_next_and_wait() {
   pdl_launch_next();
   pdl_wait();
 }
+
+// NVTX range over one C-ABI call (profilers can select the launches of a
+// call by it, e.g. ncu --nvtx --nvtx-include "dg_step/"); header-only NVTX 3,
+// inert unless a tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 template <typename... Params, typename... Args>
 cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {

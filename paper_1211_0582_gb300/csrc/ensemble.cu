@@ -277,6 +277,7 @@ int dg_ensemble_layout(const dg_ctx *ctx, int *M, int64_t *offsets) {
 }
 
 int dg_ensemble_tune(dg_ctx *ctx, int force) {
+  dgmx::NvtxRange nvtx_range("dg_ensemble_tune");
   if (!ctx || !ctx->ens) return DG_ERR_ARG;
   EnsembleState &st = *state(ctx);
   const std::string key = cache_key(st, ctx->N, ctx->precision, ctx->K);
@@ -366,6 +367,7 @@ int dg_ensemble_tuning_grid(const dg_ctx *ctx, int *best, int *eb, int *blocks_p
 }
 
 int dg_ensemble_step(dg_ctx *ctx, float *u, float *res, int nsteps, float alpha) {
+  dgmx::NvtxRange nvtx_range("dg_ensemble_step");
   if (!ctx) return DG_ERR_ARG;
   if (!ctx->ens) return fail(ctx, DG_ERR_ARG, "dg_ensemble_step: no ensemble uploaded");
   if (!u || !res || ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(res)) & 15u))
