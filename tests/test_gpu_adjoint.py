@@ -208,6 +208,31 @@ def test_adjoint_segmentations_agree():
         s.adjoint(u0d, rd, Eref, dt, steps, -1, eps=epsd)
 
 
+def test_adjoint_forms_agree_full_size():
+    # the adjoint workload as the bench times it (20^3 x 6 = 48,000 tets, N=4,
+    # 400 steps, checkpoints every 20, 256 receivers): the tensor-core reverse
+    # stage against the CUDA-core one, for J and both gradients
+    N, n, steps, ck = 4, 20, 400, 20
+    VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
+    K = EToV.shape[0]
+    eps = W.element_eps(K, seed=2)
+    s = dg.Solver(N).upload(VX, VY, VZ, EToV, eps=eps)
+    x, y, z = s.node_coords()
+    u0d = s.to_device(W.gaussian_pulse(x, y, z, seed=7))
+    recv = torch.as_tensor(W.receivers(K, s.Np, 256, seed=4), device="cuda")
+    dt = 0.5 / n / N ** 2
+    epsd = torch.as_tensor(eps, device="cuda")
+    Eref = s.receiver_traces(u0d, recv, dt, steps, eps=torch.as_tensor(W.element_eps(K, seed=6), device="cuda"))
+    out = {}
+    for form in ("tensor", "cuda"):
+        s.set_adjoint_form(form)
+        J, g_eps, g_u0 = s.adjoint(u0d, recv, Eref, dt, steps, ck, eps=epsd)
+        out[form] = (J, g_eps.cpu().numpy(), s.from_device(g_u0))
+    assert abs(out["tensor"][0] - out["cuda"][0]) <= 1e-9 * out["cuda"][0]  # the same forward sweep
+    assert rel(out["tensor"][1], out["cuda"][1]) < 1e-4
+    assert rel(out["tensor"][2], out["cuda"][2]) < 1e-4
+
+
 def test_adjoint_finite_differences_full_size():
     # the adjoint workload: 20^3 x 6 = 48,000 jittered tets, N=4, 400 steps,
     # checkpoints every 20, 256 receivers, E_ref from the target eps (seed 6)
