@@ -246,10 +246,12 @@ int dg_ensemble_graph_used(const dg_ctx *ctx);
 int dg_sync(dg_ctx *ctx);
 
 /* Device-side watchdog: every bounded wait of the stage kernels (tensor-core
- * barriers, the ensemble grid barrier) gives up after `cycles` SM clock cycles;
- * 0 restores the default of 2^31 cycles (about one second). A limit shorter
- * than the work waited for makes the launch give up and dg_sync return
- * DG_ERR_TIMEOUT: the failure-detection path, exercised without a GPU fault.
+ * barriers, the ensemble grid barrier, the tensor-core reverse stage of
+ * dg_adjoint_step) gives up after `cycles` SM clock cycles; 0 restores the
+ * default of 2^31 cycles (about one second). A limit shorter than the work
+ * waited for makes the launch give up and dg_sync (dg_adjoint_step for its
+ * reverse stage) return DG_ERR_TIMEOUT: the failure-detection path, exercised
+ * without a GPU fault.
  * Waits that only drain copies or matrix operations already in flight before
  * a kernel exits keep the default limit. Drops a captured ensemble graph.
  * Returns DG_ERR_ARG for a negative limit. */
