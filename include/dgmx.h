@@ -268,7 +268,9 @@ int dg_rhs_transpose(dg_ctx *ctx, const float *v, float *w, float alpha);
  * permittivity eps (DEVICE, K values; NULL keeps the current one, otherwise it
  * replaces it as dg_set_eps does), recording E at R receiver nodes after every
  * step: out (DEVICE FP32) is [nsteps][3][R]; recv (DEVICE int64, R entries) holds
- * node indices k*Np + i in [0, K*Np). FP32 CUDA-core kernels. Synchronises. */
+ * node indices k*Np + i in [0, K*Np). The context's stage kernel (FP32 CUDA
+ * cores; the tensor-core stage in split-precision contexts at N <= 5).
+ * Synchronises. */
 int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt, int nsteps, float alpha,
                        const int64_t *recv, int64_t R, float *out);
 
@@ -296,8 +298,10 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
  * (DEVICE, K doubles, reduced in FP64; may be NULL), dJ_du0 (DEVICE field
  * vector; may be NULL). With both gradient outputs NULL only the forward run
  * and the misfit are computed (no checkpoints, no reverse sweep; segment
- * length reported as 0). The forward sweeps run the FP32 CUDA-core stage
- * regardless of the context's precision. Each reverse stage is one volume
+ * length reported as 0). The forward sweeps run the context's stage: the
+ * FP32 CUDA-core stage in FP32 contexts (and at N > 5), the tensor-core stage
+ * in split-precision contexts (the gradient of that context's forward map).
+ * Each reverse stage is one volume
  * kernel that also runs the next stage's lift (one separate lift per step,
  * after the receiver source); for N <= 5 on a GB300 its two contractions (the
  * transposed differentiation and lifting matrices) run on the tensor cores in

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "adj_common.cuh"
 #include "flux.cuh"
+#include "tc_api.h"
 
 namespace dgmx {
 
@@ -576,6 +577,14 @@ StageArgs stage_base(const dg_ctx *c, float alpha, double dt) {
   return a;
 }
 
+// One forward LSERK stage of the adjoint's sweeps in the context's precision:
+// the tensor-core stage (with its store form) in split-precision contexts at
+// N <= 5, else the FP32 CUDA-core stage.
+cudaError_t forward_stage(dg_ctx *c, int mode, const StageArgs &a, cudaStream_t s) {
+  if (c->precision != DG_FP32 && c->tc && c->N <= 5) return launch_stage_tc(c, mode, a, s);
+  return launch_stage_simt(c->N, mode, a, s);
+}
+
 int check_common(dg_ctx *ctx, const float *u0, double dt, int nsteps, float alpha, const int64_t *recv, int64_t R,
                  const char *who) {
   if (!ctx) return DG_ERR_ARG;
@@ -658,7 +667,7 @@ int dg_receiver_traces(dg_ctx *ctx, const float *u0, const float *eps, double dt
       a.u_out = nxt;
       a.rk_a = float(kLserkA[st]);
       a.rk_b = float(kLserkB[st]);
-      e = launch_stage_simt(ctx->N, MODE_LSERK, a, s);
+      e = forward_stage(ctx, MODE_LSERK, a, s);
       std::swap(u, nxt);
     }
     if (e == cudaSuccess) {
@@ -707,7 +716,7 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
         sa.u_out = nxt;
         sa.rk_a = float(kLserkA[st]);
         sa.rk_b = float(kLserkB[st]);
-        e = launch_stage_simt(ctx->N, MODE_LSERK, sa, s);
+        e = forward_stage(ctx, MODE_LSERK, sa, s);
         std::swap(u, nxt);
       }
       if (e == cudaSuccess) {
@@ -801,7 +810,7 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
       q.rhs = RSb[b] + hfl * j;
       q.rk_a = float(kLserkA[st]);
       q.rk_b = float(kLserkB[st]);
-      e = launch_stage_simt(ctx->N, MODE_LSERK_STORE, q, st_);
+      e = forward_stage(ctx, MODE_LSERK_STORE, q, st_);
     }
     const size_t jn = size_t(n - n0 + 1) * 5;
     return jn < size_t(5) * C ? USb[b] + fl * jn : nxt_;
@@ -831,7 +840,7 @@ int dg_adjoint_step(dg_ctx *ctx, const float *u0, const float *eps, double dt, i
         sa.u_out = nxt;
         sa.rk_a = float(kLserkA[st]);
         sa.rk_b = float(kLserkB[st]);
-        e = launch_stage_simt(ctx->N, MODE_LSERK, sa, s);
+        e = forward_stage(ctx, MODE_LSERK, sa, s);
         std::swap(u, nxt);
       }
       after = u;

@@ -8,8 +8,11 @@ namespace dgmx {
 int tc_prepare(dg_ctx *ctx);
 // Releases what tc_prepare allocated.
 void tc_free(dg_ctx *ctx);
-// Launches the tensor-core stage kernel on ctx->stream.
+// Launches the tensor-core stage kernel on ctx->stream, or on stream s.
+// MODE_LSERK_STORE (the LSERK stage that also writes the E rows of the
+// right-hand side to a.rhs, [3][K][Np_pad]) is supported at N <= 5.
 cudaError_t launch_stage_tc(dg_ctx *ctx, int mode, const StageArgs &a);
+cudaError_t launch_stage_tc(dg_ctx *ctx, int mode, const StageArgs &a, cudaStream_t s);
 // Orders the persistent multi-step tensor-core kernel supports (N <= 5).
 bool tc_ensemble_supported(const dg_ctx *ctx);
 // Persistent multi-step form for ensembles: nsteps LSERK4 steps in one

@@ -198,7 +198,8 @@ __device__ uint32_t g_tc_trace[kTraceBlocks * kTraceTiles * kTcEvents];
   } while (0)
 #endif
 
-// ENS = false: one stage (MODE_RHS or MODE_LSERK) over all tiles. ENS = true:
+// ENS = false: one stage (MODE_RHS, MODE_LSERK, or MODE_LSERK_STORE, which
+// also writes the E rows of the right-hand side) over all tiles. ENS = true:
 // 5 * nsteps LSERK stages in one cooperative launch, a grid barrier after each
 // stage (a stage reads the neighbours' states the previous one wrote), field
 // gathers through L2 (another SM's L1 may hold a copy from two stages ago).
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t sbase = umma::smem_u32(smem);
   const long long wlim = umma::wait_cycles(a.wait_limit); // main waits; drains use the default
   // the first LSERK4 stage has a = 0: the residual it overwrites is not read
-  bool read_res = MODE == MODE_LSERK && a.rk_a != 0.f;
+  bool read_res = (MODE == MODE_LSERK || MODE == MODE_LSERK_STORE) && a.rk_a != 0.f;
 
   // fields of tile t into the tile buffer, its face and element data into a
   // slot (one thread; completes on barU)
@@ -753,6 +754,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 op[0] = make_float4(nr[0].x, nr[0].y, nr[1].x, nr[1].y);
                 op[6 * FS / 4] = make_float4(nu[0].x, nu[0].y, nu[1].x, nu[1].y);
+                // the store form also keeps the E rows of the right-hand side
+                // (the adjoint's eps gradient reads them): [3][K][Np_pad]
+                if (MODE == MODE_LSERK_STORE && isE)
+                  *reinterpret_cast<float4 *>(a.rhs + fld * KN + (k0 + e_loc) * NPP + i) =
+                      make_float4(r2[0].x, r2[0].y, r2[1].x, r2[1].y);
               }
             }
           }
@@ -1544,6 +1550,9 @@ cudaError_t launch_tc_ens_order(bool bf16, const StageArgs &a, const TcState &st
 
 template <int N>
 cudaError_t launch_tc_order(int mode, bool bf16, const StageArgs &a, const TcState &st, int *flag, cudaStream_t s) {
+  if (mode == MODE_LSERK_STORE) // the single-tile form only
+    return bf16 ? launch_tc_kernel<N, MODE_LSERK_STORE, true>(a, st, flag, s)
+                : launch_tc_kernel<N, MODE_LSERK_STORE, false>(a, st, flag, s);
   if (st.form == 0) {
     if (mode == MODE_RHS)
       return bf16 ? launch_tcw_kernel<N, MODE_RHS, true>(a, st, flag, s)
@@ -1645,17 +1654,22 @@ cudaError_t launch_tc_ensemble(dg_ctx *ctx, const StageArgs &a, const StageCoeff
 }
 
 cudaError_t launch_stage_tc(dg_ctx *ctx, int mode, const StageArgs &a) {
+  return launch_stage_tc(ctx, mode, a, ctx->stream);
+}
+
+cudaError_t launch_stage_tc(dg_ctx *ctx, int mode, const StageArgs &a, cudaStream_t s) {
   const TcState *st = static_cast<const TcState *>(ctx->tc);
   if (!st) return cudaErrorNotReady;
+  if (mode == MODE_LSERK_STORE && ctx->N > 5) return cudaErrorNotSupported;
   const bool bf16 = ctx->precision == DG_BF16X3;
   int *flag = ctx->d_flag + 1;
   switch (ctx->N) {
-  case 1: return launch_tc_order<1>(mode, bf16, a, *st, flag, ctx->stream);
-  case 2: return launch_tc_order<2>(mode, bf16, a, *st, flag, ctx->stream);
-  case 3: return launch_tc_order<3>(mode, bf16, a, *st, flag, ctx->stream);
-  case 4: return launch_tc_order<4>(mode, bf16, a, *st, flag, ctx->stream);
-  case 5: return launch_tc_order<5>(mode, bf16, a, *st, flag, ctx->stream);
-  default: return launch_tc_streamed(ctx->N, mode, bf16, a, *st, flag, ctx->stream);
+  case 1: return launch_tc_order<1>(mode, bf16, a, *st, flag, s);
+  case 2: return launch_tc_order<2>(mode, bf16, a, *st, flag, s);
+  case 3: return launch_tc_order<3>(mode, bf16, a, *st, flag, s);
+  case 4: return launch_tc_order<4>(mode, bf16, a, *st, flag, s);
+  case 5: return launch_tc_order<5>(mode, bf16, a, *st, flag, s);
+  default: return launch_tc_streamed(ctx->N, mode, bf16, a, *st, flag, s);
   }
 }
 

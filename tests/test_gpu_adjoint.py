@@ -28,11 +28,11 @@ def rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-def setup(N, n, eps_seed=2):
+def setup(N, n, eps_seed=2, precision="fp32"):
     VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
     K = EToV.shape[0]
     eps = W.element_eps(K, seed=eps_seed)
-    s = dg.Solver(N).upload(VX, VY, VZ, EToV, eps=eps)
+    s = dg.Solver(N, precision=precision).upload(VX, VY, VZ, EToV, eps=eps)
     m = O.Mesh(N, VX, VY, VZ, EToV, eps=eps.astype(np.float64))
     return s, m, eps
 
@@ -50,8 +50,8 @@ def test_transpose_parity_and_identity(N, n):
         assert abs(lhs - rhs) < 1e-5 * np.linalg.norm(Au) * np.linalg.norm(v)
 
 
-def _misfit_problem(N, n, steps):
-    s, m, eps = setup(N, n, eps_seed=2)
+def _misfit_problem(N, n, steps, precision="fp32"):
+    s, m, eps = setup(N, n, eps_seed=2, precision=precision)
     K = m.K
     x, y, z = s.node_coords()
     u0 = W.gaussian_pulse(x, y, z, seed=7)
@@ -107,6 +107,25 @@ def test_adjoint_forms_agree_with_the_oracle(N, n):
         out[form] = (g_eps.cpu().numpy(), s.from_device(g_u0))
     assert rel(out["tensor"][0], out["cuda"][0]) < 2e-5
     assert rel(out["tensor"][1], out["cuda"][1]) < 2e-5
+
+
+@pytest.mark.parametrize("N,n", [(3, 3), (4, 3), (5, 2)])
+def test_adjoint_in_split_precision_context_matches_oracle(N, n):
+    # an FP16x3 context: the receiver traces and the adjoint's forward sweeps
+    # run the tensor-core stage (its store form keeps the stage states and
+    # right-hand sides of a segment), the reverse stage the tensor-core one;
+    # checkpoints every 3 of 7 steps
+    steps, ck = 7, 3
+    s, m, eps, eps_t, u0, u0d, recv, rd, Eref, dt = _misfit_problem(N, n, steps, precision="fp16x3")
+    ref = m.receiver_traces(u0, dt, steps, recv, eps=eps_t.astype(np.float64))
+    assert rel(Eref.double().cpu().numpy(), ref) < 1e-5
+    epsd = torch.as_tensor(eps, device="cuda")
+    J, g_eps, g_u0 = s.adjoint(u0d, rd, Eref, dt, steps, ck, eps=epsd)
+    Jo, go_eps, go_u0 = m.misfit_gradient(u0, dt, steps, recv, Eref.double().cpu().numpy(),
+                                          eps=eps.astype(np.float64))
+    assert abs(J - Jo) < 1e-5 * Jo
+    assert rel(g_eps.cpu().numpy(), go_eps) < 1e-4
+    assert rel(s.from_device(g_u0), go_u0) < 1e-4
 
 
 def test_adjoint_tensor_form_wait_timeout_and_recovery():
