@@ -602,7 +602,7 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
-def adjoint_leg(stream, steps: int = 400, fd_dirs: int = 16) -> dict:
+def adjoint_leg(stream, steps: int = 400, fd_dirs: int = 16, precision: str = "fp32") -> dict:
     """Adjoint workload: 20^3 x 6 jittered tets, N=4, FP32, 256 receivers, `steps`
     steps; adjoint-to-forward cost with checkpoints every 20 steps and with the
     segment length the library picks from the free device memory (the whole run
@@ -616,7 +616,7 @@ def adjoint_leg(stream, steps: int = 400, fd_dirs: int = 16) -> dict:
     VX, VY, VZ, EToV = W.kuhn_cube(n, jitter=0.1, seed=1)
     K = EToV.shape[0]
     eps = W.element_eps(K, seed=2)
-    s = dg.Solver(N, stream=stream).upload(VX, VY, VZ, EToV, eps=eps)
+    s = dg.Solver(N, precision=precision, stream=stream).upload(VX, VY, VZ, EToV, eps=eps)
     x, y, z = s.node_coords()
     u0 = s.to_device(W.gaussian_pulse(x, y, z, seed=7))
     recv = torch.as_tensor(W.receivers(K, s.Np, 256, seed=4), device="cuda")
@@ -646,14 +646,16 @@ def adjoint_leg(stream, steps: int = 400, fd_dirs: int = 16) -> dict:
         s.set_adjoint_form("tensor")
     # the same gradient in an FP16x3 context: the forward sweeps and the
     # forward it is compared with run the tensor-core stage
-    s16 = dg.Solver(N, precision="fp16x3", stream=stream).upload(VX, VY, VZ, EToV, eps=eps)
+    s16 = s if precision == "fp16x3" else \
+        dg.Solver(N, precision="fp16x3", stream=stream).upload(VX, VY, VZ, EToV, eps=eps)
     uf16, rf16 = u0.clone(), s16.zeros()
     s16.step(uf16, rf16, dt, 3)
     uf16, rf16 = u0.clone(), s16.zeros()
     fwd16_ms = _timed(lambda: s16.step(uf16, rf16, dt, steps), stream)
     s16.adjoint(u0, recv, Eref, dt, steps, 20, eps=epsd)
     adj16_20_ms = _timed(lambda: s16.adjoint(u0, recv, Eref, dt, steps, 20, eps=epsd), stream)
-    del s16
+    if s16 is not s:
+        del s16
     h = 1e-3
     dirs = 2.0 * W.uniform(5, 16 * K).reshape(16, K)[:fd_dirs] - 1.0
     rels = []
@@ -665,7 +667,7 @@ def adjoint_leg(stream, steps: int = 400, fd_dirs: int = 16) -> dict:
         fd, ad = Jp - Jm, float((g_eps * (ep.double() - em.double())).sum())
         rels.append(abs(fd - ad) / abs(fd))
     dof = 6 * s.Np * K
-    return {"workload": f"adjoint, 20^3x6 jittered tets, N=4, FP32, 256 receivers, {steps} steps",
+    return {"workload": f"adjoint, 20^3x6 jittered tets, N=4, {precision} context, 256 receivers, {steps} steps",
             "K": K, "dof": dof, "steps": steps, "forward_ms": fwd_ms,
             "forward_gdof_s": STAGES * dof * steps / (fwd_ms * 1e-3) / 1e9, "J": J,
             "reverse_stage": form + (" cores: FP16x3 tcgen05 transposed contractions, face loop on the CUDA cores"
@@ -691,10 +693,11 @@ def run_adjoint(args):
     16 finite-difference directions)."""
     import torch
     torch.cuda.set_device(0)
-    leg = adjoint_leg(torch.cuda.current_stream(), steps=args.steps, fd_dirs=16)
+    leg = adjoint_leg(torch.cuda.current_stream(), steps=args.steps, fd_dirs=16, precision=args.adjoint_precision)
     line = {"metric": METRIC, "value": leg["automatic_segments"]["ratio"], "unit": "adjoint/forward time",
             "n_gpus": 1, "steps": args.steps, "warmup": 3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.adjoint_precision == "fp32" else args.adjoint_precision,
+            "data": "synthetic",
             "config": {"workload": leg["workload"] + " (value: automatic segments)", "K": leg["K"],
                        "dof": leg["dof"]}, "adjoint": leg}
     print(json.dumps(line), flush=True)
@@ -715,6 +718,8 @@ def main():
     ap.add_argument("--e2e-streams", type=int, default=4, help="contexts/streams the end-to-end steps alternate over")
     ap.add_argument("--cpu-sample", type=int, default=50000, help="elements in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-precision", choices=["fp32", "bf16x3", "fp16x3"], default="fp32",
+                    help="context precision of the adjoint workload (the configuration's is fp32)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="leave the adjoint block (20^3 N=4, 400 steps, cost ratios) out of the default line")
     ap.add_argument("--no-precisions", action="store_true",
