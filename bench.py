@@ -314,21 +314,26 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(streams[0])
-    for j in range(1, ns):
-        streams[j].wait_event(e0)
-    for i in range(e2e_steps):
-        j = i % ns
-        with torch.cuda.stream(streams[j]):
-            ud[j].copy_(u_h, non_blocking=True)
-            solvers[j].step(ud[j], rd[j], dt, 1)
-            out_h[j].copy_(ud[j], non_blocking=True)
-    for j in range(1, ns):
-        streams[0].wait_stream(streams[j])
-    e1.record(streams[0])
-    torch.cuda.synchronize()
-    e2e_ms = replica_max_ms(e0.elapsed_time(e1), dist, device)
+    # three repetitions of the timed pipeline; the median is reported (the
+    # figure has varied between runs on boxes with equal host-link rates)
+    e2e_reps = []
+    for _rep in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(streams[0])
+        for j in range(1, ns):
+            streams[j].wait_event(e0)
+        for i in range(e2e_steps):
+            j = i % ns
+            with torch.cuda.stream(streams[j]):
+                ud[j].copy_(u_h, non_blocking=True)
+                solvers[j].step(ud[j], rd[j], dt, 1)
+                out_h[j].copy_(ud[j], non_blocking=True)
+        for j in range(1, ns):
+            streams[0].wait_stream(streams[j])
+        e1.record(streams[0])
+        torch.cuda.synchronize()
+        e2e_reps.append(replica_max_ms(e0.elapsed_time(e1), dist, device))
+    e2e_ms = statistics.median(e2e_reps)
     field_bytes = 6 * K * Npad * 4
     e2e_value = job_gdof_s(world, dof, e2e_steps, e2e_ms)
     # the host link's own rate on this machine (the end-to-end number is bounded by
@@ -362,7 +367,8 @@ def run_ours(args):
                        "scratch: stage 1 overwrites it unread); the steps are independent problems (the same "
                        "state advanced by one step each time, not one time-marching run), alternating over "
                        f"{ns} contexts/streams so that copies overlap compute",
-                "h2d_gbs": field_bytes / (h2d_ms * 1e-3) / 1e9, "d2h_gbs": field_bytes / (d2h_ms * 1e-3) / 1e9},
+                "h2d_gbs": field_bytes / (h2d_ms * 1e-3) / 1e9, "d2h_gbs": field_bytes / (d2h_ms * 1e-3) / 1e9,
+                "repeats_ms": e2e_reps, "statistic": "median of 3 repetitions"},
         "gpu_launches": launches, "roofline": roof, "clocks": clk,
         "kernel_ms_per_launch": launch_ms, "energy_after": energy,
     }
